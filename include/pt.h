@@ -1,0 +1,185 @@
+/*
+ * pt.h -- C ABI of the GB300 parallel-tempering quantum Monte Carlo (PT-QMC) library.
+ *
+ * The method is the data-parallel core of Karimi, Dickson & Hamze, "High-Performance
+ * Physics Simulations Using Multi-Core CPUs and GPGPUs in a Volunteer Computing
+ * Context": Parallel Tempering over R chains (Sec. 2), each chain a Suzuki-Trotter stack
+ * of P coupled copies of an N-spin Ising problem (Sec. 6, Table 1), swept with the
+ * Metropolis rule in two groups of independent regions (Sec. 5), and neighbouring
+ * chains swapped in disjoint pairs (Sec. 2). Every step runs in sm_103a CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (PT_OK) or a negative PT_E* code. Errors are sticky per context: once a
+ *     call on a context fails with PT_ECUDA or PT_ETIMEDOUT, later calls return the same
+ *     code. pt_last_error() gives a one-line message.
+ *   - Inputs are copied at create; the caller keeps ownership of every pointer passed.
+ *   - Outputs go into caller-allocated HOST buffers; the calls that fill them synchronise
+ *     the context's stream.
+ *   - pt_sweep / pt_swap / pt_run only enqueue work on the context's stream (asynchronous).
+ *   - Spin states cross the boundary as int8 +1/-1 in rung order:
+ *       state[(r*N + i)*P + k] = copy k of site i of the chain currently on rung r.
+ *   - The library needs a CUDA device (sm_103a). There is no CPU fallback: without one,
+ *     pt_create fails with PT_ENODEV.
+ *
+ * The model (Sec. 6's coupled classical copies of a quantum Ising problem):
+ *   E(s) = sum_edges J_ij s_i s_j + sum_i h_i s_i, integer;
+ *   rung r: beta = 1/T_r, a = beta*Gamma_r/P, K_r = -1/2 ln tanh(a);
+ *   a chain X = s[i][k] (k periodic mod P) on rung r samples exp(-S_r(X)) with
+ *   S_r = (beta/P) sum_k E(s^k) - K_r M(X),  M(X) = sum_k sum_i s_i^k s_i^{k+1}.
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PT_OK 0
+#define PT_EINVAL -1     /* invalid argument (message in pt_last_error) */
+#define PT_ENOMEM -2     /* device or host allocation failed */
+#define PT_ECUDA -3      /* a CUDA call failed (sticky) */
+#define PT_EOVERFLOW -4  /* a counter or int64 accumulator could overflow */
+#define PT_ETIMEDOUT -5  /* a device-side wait gave up (sticky) */
+#define PT_EBUSY -6      /* no free slot or device memory for a request */
+#define PT_ENODEV -7     /* no usable CUDA device */
+
+typedef struct pt_ctx pt_ctx;
+
+/* One Ising instance. Edges (ei[b], ej[b]) are distinct unordered pairs of distinct
+ * sites in [0, n) with J[b] != 0; |h_i| + sum_j |J_ij| <= 127 for every site; n <= 65535. */
+typedef struct {
+    int32_t n;
+    int32_t n_edges;
+    const int32_t* ei;
+    const int32_t* ej;
+    const int32_t* J;
+    const int32_t* h;
+} pt_instance;
+
+/* One rung of the ladder: temperature T > 0 and transverse field gamma > 0. */
+typedef struct {
+    double T;
+    double gamma;
+} pt_rung;
+
+/* Optional settings (zero-initialised = defaults). */
+typedef struct {
+    int32_t threads_per_block;  /* 0 = choose automatically; else a multiple of 32 <= 1024 */
+    int32_t wait_timeout_ms;    /* limit of every device-side wait; 0 = 5000 ms */
+    int32_t swap_mode;          /* 0 = auto, 1 = swaps inside one cooperative launch,
+                                   2 = one launch per sweep interval + a swap launch */
+    int32_t test_withhold_rung; /* test hook, 0 = off: if r+1, the chain on rung r never
+                                   publishes its swap mailbox, so its partner's wait runs out
+                                   and the call fails with PT_ETIMEDOUT (no fault, no hang) */
+    int32_t reserved[4];
+} pt_options;
+
+/* Statistics (Fig. 4 "gather statistics"; Sec. 5 accumulates in high precision).
+ * Per-rung arrays have R entries, per-pair arrays R-1. All caller-allocated. */
+typedef struct {
+    int64_t t;          /* sweeps done */
+    int64_t q;          /* swap passes done */
+    int64_t* E;         /* [R] sum_k E(s^k) of the chain on rung r */
+    int64_t* M;         /* [R] M(X) of the chain on rung r */
+    int64_t* n_meas;    /* [R] sweeps accumulated (one measurement after every sweep) */
+    int64_t* sum_E;     /* [R] sum over measurements of E */
+    int64_t* sum_E2;    /* [R] ... of E^2 */
+    int64_t* sum_M;     /* [R] ... of M */
+    int64_t* sum_M2;    /* [R] ... of M^2 */
+    int64_t* flip_acc;  /* [R] accepted spin flips while on rung r */
+    int64_t* swap_att;  /* [R-1] swap attempts of pair (r, r+1) */
+    int64_t* swap_acc;  /* [R-1] accepted swaps of pair (r, r+1) */
+    int32_t* replica_at;/* [R] chain (replica id, = its starting rung) now on rung r */
+} pt_observables;
+
+/* Layout and schedule facts of a context (for tests and the benchmark). */
+typedef struct {
+    int32_t n, P, R, lmax, max_degree;
+    int32_t n_levels;          /* dependency levels of one sweep (see pt_create) */
+    int32_t threads_per_block;
+    int32_t cooperative;       /* 1 if swaps run inside one launch */
+    int64_t device_bytes;      /* device memory held by the context */
+    int64_t kernel_launches;   /* kernels this context has launched so far */
+    int64_t h2d_bytes;         /* bytes copied host -> device so far */
+} pt_info;
+
+/* Create a PT-QMC problem on the current CUDA device (Sec. 2: chains and temperatures
+ * are fixed before the run, Sec. 5 / Fig. 6: data moved to the device once).
+ *   inst        Ising instance (copied).
+ *   P           Trotter copies, even, 2 <= P <= 4096.
+ *   ladder, R   R >= 1 rungs (copied), 1 <= R <= 65535.
+ *   flip_thr    NULL to build the Metropolis table in FP64 on the host, or R*(2*Lmax+1)*3
+ *               uint32 thresholds [r][L+Lmax][m/2+1] (accept iff thr == 0xFFFFFFFF or
+ *               u < thr) where Lmax = max_i(|h_i| + sum_j |J_ij|).
+ *   swap_coef   NULL to build from the ladder, or 2*(R-1) doubles a_0..a_{R-2}, c_0..c_{R-2}
+ *               (swap of X on r with Y on r+1 has log-ratio a_r (E_X-E_Y) + c_r (M_X-M_Y)).
+ *   seed        64-bit Philox4x32-10 key; every random number is a function of
+ *               (seed, counter), independent of the launch layout.
+ *   opt         NULL for defaults.
+ *   cuda_stream cudaStream_t to use, or NULL for a stream owned by the context.
+ * Initial spins come from the key: copy k of site i of chain rho is -1 iff bit 31 of
+ * word k%4 of philox((0, i, rho, 2<<28 | k/4), seed) is set.
+ * Returns PT_EINVAL, PT_ENOMEM, PT_ECUDA or PT_ENODEV on failure (*out untouched). */
+int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladder, int32_t R,
+              const uint32_t* flip_thr, const double* swap_coef, uint64_t seed,
+              const pt_options* opt, void* cuda_stream, pt_ctx** out);
+
+/* n >= 0 Metropolis sweeps of every chain (Sec. 2, Sec. 5). Sweep t visits sites in
+ * index order; at each site it updates the even copies, then the odd copies. Copy
+ * k = p + 2h of site i of chain rho draws word h%4 of philox((t, i, rho, p<<24 | h/4)).
+ * Statistics are accumulated after every sweep. Asynchronous. */
+int pt_sweep(pt_ctx* ctx, int64_t n);
+
+/* One swap pass q (Sec. 2: neighbouring chains, disjoint pairs): pairs (r, r+1) for
+ * r = q%2, q%2+2, ...; accept iff Delta >= 0, or Delta > -23 and u < min(floor(2^32
+ * exp(Delta)), 2^32-1) with u = word 0 of philox((q, r, 0, 1<<28)) and exp evaluated by
+ * the Cody-Waite/Taylor sequence of IEEE operations. Asynchronous. */
+int pt_swap(pt_ctx* ctx);
+
+/* Fig. 4's loop: n_sweeps sweeps with a swap pass after every sweeps_per_swap-th sweep
+ * (0 = no swaps). Bit-identical to the equivalent sequence of pt_sweep / pt_swap calls. */
+int pt_run(pt_ctx* ctx, int64_t n_sweeps, int32_t sweeps_per_swap);
+
+/* Copy the state, rung-ordered int8 (+1/-1), into out (bytes >= R*N*P). Synchronises. */
+int pt_read_state(pt_ctx* ctx, int8_t* out, size_t bytes);
+
+/* Overwrite the state (rung-ordered int8 +1/-1, bytes = R*N*P) and recompute E and M
+ * of every chain on the device. Counters and statistics are kept. Synchronises. */
+int pt_write_state(pt_ctx* ctx, const int8_t* in, size_t bytes);
+
+/* Fill the caller's arrays with the current statistics. Synchronises. */
+int pt_read_observables(pt_ctx* ctx, pt_observables* out);
+
+/* Copy the tables the context uses: thr (R*(2*Lmax+1)*3) and coef (2*(R-1)); either
+ * pointer may be NULL. Host data, no synchronisation. */
+int pt_read_tables(const pt_ctx* ctx, uint32_t* thr, size_t thr_count, double* coef,
+                   size_t coef_count);
+
+int pt_get_info(const pt_ctx* ctx, pt_info* out);
+
+/* Host-only helpers (no device needed): the exact setup data pt_create uses.
+ * pt_make_tables fills thr[R*(2*lmax+1)*3] and coef[2*(R-1)] from the ladder in FP64
+ * (either may be NULL). pt_make_schedule writes the sweep's level schedule: items[2n]
+ * ((i<<1)|parity, grouped by level) and level_off[n_levels+1] (room for 2n+1 entries);
+ * update (i,1) comes after (i,0), and (i,p) after (j,p) for every neighbour j < i. */
+int pt_make_tables(int32_t P, const pt_rung* ladder, int32_t R, int32_t lmax, uint32_t* thr,
+                   double* coef);
+int pt_make_schedule(const pt_instance* inst, uint32_t* items, int32_t* level_off,
+                     int32_t* n_levels);
+
+/* Wait for all queued work of the context. */
+int pt_sync(pt_ctx* ctx);
+
+/* Free the context (synchronises first). NULL is a no-op. */
+int pt_destroy(pt_ctx* ctx);
+
+/* One-line message of the last error on ctx (or of the last failed create if ctx is NULL). */
+const char* pt_last_error(const pt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,612 @@
+// pt_host.cu -- host side of the PT-QMC C ABI (include/pt.h): validation, the FP64
+// Metropolis and swap tables, the neighbour table, the sweep's level schedule, device
+// memory, and the launch sequence. Every step of the method itself runs in the kernels
+// of pt_kernels.cu; this file only prepares inputs and orders launches.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pt.h"
+#include "pt_internal.h"
+
+using namespace ptq;
+
+struct pt_ctx {
+    DevProblem dp;
+    LaunchPlan plan;
+    cudaStream_t stream;
+    bool own_stream;
+    int device;
+    int n_edges;
+    int max_degree;
+    long long t, q;
+    long long sweep_limit;   // t never exceeds this (int64 statistics, 32-bit Philox counter)
+    int max_passes;          // mailbox capacity of one launch
+    bool cooperative;
+    long long timeout_ns;
+    int err;
+    char msg[256];
+    std::vector<uint32_t> thr;   // host copy of the tables
+    std::vector<double> coef;
+    std::vector<void*> allocs;
+    int8_t* staging;             // [R*N*P] rung-ordered state for reads and writes
+    int64_t device_bytes;
+    int64_t launches;            // kernels launched by this context
+    int64_t h2d_bytes;           // bytes copied host -> device
+};
+
+static thread_local char g_create_msg[256] = "";
+
+static int ctx_fail(pt_ctx* c, int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+    va_end(ap);
+    if (code == PT_ECUDA || code == PT_ETIMEDOUT) c->err = code;  // sticky
+    return code;
+}
+
+static int create_fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_create_msg, sizeof(g_create_msg), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+// ---------------------------------------------------------------------------------
+// Metropolis thresholds and swap coefficients in FP64 (host libm), in this order of
+// operations: beta = 1/T; a = (beta*Gamma)/P; K = -0.5*log(tanh(a)); for copy flips
+// x = ((2*beta)/P)*L - (2*K)*m and thr = 0xFFFFFFFF if x >= 0, else
+// min(floor(exp(x)*2^32), 0xFFFFFFFF); for swaps a_r = beta_r/P - beta_{r+1}/P and
+// c_r = K_{r+1} - K_r. Flipping copy k of site i changes the action S by
+// -(2 beta/P) L + 2 K m, with L = s(h + sum J s_j) and m = s(s^{k-1} + s^{k+1}).
+static void build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vector<uint32_t>& thr,
+                         std::vector<double>& coef) {
+    const int nL = 2 * Lmax + 1;
+    thr.assign((size_t)R * nL * 3, 0u);
+    coef.assign(2 * (size_t)(R > 1 ? R - 1 : 0), 0.0);
+    std::vector<double> K(R), b(R);
+    for (int r = 0; r < R; ++r) {
+        const double beta = 1.0 / ladder[r].T;
+        const double a = beta * ladder[r].gamma / (double)P;
+        K[r] = -0.5 * log(tanh(a));
+        b[r] = beta / (double)P;
+        const double c_flip = 2.0 * beta / (double)P;
+        const double c_trot = 2.0 * K[r];
+        for (int L = -Lmax; L <= Lmax; ++L) {
+            for (int mi = 0; mi < 3; ++mi) {
+                const int m = 2 * mi - 2;
+                const double x = c_flip * (double)L - c_trot * (double)m;
+                uint32_t v;
+                if (x >= 0.0) {
+                    v = 0xFFFFFFFFu;
+                } else {
+                    const double f = floor(ldexp(exp(x), 32));
+                    v = (f >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)f;
+                }
+                thr[((size_t)r * nL + (size_t)(L + Lmax)) * 3 + (size_t)mi] = v;
+            }
+        }
+    }
+    for (int r = 0; r + 1 < R; ++r) {
+        coef[r] = b[r] - b[r + 1];
+        coef[(size_t)(R - 1) + r] = K[r + 1] - K[r];
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Level schedule of one sweep. The sequential order is (0,0), (0,1), (1,0), (1,1), ...
+// where (i, p) updates every copy of parity p of site i. Two updates conflict only if
+// they are (i,0) and (i,1), or (i,p) and (j,p) with i, j adjacent; the level of an update
+// is one more than the largest level of the earlier updates it conflicts with.
+static void level_schedule(int N, const std::vector<std::vector<int>>& adj, std::vector<uint32_t>& items,
+                           std::vector<int32_t>& level_off) {
+    std::vector<int> l0(N), l1(N);
+    int nlev = 0;
+    for (int i = 0; i < N; ++i) {
+        int a = 0, b = 0;
+        for (int j : adj[i])
+            if (j < i) {
+                a = std::max(a, l0[j] + 1);
+                b = std::max(b, l1[j] + 1);
+            }
+        l0[i] = a;
+        l1[i] = std::max(b, a + 1);
+        nlev = std::max(nlev, l1[i] + 1);
+    }
+    std::vector<int> count(nlev + 1, 0);
+    for (int i = 0; i < N; ++i) {
+        count[l0[i] + 1]++;
+        count[l1[i] + 1]++;
+    }
+    level_off.assign(nlev + 1, 0);
+    for (int l = 0; l < nlev; ++l) level_off[l + 1] = level_off[l] + count[l + 1];
+    items.assign(2 * (size_t)N, 0u);
+    std::vector<int> fill(level_off.begin(), level_off.end() - 1);
+    for (int i = 0; i < N; ++i) {
+        items[fill[l0[i]]++] = ((uint32_t)i << 1) | 0u;
+        items[fill[l1[i]]++] = ((uint32_t)i << 1) | 1u;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+template <typename T>
+static cudaError_t dev_alloc(pt_ctx* c, T** ptr, size_t count) {
+    void* p = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return e;
+    c->allocs.push_back(p);
+    c->device_bytes += (int64_t)bytes;
+    *ptr = (T*)p;
+    return cudaSuccess;
+}
+
+static void free_ctx(pt_ctx* c) {
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+static int check_status(pt_ctx* c) {
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, c->dp.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ctx_fail(c, PT_ECUDA, "CUDA error: %s", cudaGetErrorString(e));
+    if (st == PT_ETIMEDOUT) return ctx_fail(c, PT_ETIMEDOUT, "a device-side wait for a swap partner timed out");
+    if (st != 0) return ctx_fail(c, PT_ECUDA, "device status %d", st);
+    return PT_OK;
+}
+
+#define CUDA_OR_FAIL(c, call)                                                                   \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return ctx_fail((c), PT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladder, int32_t R,
+                         const uint32_t* flip_thr, const double* swap_coef, uint64_t seed,
+                         const pt_options* opt, void* cuda_stream, pt_ctx** out) {
+    if (!inst || !ladder || !out) return create_fail(PT_EINVAL, "null argument");
+    const int N = inst->n, nE = inst->n_edges;
+    if (N < 1 || N > 65535) return create_fail(PT_EINVAL, "n must be in [1, 65535]");
+    if (nE < 0 || (nE > 0 && (!inst->ei || !inst->ej || !inst->J)) || !inst->h)
+        return create_fail(PT_EINVAL, "bad edge arrays");
+    if (P < 2 || (P & 1) || P > 4096) return create_fail(PT_EINVAL, "P must be even and in [2, 4096]");
+    if (R < 1 || R > 65535) return create_fail(PT_EINVAL, "R must be in [1, 65535]");
+    const bool need_ladder = !flip_thr || !swap_coef;
+    if (need_ladder)
+        for (int r = 0; r < R; ++r)
+            if (!(ladder[r].T > 0.0) || !(ladder[r].gamma > 0.0) || !isfinite(ladder[r].T) ||
+                !isfinite(ladder[r].gamma))
+                return create_fail(PT_EINVAL, "rung %d: T and gamma must be finite and > 0", r);
+
+    // adjacency, duplicate / self-loop checks
+    std::vector<std::vector<int>> adj(N);
+    std::vector<std::vector<int>> adjJ(N);
+    for (int b = 0; b < nE; ++b) {
+        const int u = inst->ei[b], v = inst->ej[b], J = inst->J[b];
+        if (u < 0 || u >= N || v < 0 || v >= N || u == v)
+            return create_fail(PT_EINVAL, "edge %d: endpoints must be distinct sites in range", b);
+        if (J == 0 || J < -127 || J > 127) return create_fail(PT_EINVAL, "edge %d: J must be in [-127,127]\\{0}", b);
+        adj[u].push_back(v);
+        adjJ[u].push_back(J);
+        adj[v].push_back(u);
+        adjJ[v].push_back(J);
+    }
+    int dmax = 0, Lmax = 0;
+    for (int i = 0; i < N; ++i) {
+        std::vector<int> sorted = adj[i];
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+            return create_fail(PT_EINVAL, "duplicate edge at site %d", i);
+        dmax = std::max(dmax, (int)adj[i].size());
+        int l = abs(inst->h[i]);
+        for (int J : adjJ[i]) l += abs(J);
+        if (l > 127) return create_fail(PT_EINVAL, "site %d: |h| + sum |J| must be <= 127", i);
+        Lmax = std::max(Lmax, l);
+    }
+    if (dmax > 32) return create_fail(PT_EINVAL, "maximum degree 32 supported");
+    const int dclass = dmax <= 4 ? 4 : (dmax <= 8 ? 8 : 32);
+
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1)
+        return create_fail(PT_ENODEV, "no CUDA device");
+
+    pt_ctx* c = new pt_ctx();
+    c->own_stream = false;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->t = c->q = 0;
+    c->err = 0;
+    c->msg[0] = 0;
+    c->staging = nullptr;
+    c->device_bytes = 0;
+    c->launches = 0;
+    c->h2d_bytes = 0;
+    c->n_edges = nE;
+    c->max_degree = dmax;
+    cudaGetDevice(&c->device);
+    if (!c->stream) {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return create_fail(PT_ECUDA, "cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    const int timeout_ms = (opt && opt->wait_timeout_ms > 0) ? opt->wait_timeout_ms : 5000;
+    c->timeout_ns = (long long)timeout_ms * 1000000ll;
+
+    // tables
+    if (!flip_thr || !swap_coef) build_tables(R, P, Lmax, ladder, c->thr, c->coef);
+    const size_t nthr = (size_t)R * (2 * Lmax + 1) * 3;
+    if (flip_thr) c->thr.assign(flip_thr, flip_thr + nthr);
+    if (swap_coef) c->coef.assign(swap_coef, swap_coef + 2 * (size_t)(R - 1));
+    if (c->coef.empty()) c->coef.assign(2, 0.0);
+
+    // neighbour table (j << 8) | (uint8)J, rows padded to the kernel's degree class with (i, 0)
+    std::vector<uint32_t> nbr((size_t)N * dclass);
+    std::vector<int8_t> h8(N);
+    for (int i = 0; i < N; ++i) {
+        h8[i] = (int8_t)inst->h[i];
+        for (int d = 0; d < dclass; ++d) {
+            if (d < (int)adj[i].size())
+                nbr[(size_t)i * dclass + d] = ((uint32_t)adj[i][d] << 8) | (uint32_t)(uint8_t)(int8_t)adjJ[i][d];
+            else
+                nbr[(size_t)i * dclass + d] = (uint32_t)i << 8;
+        }
+    }
+    std::vector<uint32_t> items;
+    std::vector<int32_t> level_off;
+    level_schedule(N, adj, items, level_off);
+
+    DevProblem& p = c->dp;
+    memset(&p, 0, sizeof(p));
+    p.N = N;
+    p.P = P;
+    p.R = R;
+    p.Lmax = Lmax;
+    p.nL3 = (2 * Lmax + 1) * 3;
+    p.dmax = dclass;
+    p.n_levels = (int)level_off.size() - 1;
+    p.slot_stride = (int)(((size_t)N * P + 15) & ~(size_t)15);
+    p.withhold_rung = (opt && opt->test_withhold_rung > 0) ? opt->test_withhold_rung - 1 : -1;
+    p.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
+    p.key1 = (uint32_t)(seed >> 32);
+
+    // launch plan
+    int max_smem = 0, n_sm = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    c->plan.dclass = dclass;
+    c->plan.smem_bytes = sweep_smem_bytes(p);
+    if ((long long)c->plan.smem_bytes > (long long)max_smem) {
+        free_ctx(c);
+        return create_fail(PT_EINVAL, "one chain needs %zu bytes of shared memory; the device allows %d",
+                           sweep_smem_bytes(p), max_smem);
+    }
+    if (opt && opt->threads_per_block > 0) {
+        if (opt->threads_per_block % 32 || opt->threads_per_block > 512) {
+            free_ctx(c);
+            return create_fail(PT_EINVAL, "threads_per_block must be a multiple of 32 <= 512");
+        }
+        c->plan.threads = opt->threads_per_block;
+    } else {
+        // enough threads for the average level (units = items * padded groups per parity)
+        int G = ((P / 2) + 3) / 4, Gp = 1;
+        while (Gp < G) Gp <<= 1;
+        const long long units = 2ll * N * Gp;
+        long long avg = (units + p.n_levels - 1) / p.n_levels;
+        avg = ((avg + 31) / 32) * 32;
+        c->plan.threads = (int)std::min<long long>(512, std::max<long long>(128, avg));
+    }
+
+    // overflow guard: |E| <= P * (sum|J| + sum|h|), |M| <= N*P; sum of squares stays in int64
+    {
+        long long eb = 0;
+        for (int b = 0; b < nE; ++b) eb += abs(inst->J[b]);
+        for (int i = 0; i < N; ++i) eb += abs(inst->h[i]);
+        eb *= P;
+        const long long mb = (long long)N * P;
+        const long long big = std::max(std::max(eb, mb), 1ll);
+        const long long lim_sq = big > 3037000499ll ? 0 : (long long)(9223372036854775807ll / (big * big));
+        c->sweep_limit = std::min<long long>(lim_sq, 0xFFFFFFFFll);
+    }
+
+    // device memory
+    cudaError_t e = cudaSuccess;
+    uint32_t *d_nbr, *d_items, *d_thr;
+    int8_t* d_h;
+    int32_t* d_loff;
+    double* d_coef;
+    const int max_passes = 1024;
+    c->max_passes = max_passes;
+    if ((e = dev_alloc(c, &d_nbr, nbr.size())) != cudaSuccess ||
+        (e = dev_alloc(c, &d_h, (size_t)N)) != cudaSuccess ||
+        (e = dev_alloc(c, &d_items, items.size())) != cudaSuccess ||
+        (e = dev_alloc(c, &d_loff, level_off.size())) != cudaSuccess ||
+        (e = dev_alloc(c, &d_thr, c->thr.size())) != cudaSuccess ||
+        (e = dev_alloc(c, &d_coef, c->coef.size())) != cudaSuccess ||
+        (e = dev_alloc(c, &p.spins, (size_t)R * p.slot_stride)) != cudaSuccess ||
+        (e = dev_alloc(c, &p.E, (size_t)R)) != cudaSuccess || (e = dev_alloc(c, &p.M, (size_t)R)) != cudaSuccess ||
+        (e = dev_alloc(c, &p.rung_of_slot, (size_t)R)) != cudaSuccess ||
+        (e = dev_alloc(c, &p.slot_of_rung, (size_t)R)) != cudaSuccess ||
+        (e = dev_alloc(c, &p.acc, (size_t)R * kAccCount)) != cudaSuccess ||
+        (e = dev_alloc(c, &p.swap_stats, 2 * (size_t)R)) != cudaSuccess ||
+        (e = dev_alloc(c, &p.mbox, (size_t)max_passes * R)) != cudaSuccess ||
+        (e = dev_alloc(c, &p.status, (size_t)4)) != cudaSuccess ||
+        (e = dev_alloc(c, &c->staging, (size_t)R * N * P)) != cudaSuccess) {
+        free_ctx(c);
+        return create_fail(e == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA, "cudaMalloc: %s",
+                           cudaGetErrorString(e));
+    }
+    p.nbr = d_nbr;
+    p.h = d_h;
+    p.items = d_items;
+    p.level_off = d_loff;
+    p.thr = d_thr;
+    p.coef = d_coef;
+
+    cudaStream_t s = c->stream;
+#define CREATE_CUDA(call)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            cudaStreamSynchronize(s);                                                  \
+            free_ctx(c);                                                               \
+            return create_fail(PT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));     \
+        }                                                                              \
+    } while (0)
+    CREATE_CUDA(cudaMemcpyAsync(d_nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(cudaMemcpyAsync(d_h, h8.data(), (size_t)N, cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(cudaMemcpyAsync(d_loff, level_off.data(), level_off.size() * 4, cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(cudaMemcpyAsync(d_thr, c->thr.data(), c->thr.size() * 4, cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(cudaMemcpyAsync(d_coef, c->coef.data(), c->coef.size() * 8, cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(cudaMemsetAsync(p.spins, 0, (size_t)R * p.slot_stride, s));
+    CREATE_CUDA(cudaMemsetAsync(p.acc, 0, (size_t)R * kAccCount * 8, s));
+    CREATE_CUDA(cudaMemsetAsync(p.swap_stats, 0, 2 * (size_t)R * 8, s));
+    CREATE_CUDA(cudaMemsetAsync(p.mbox, 0, (size_t)max_passes * R * sizeof(Mailbox), s));
+    CREATE_CUDA(cudaMemsetAsync(p.status, 0, 16, s));
+    CREATE_CUDA(launch_init(p, s));
+    CREATE_CUDA(launch_energy(p, s));
+    c->launches += 2;
+    c->h2d_bytes += (int64_t)(nbr.size() * 4 + (size_t)N + items.size() * 4 + level_off.size() * 4 +
+                              c->thr.size() * 4 + c->coef.size() * 8);
+    CREATE_CUDA(prepare_sweep_kernel(c->plan));
+    CREATE_CUDA(cudaStreamSynchronize(s));
+#undef CREATE_CUDA
+
+    // cooperative launch (swaps inside one launch) needs every chain resident at once
+    int per_sm = 0;
+    int coop_ok = 0;
+    cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, c->device);
+    if (sweep_kernel_occupancy(p, c->plan, &per_sm) != cudaSuccess) per_sm = 0;
+    const int mode = opt ? opt->swap_mode : 0;
+    c->cooperative = coop_ok && (long long)per_sm * n_sm >= R && mode != 2;
+    if (mode == 1 && !c->cooperative) {
+        free_ctx(c);
+        return create_fail(PT_EINVAL, "swap_mode 1 needs all %d chains resident at once (%d per SM x %d SMs)", R,
+                           per_sm, n_sm);
+    }
+    *out = c;
+    return PT_OK;
+}
+
+static int guard(pt_ctx* c) {
+    if (!c) return PT_EINVAL;
+    if (c->err) return c->err;
+    return PT_OK;
+}
+
+static int enqueue_sweeps(pt_ctx* c, long long n, int sps) {
+    // chunks of at most max_passes swap passes (mailbox capacity), aligned to the swap interval
+    long long done = 0;
+    while (done < n) {
+        long long chunk = n - done;
+        if (sps > 0) chunk = std::min<long long>(chunk, (long long)c->max_passes * sps);
+        chunk = std::min<long long>(chunk, 1ll << 30);
+        const int passes = sps > 0 ? (int)(chunk / sps) : 0;
+        CUDA_OR_FAIL(c, launch_sweeps(c->dp, c->plan, c->t, c->q, (int)chunk, sps, passes, c->timeout_ns,
+                                      sps > 0, c->stream));
+        c->launches += 1;
+        c->t += chunk;
+        c->q += passes;
+        done += chunk;
+    }
+    return PT_OK;
+}
+
+extern "C" int pt_sweep(pt_ctx* c, int64_t n) {
+    int g = guard(c);
+    if (g) return g;
+    if (n < 0) return ctx_fail(c, PT_EINVAL, "n must be >= 0");
+    if (c->t + n > c->sweep_limit) return ctx_fail(c, PT_EOVERFLOW, "sweep count would exceed %lld", c->sweep_limit);
+    return enqueue_sweeps(c, n, 0);
+}
+
+extern "C" int pt_swap(pt_ctx* c) {
+    int g = guard(c);
+    if (g) return g;
+    if (c->q + 1 > 0xFFFFFFFFll) return ctx_fail(c, PT_EOVERFLOW, "swap pass counter exhausted");
+    CUDA_OR_FAIL(c, launch_swap(c->dp, c->q, c->stream));
+    c->launches += 1;
+    c->q += 1;
+    return PT_OK;
+}
+
+extern "C" int pt_run(pt_ctx* c, int64_t n_sweeps, int32_t sps) {
+    int g = guard(c);
+    if (g) return g;
+    if (n_sweeps < 0 || sps < 0) return ctx_fail(c, PT_EINVAL, "n_sweeps and sweeps_per_swap must be >= 0");
+    if (c->t + n_sweeps > c->sweep_limit)
+        return ctx_fail(c, PT_EOVERFLOW, "sweep count would exceed %lld", c->sweep_limit);
+    if (sps == 0 || c->dp.R == 1) {
+        int rc = enqueue_sweeps(c, n_sweeps, 0);
+        if (rc) return rc;
+        if (sps > 0) c->q += n_sweeps / sps;  // R == 1: passes have no pairs
+        return PT_OK;
+    }
+    if (c->q + n_sweeps / sps > 0xFFFFFFFFll) return ctx_fail(c, PT_EOVERFLOW, "swap pass counter exhausted");
+    if (c->cooperative) {
+        const long long full = (n_sweeps / sps) * sps;
+        int rc = enqueue_sweeps(c, full, sps);
+        if (rc) return rc;
+        return enqueue_sweeps(c, n_sweeps - full, 0);
+    }
+    for (long long s = 0; s + sps <= n_sweeps; s += sps) {
+        int rc = enqueue_sweeps(c, sps, 0);
+        if (rc) return rc;
+        CUDA_OR_FAIL(c, launch_swap(c->dp, c->q, c->stream));
+        c->launches += 1;
+        c->q += 1;
+    }
+    return enqueue_sweeps(c, n_sweeps % sps, 0);
+}
+
+extern "C" int pt_sync(pt_ctx* c) {
+    int g = guard(c);
+    if (g) return g;
+    return check_status(c);
+}
+
+extern "C" int pt_read_state(pt_ctx* c, int8_t* out, size_t bytes) {
+    int g = guard(c);
+    if (g) return g;
+    const size_t need = (size_t)c->dp.R * c->dp.N * c->dp.P;
+    if (!out || bytes < need) return ctx_fail(c, PT_EINVAL, "state buffer needs %zu bytes", need);
+    CUDA_OR_FAIL(c, launch_gather_state(c->dp, c->staging, c->stream));
+    c->launches += 1;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(out, c->staging, need, cudaMemcpyDeviceToHost, c->stream));
+    return check_status(c);
+}
+
+extern "C" int pt_write_state(pt_ctx* c, const int8_t* in, size_t bytes) {
+    int g = guard(c);
+    if (g) return g;
+    const size_t need = (size_t)c->dp.R * c->dp.N * c->dp.P;
+    if (!in || bytes != need) return ctx_fail(c, PT_EINVAL, "state buffer must be %zu bytes", need);
+    for (size_t x = 0; x < need; ++x)
+        if (in[x] != 1 && in[x] != -1) return ctx_fail(c, PT_EINVAL, "spins must be +1 or -1");
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->staging, in, need, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, launch_scatter_state(c->dp, c->staging, c->stream));
+    CUDA_OR_FAIL(c, launch_energy(c->dp, c->stream));
+    c->launches += 2;
+    c->h2d_bytes += (int64_t)need;
+    return check_status(c);
+}
+
+extern "C" int pt_read_observables(pt_ctx* c, pt_observables* o) {
+    int g = guard(c);
+    if (g) return g;
+    if (!o) return ctx_fail(c, PT_EINVAL, "null observables");
+    const int R = c->dp.R;
+    std::vector<long long> E(R), M(R);
+    std::vector<int32_t> rung_of(R), slot_of(R);
+    std::vector<unsigned long long> acc((size_t)R * kAccCount), sw(2 * (size_t)R);
+    cudaStream_t s = c->stream;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(E.data(), c->dp.E, R * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(M.data(), c->dp.M, R * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(slot_of.data(), c->dp.slot_of_rung, R * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(acc.data(), c->dp.acc, acc.size() * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(sw.data(), c->dp.swap_stats, sw.size() * 8, cudaMemcpyDeviceToHost, s));
+    int rc = check_status(c);
+    if (rc) return rc;
+    o->t = c->t;
+    o->q = c->q;
+    for (int r = 0; r < R; ++r) {
+        const int slot = slot_of[r];
+        if (o->E) o->E[r] = E[slot];
+        if (o->M) o->M[r] = M[slot];
+        const unsigned long long* a = &acc[(size_t)r * kAccCount];
+        if (o->n_meas) o->n_meas[r] = (int64_t)a[kAccN];
+        if (o->sum_E) o->sum_E[r] = (int64_t)a[kAccE];
+        if (o->sum_E2) o->sum_E2[r] = (int64_t)a[kAccE2];
+        if (o->sum_M) o->sum_M[r] = (int64_t)a[kAccM];
+        if (o->sum_M2) o->sum_M2[r] = (int64_t)a[kAccM2];
+        if (o->flip_acc) o->flip_acc[r] = (int64_t)a[kAccFlip];
+        if (o->replica_at) o->replica_at[r] = slot;
+    }
+    for (int r = 0; r + 1 < R; ++r) {
+        if (o->swap_att) o->swap_att[r] = (int64_t)sw[2 * r];
+        if (o->swap_acc) o->swap_acc[r] = (int64_t)sw[2 * r + 1];
+    }
+    return PT_OK;
+}
+
+extern "C" int pt_read_tables(const pt_ctx* c, uint32_t* thr, size_t thr_count, double* coef, size_t coef_count) {
+    if (!c) return PT_EINVAL;
+    if (thr) {
+        if (thr_count < c->thr.size()) return PT_EINVAL;
+        memcpy(thr, c->thr.data(), c->thr.size() * 4);
+    }
+    if (coef) {
+        const size_t n = 2 * (size_t)(c->dp.R - 1);
+        if (coef_count < n) return PT_EINVAL;
+        memcpy(coef, c->coef.data(), n * 8);
+    }
+    return PT_OK;
+}
+
+extern "C" int pt_get_info(const pt_ctx* c, pt_info* o) {
+    if (!c || !o) return PT_EINVAL;
+    o->n = c->dp.N;
+    o->P = c->dp.P;
+    o->R = c->dp.R;
+    o->lmax = c->dp.Lmax;
+    o->max_degree = c->max_degree;
+    o->n_levels = c->dp.n_levels;
+    o->threads_per_block = c->plan.threads;
+    o->cooperative = c->cooperative ? 1 : 0;
+    o->device_bytes = c->device_bytes;
+    o->kernel_launches = c->launches;
+    o->h2d_bytes = c->h2d_bytes;
+    return PT_OK;
+}
+
+extern "C" int pt_make_tables(int32_t P, const pt_rung* ladder, int32_t R, int32_t lmax, uint32_t* thr,
+                              double* coef) {
+    if (!ladder || P < 2 || (P & 1) || R < 1 || lmax < 0 || lmax > 127) return PT_EINVAL;
+    for (int r = 0; r < R; ++r)
+        if (!(ladder[r].T > 0.0) || !(ladder[r].gamma > 0.0)) return PT_EINVAL;
+    std::vector<uint32_t> t;
+    std::vector<double> c;
+    build_tables(R, P, lmax, ladder, t, c);
+    if (thr) memcpy(thr, t.data(), t.size() * 4);
+    if (coef && R > 1) memcpy(coef, c.data(), 2 * (size_t)(R - 1) * 8);
+    return PT_OK;
+}
+
+extern "C" int pt_make_schedule(const pt_instance* inst, uint32_t* items, int32_t* level_off, int32_t* n_levels) {
+    if (!inst || !items || !level_off || !n_levels || inst->n < 1) return PT_EINVAL;
+    std::vector<std::vector<int>> adj(inst->n);
+    for (int b = 0; b < inst->n_edges; ++b) {
+        const int u = inst->ei[b], v = inst->ej[b];
+        if (u < 0 || u >= inst->n || v < 0 || v >= inst->n || u == v) return PT_EINVAL;
+        adj[u].push_back(v);
+        adj[v].push_back(u);
+    }
+    std::vector<uint32_t> it;
+    std::vector<int32_t> off;
+    level_schedule(inst->n, adj, it, off);
+    memcpy(items, it.data(), it.size() * 4);
+    memcpy(level_off, off.data(), off.size() * 4);
+    *n_levels = (int32_t)off.size() - 1;
+    return PT_OK;
+}
+
+extern "C" int pt_destroy(pt_ctx* c) {
+    if (!c) return PT_OK;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+    return PT_OK;
+}
+
+extern "C" const char* pt_last_error(const pt_ctx* c) { return c ? c->msg : g_create_msg; }

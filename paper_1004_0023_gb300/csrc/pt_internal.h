@@ -1,0 +1,73 @@
+// pt_internal.h -- structures shared by the host side (pt_host.cu) and the kernels
+// (pt_kernels.cu) of the PT-QMC library. Not part of the public ABI (include/pt.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ptq {
+
+// Stream tags in the top nibble of Philox counter word 3.
+constexpr uint32_t kTagFlip = 0u;
+constexpr uint32_t kTagSwap = 1u;
+constexpr uint32_t kTagInit = 2u;
+
+// One (pass, rung) mailbox of the in-kernel swap: the chain on rung r publishes its
+// (E, M) after the sweep that precedes pass q, then sets tag = q + 1 (release).
+struct alignas(32) Mailbox {
+    long long E;
+    long long M;
+    unsigned long long tag;
+    long long pad;
+};
+
+// Per-rung statistics, in this order, as unsigned 64-bit two's-complement sums.
+enum { kAccN = 0, kAccE, kAccE2, kAccM, kAccM2, kAccFlip, kAccCount };
+
+// Device view of one PT problem. All pointers are device pointers.
+struct DevProblem {
+    // instance (read-only)
+    const uint32_t* nbr;       // [N][dmax]: (j << 8) | (uint8_t)J; padding has J = 0, j = i
+    const int8_t* h;           // [N]
+    const uint32_t* items;     // [2N] (i << 1) | parity, grouped by dependency level
+    const int32_t* level_off;  // [n_levels + 1]
+    const uint32_t* thr;       // [R][nL*3] Metropolis thresholds
+    const double* coef;        // [2(R-1)] a_r then c_r
+    // state
+    int8_t* spins;             // [R slots][slot_stride] int8, copy index fastest
+    long long* E;              // [slot]
+    long long* M;              // [slot]
+    int32_t* rung_of_slot;     // [slot]
+    int32_t* slot_of_rung;     // [rung]
+    unsigned long long* acc;   // [rung][kAccCount]
+    unsigned long long* swap_stats;  // [pair][2] attempts, accepts
+    Mailbox* mbox;             // [max_passes][R]
+    int* status;               // 0 or a PT_E* code set by a kernel
+    int N, P, R, Lmax, nL3, dmax, n_levels;
+    int slot_stride;           // bytes between slots in `spins` (multiple of 16)
+    int withhold_rung;         // test hook: rung whose chain never publishes (-1 = off)
+    uint32_t key0, key1;
+};
+
+struct LaunchPlan {
+    int threads;         // threads per CTA
+    int dclass;          // 4, 8 or 32: padded neighbour count the kernel is built for
+    size_t smem_bytes;   // dynamic shared memory per CTA
+};
+
+// Sizes of the dynamic shared-memory carve-up of the sweep kernel.
+size_t sweep_smem_bytes(const DevProblem& p);
+
+// Kernel launchers (pt_kernels.cu). Each returns a cudaError_t from the launch.
+cudaError_t launch_init(const DevProblem& p, cudaStream_t s);
+cudaError_t launch_energy(const DevProblem& p, cudaStream_t s);
+cudaError_t launch_sweeps(const DevProblem& p, const LaunchPlan& plan, long long t0,
+                          long long q0, int n_sweeps, int sweeps_per_swap, int n_passes,
+                          long long timeout_ns, bool cooperative, cudaStream_t s);
+cudaError_t launch_swap(const DevProblem& p, long long q, cudaStream_t s);
+cudaError_t launch_gather_state(const DevProblem& p, int8_t* out, cudaStream_t s);
+cudaError_t launch_scatter_state(const DevProblem& p, const int8_t* in, cudaStream_t s);
+cudaError_t sweep_kernel_occupancy(const DevProblem& p, const LaunchPlan& plan, int* blocks_per_sm);
+cudaError_t prepare_sweep_kernel(const LaunchPlan& plan);
+
+}  // namespace ptq

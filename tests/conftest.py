@@ -18,3 +18,21 @@ def oracle_lib():
     from oracle import oracle as orc
 
     return orc.load()
+
+
+@pytest.fixture(scope="session")
+def libpt():
+    """Build (if stale) and load the CUDA library; nvcc cross-compiles without a GPU."""
+    from paper_1004_0023_gb300 import build, pt
+
+    build.build()
+    return pt.load()
+
+
+def has_gpu():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False

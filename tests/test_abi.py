@@ -1,0 +1,105 @@
+"""The C-ABI library builds, loads and exports every entry point of include/pt.h; its
+host-only setup (FP64 tables, level schedule) matches the oracle and the sequential
+order. No compute call needs a GPU here."""
+import ctypes
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_1004_0023_gb300 import instances
+from paper_1004_0023_gb300 import pt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(pt_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_every_declared_symbol_is_exported(libpt):
+    names = declared_entry_points()
+    assert {"pt_create", "pt_sweep", "pt_swap", "pt_run", "pt_read_state",
+            "pt_read_observables"} <= names
+    for n in sorted(names):
+        assert hasattr(libpt, n), n
+    assert names <= set(pt.exported_symbols()) | names
+
+
+def test_create_without_device_fails_loudly(libpt):
+    import conftest
+
+    if conftest.has_gpu():
+        pytest.skip("a GPU is present")
+    prob = instances.workload("regular3_n16_p32_r16", 1)
+    with pytest.raises(pt.PTError) as e:
+        pt.PT.from_problem(prob)
+    assert e.value.code in (pt.PT_ENODEV, pt.PT_ECUDA)
+
+
+@pytest.mark.parametrize("name", ["regular3_n16_p32_r16", "regular3_n256_p64_r64", "chimera16_n2048_p128_r96"])
+def test_host_tables_bit_identical_to_oracle(libpt, name):
+    prob = instances.workload(name, 1)
+    o = Oracle.from_problem(prob)
+    thr, coef = pt.make_tables(prob.P, prob.T, prob.gamma, o.lmax)
+    assert np.array_equal(thr, o.flip_table())
+    assert np.array_equal(coef.view(np.uint64), o.swap_coef().view(np.uint64))
+
+
+def test_host_tables_reject_bad_ladder(libpt):
+    with pytest.raises(pt.PTError):
+        pt.make_tables(4, [1.0, 0.0], [1.0, 1.0], 3)
+    with pytest.raises(pt.PTError):
+        pt.make_tables(3, [1.0], [1.0], 3)
+
+
+def _check_schedule(n, ei, ej):
+    items, off = pt.make_schedule(n, ei, ej)
+    assert sorted(items.tolist()) == list(range(2 * n))
+    level = np.empty(2 * n, np.int64)
+    for l in range(off.size - 1):
+        for it in items[off[l]:off[l + 1]]:
+            level[it] = l
+    adj = [set() for _ in range(n)]
+    for a, b in zip(ei, ej):
+        adj[a].add(b)
+        adj[b].add(a)
+    # every pair of conflicting updates keeps its sequential order (strictly earlier level)
+    for i in range(n):
+        assert level[2 * i] < level[2 * i + 1]
+        for j in adj[i]:
+            if j < i:
+                assert level[2 * j] < level[2 * i]
+                assert level[2 * j + 1] < level[2 * i + 1]
+    # and the schedule is as short as the dependencies allow: each update at level l > 0
+    # has a predecessor at level l - 1
+    for i in range(n):
+        for p in (0, 1):
+            l = level[2 * i + p]
+            if l == 0:
+                continue
+            preds = [level[2 * j + p] for j in adj[i] if j < i] + ([level[2 * i]] if p == 1 else [])
+            assert max(preds) == l - 1
+    return off.size - 1
+
+
+def test_schedule_respects_sequential_order():
+    for name in ("regular3_n16_p32_r16", "regular3_n256_p64_r64", "chimera16_n2048_p128_r96"):
+        prob = instances.workload(name, 1)
+        nlev = _check_schedule(prob.n, prob.ei, prob.ej)
+        assert nlev < 2 * prob.n
+    # a path 0-1-2-...: fully sequential even part, odd part one level behind
+    n = 6
+    nlev = _check_schedule(n, list(range(n - 1)), list(range(1, n)))
+    assert nlev == n + 1
+    # no edges: everything in two levels
+    assert _check_schedule(5, [], []) == 2

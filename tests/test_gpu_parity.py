@@ -1,0 +1,191 @@
+"""GPU path (through the C ABI) against the CPU oracle: bit-exact spins, integer E and M,
+int64 statistics, counters and the rung permutation, at many checkpoints.
+
+Tolerance is zero: integer couplings keep every quantity exact, the Metropolis table is
+the same FP64-built uint32 table on both sides, random numbers are the same Philox4x32-10
+counters, and the swap exp is the same sequence of IEEE operations.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_1004_0023_gb300 import instances
+from paper_1004_0023_gb300 import pt
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 1
+
+
+def assert_same(g, o, where=""):
+    xs_g, xs_o = g.read_state(), o.read_state()
+    if not np.array_equal(xs_g, xs_o):
+        bad = np.argwhere(xs_g != xs_o)
+        raise AssertionError("%s: %d spins differ, first (rung, site, copy) = %s" % (where, len(bad), bad[:5].tolist()))
+    og, oo = g.obs(), o.obs()
+    for k in oo:
+        assert np.array_equal(np.asarray(og[k]), np.asarray(oo[k])), (where, k, og[k], oo[k])
+
+
+def both(prob, threads=THREADS, **kw):
+    okw = {k: v for k, v in kw.items() if k in ("flip_thr", "swap_coef")}
+    return pt.PT.from_problem(prob, **kw), Oracle.from_problem(prob, threads=threads, **okw)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(libpt):
+    return libpt
+
+
+TINY = {
+    "line_p4_r3": instances.tiny_problem(3, [(0, 1), (1, 2)], [1, -2], [1, 0, -1], 4, [0.7, 1.0, 1.4],
+                                         [0.9, 1.2, 1.6], seed=11),
+    "single_spin_p2_r2": instances.tiny_problem(1, [], [], [1], 2, [0.5, 1.0], [0.5, 1.5], seed=12),
+    "no_edges_p6_r1": instances.tiny_problem(4, [], [], [1, -1, 0, 2], 6, [0.8], [1.1], seed=13),
+    "prism_p10_r4": instances.tiny_problem(6, [(0, 1), (1, 2), (2, 0), (3, 4), (4, 5), (5, 3), (0, 3), (1, 4), (2, 5)],
+                                           [1, -2, 1, 2, -1, -1, 1, -2, 2], [1, 0, -1, 0, 1, 0], 10,
+                                           [0.6, 0.8, 1.1, 1.5], [0.4, 0.8, 1.4, 2.2], seed=14),
+    "complete10_p12_r5": instances.tiny_problem(
+        10, [(i, j) for i in range(10) for j in range(i + 1, 10)],
+        [((i * 7 + j * 3) % 5) - 2 or 1 for i in range(10) for j in range(i + 1, 10)],
+        [0, 1, -1, 2, 0, 0, 1, -2, 0, 1], 12, [0.5, 0.7, 1.0, 1.4, 2.0], [0.3, 0.6, 1.0, 1.5, 2.5], seed=15),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TINY))
+def test_tiny_problems_every_sweep(name):
+    prob = TINY[name]
+    g, o = both(prob)
+    assert_same(g, o, "initial")
+    for s in range(1, 41):
+        g.run(1, 1)
+        o.run(1, 1)
+        assert_same(g, o, "sweep %d" % s)
+    g.run(500, 3)
+    o.run(500, 3)
+    assert_same(g, o, "after 500 more")
+
+
+def test_small_workload_full_length():
+    """Random 3-regular N=16, P=32, R=16, linear Gamma 0.1..3.0 at T=0.05, 10^4 sweeps,
+    one swap pass per sweep; checked every 500 sweeps."""
+    prob = instances.workload("regular3_n16_p32_r16", 1)
+    g, o = both(prob)
+    for chunk in range(prob.n_sweeps // 500):
+        g.run(500, 1)
+        o.run(500, 1)
+        assert_same(g, o, "sweep %d" % (500 * (chunk + 1)))
+
+
+def test_medium_workload_full_length():
+    """Random 3-regular N=256, P=64, R=64, geometric Gamma 0.05..4.0 at T=0.02, 2000 sweeps;
+    bit-exact state check every 100 sweeps."""
+    prob = instances.workload("regular3_n256_p64_r64", 1)
+    g, o = both(prob)
+    for chunk in range(prob.n_sweeps // 100):
+        g.run(100, 1)
+        o.run(100, 1)
+        assert_same(g, o, "sweep %d" % (100 * (chunk + 1)))
+
+
+@pytest.mark.parametrize("seed_index", [2, 3])
+def test_medium_workload_other_seeds(seed_index):
+    prob = instances.workload("regular3_n256_p64_r64", seed_index)
+    g, o = both(prob)
+    g.run(200, 1)
+    o.run(200, 1)
+    assert_same(g, o, "seed %d" % seed_index)
+
+
+def test_layouts_and_swap_modes_give_identical_bits():
+    prob = instances.workload("regular3_n16_p32_r16", 2)
+    ref = None
+    for kw in (dict(threads_per_block=32), dict(threads_per_block=128), dict(threads_per_block=512),
+               dict(swap_mode=2), dict(swap_mode=1, threads_per_block=64)):
+        g = pt.PT.from_problem(prob, **kw)
+        g.run(300, 1)
+        g.run(77, 5)
+        cur = (g.read_state(), g.obs())
+        if ref is None:
+            ref = cur
+        else:
+            assert np.array_equal(cur[0], ref[0]), kw
+            for k in ref[1]:
+                assert np.array_equal(np.asarray(cur[1][k]), np.asarray(ref[1][k])), (kw, k)
+
+
+def test_run_equals_sweep_and_swap_calls():
+    prob = instances.workload("regular3_n16_p32_r16", 3)
+    a = pt.PT.from_problem(prob)
+    b = pt.PT.from_problem(prob)
+    a.run(60, 3)
+    for _ in range(20):
+        b.sweep(3)
+        b.swap()
+    assert np.array_equal(a.read_state(), b.read_state())
+    oa, ob = a.obs(), b.obs()
+    for k in oa:
+        assert np.array_equal(np.asarray(oa[k]), np.asarray(ob[k])), k
+
+
+def test_tables_read_back_equal_oracle():
+    prob = instances.workload("regular3_n256_p64_r64", 1)
+    g, o = both(prob)
+    thr, coef = g.tables()
+    assert np.array_equal(thr, o.flip_table())
+    assert np.array_equal(coef.view(np.uint64), o.swap_coef().view(np.uint64))
+
+
+def test_all_accept_table_and_write_state():
+    prob = instances.workload("regular3_n16_p32_r16", 4)
+    lmax = Oracle.from_problem(prob).lmax
+    thr = np.full((prob.R, 2 * lmax + 1, 3), 0xFFFFFFFF, np.uint32)
+    g, o = both(prob, flip_thr=thr)
+    rng = np.random.default_rng(0)
+    x = np.where(rng.random((prob.R, prob.n, prob.P)) < 0.5, -1, 1).astype(np.int8)
+    g.write_state(x)
+    o.write_state(x)
+    assert_same(g, o, "written")
+    g.sweep(1)
+    o.sweep(1)
+    assert np.array_equal(g.read_state(), -x)
+    assert_same(g, o, "negated")
+
+
+def test_invalid_arguments_are_rejected():
+    prob = instances.workload("regular3_n16_p32_r16", 1)
+    with pytest.raises(pt.PTError) as e:
+        pt.PT(prob.n, prob.ei, prob.ej, prob.J, prob.h, 3, prob.T, prob.gamma, 1)
+    assert e.value.code == pt.PT_EINVAL
+    bad_J = prob.J.copy()
+    bad_J[0] = 0
+    with pytest.raises(pt.PTError):
+        pt.PT(prob.n, prob.ei, prob.ej, bad_J, prob.h, prob.P, prob.T, prob.gamma, 1)
+    g = pt.PT.from_problem(prob)
+    with pytest.raises(pt.PTError) as e:
+        g.write_state(np.zeros((prob.R, prob.n, prob.P), np.int8))
+    assert e.value.code == pt.PT_EINVAL
+    with pytest.raises(pt.PTError) as e:
+        g.sweep(1 << 40)
+    assert e.value.code == pt.PT_EOVERFLOW
+    g.run(10, 1)  # still usable after argument errors
+
+
+def test_partner_that_never_publishes_times_out_without_fault():
+    """The chain on rung 3 withholds its mailbox: its partner's bounded wait runs out, the
+    call reports PT_ETIMEDOUT, and the device stays usable for a new context."""
+    prob = instances.workload("regular3_n16_p32_r16", 5)
+    g = pt.PT.from_problem(prob, wait_timeout_ms=200, test_withhold_rung=3, swap_mode=1)
+    g.run(4, 1)
+    with pytest.raises(pt.PTError) as e:
+        g.sync()
+    assert e.value.code == pt.PT_ETIMEDOUT
+    with pytest.raises(pt.PTError):  # sticky
+        g.run(1, 1)
+    g.close()
+    h, o = both(prob)
+    h.run(50, 1)
+    o.run(50, 1)
+    assert_same(h, o, "after timeout")
