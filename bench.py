@@ -48,6 +48,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="regular3_n256_p64_r64")
+    ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per step (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
@@ -149,9 +150,13 @@ def run_ours(args, rank, world, local_rank):
         pbuild.build()
     barrier(world)
     prob = instances.workload(args.workload, 1 + rank)
+    if args.sweeps > 0:
+        prob.n_sweeps = args.sweeps
     attempts_step = prob.attempts_per_sweep * prob.n_sweeps
     degree = int(np.bincount(np.concatenate([prob.ei, prob.ej]), minlength=prob.n).max())
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library launches on it and the CUDA events are recorded on it
+    stream = torch.cuda.Stream()
+    assert stream.cuda_stream != 0
     ctx = pt.PT.from_problem(prob, stream=stream.cuda_stream)
     info = ctx.info
 
@@ -174,7 +179,8 @@ def run_ours(args, rank, world, local_rank):
     wall0 = time.perf_counter()
     times = []
     for _ in range(args.steps):
-        flush.fill_(1)
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
