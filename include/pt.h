@@ -74,7 +74,11 @@ typedef struct {
     int32_t test_withhold_rung; /* test hook, 0 = off: if r+1, the chain on rung r never
                                    publishes its swap mailbox, so its partner's wait runs out
                                    and the call fails with PT_ETIMEDOUT (no fault, no hang) */
-    int32_t reserved[4];
+    int32_t kernel_path;        /* 0 = auto, 1 = byte-wise, 2 = packed with inline random
+                                   words, 3 = packed with random words produced one sweep
+                                   ahead by dedicated warps (needs P % 8 == 0, degree <= 7) */
+    int32_t producer_threads;   /* path 3: threads producing random words (0 = auto) */
+    int32_t reserved[2];
 } pt_options;
 
 /* Statistics (Fig. 4 "gather statistics"; Sec. 5 accumulates in high precision).
@@ -101,6 +105,8 @@ typedef struct {
     int32_t n_levels;          /* dependency levels of one sweep (see pt_create) */
     int32_t threads_per_block;
     int32_t cooperative;       /* 1 if swaps run inside one launch */
+    int32_t kernel_path;       /* path chosen (see pt_options.kernel_path) */
+    int32_t producer_threads;  /* random-word producer threads per CTA (path 3) */
     int64_t device_bytes;      /* device memory held by the context */
     int64_t kernel_launches;   /* kernels this context has launched so far */
     int64_t h2d_bytes;         /* bytes copied host -> device so far */

@@ -281,16 +281,36 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     p.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
     p.key1 = (uint32_t)(seed >> 32);
 
-    // launch plan
+    // launch plan: the packed path needs P % 8 == 0 and a spare neighbour slot for h
     int max_smem = 0, n_sm = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device);
-    c->plan.dclass = dclass;
-    c->plan.smem_bytes = sweep_smem_bytes(p);
+    const int packed_dc = (dmax + 1 <= 4) ? 4 : ((dmax + 1 <= 8) ? 8 : 0);
+    const bool packed_ok = (P % 8 == 0) && packed_dc > 0;
+    const int want_path = opt ? opt->kernel_path : 0;
+    if (want_path < 0 || want_path > 3) {
+        free_ctx(c);
+        return create_fail(PT_EINVAL, "kernel_path must be 0..3");
+    }
+    if ((want_path == kPathPacked || want_path == kPathPackedInline) && !packed_ok) {
+        free_ctx(c);
+        return create_fail(PT_EINVAL, "the packed kernel needs P %% 8 == 0 and degree <= 7");
+    }
+    int path = want_path;
+    if (path == 0) {
+        path = kPathGeneric;
+        if (packed_ok) {
+            if (sweep_smem_bytes(p, kPathPacked, packed_dc) <= (size_t)max_smem) path = kPathPacked;
+            else if (sweep_smem_bytes(p, kPathPackedInline, packed_dc) <= (size_t)max_smem) path = kPathPackedInline;
+        }
+    }
+    c->plan.path = path;
+    c->plan.dclass = (path == kPathGeneric) ? dclass : packed_dc;
+    c->plan.smem_bytes = sweep_smem_bytes(p, path, c->plan.dclass);
     if ((long long)c->plan.smem_bytes > (long long)max_smem) {
         free_ctx(c);
         return create_fail(PT_EINVAL, "one chain needs %zu bytes of shared memory; the device allows %d",
-                           sweep_smem_bytes(p), max_smem);
+                           c->plan.smem_bytes, max_smem);
     }
     if (opt && opt->threads_per_block > 0) {
         if (opt->threads_per_block % 32 || opt->threads_per_block > 512) {
@@ -298,6 +318,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             return create_fail(PT_EINVAL, "threads_per_block must be a multiple of 32 <= 512");
         }
         c->plan.threads = opt->threads_per_block;
+    } else if (path == kPathPacked) {
+        c->plan.threads = 512;
     } else {
         // enough threads for the average level (units = items * padded groups per parity)
         int G = ((P / 2) + 3) / 4, Gp = 1;
@@ -306,6 +328,49 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         long long avg = (units + p.n_levels - 1) / p.n_levels;
         avg = ((avg + 31) / 32) * 32;
         c->plan.threads = (int)std::min<long long>(512, std::max<long long>(128, avg));
+    }
+    c->plan.n_consumer = c->plan.threads;
+    if (path == kPathPacked) {
+        int prod = (opt && opt->producer_threads > 0) ? opt->producer_threads : c->plan.threads / 4;
+        if (prod % 32 || prod >= c->plan.threads) {
+            free_ctx(c);
+            return create_fail(PT_EINVAL, "producer_threads must be a multiple of 32 below threads_per_block");
+        }
+        c->plan.n_consumer = c->plan.threads - prod;
+    }
+
+    // packed-path unit descriptors, one per schedule position q: row offset of site i,
+    // i | parity << 31, packed J bytes, then the row offsets of the neighbours; the slot
+    // after the last neighbour carries h against a constant row of +1 copies.
+    std::vector<uint32_t> desc;
+    if (path != kPathGeneric) {
+        const int DW = c->plan.dclass == 4 ? 8 : 16;
+        const uint32_t ones_row = (uint32_t)(((size_t)N * P + 15) & ~(size_t)15);
+        desc.assign((size_t)2 * N * DW, 0u);
+        for (size_t qpos = 0; qpos < items.size(); ++qpos) {
+            const int i = (int)(items[qpos] >> 1);
+            const uint32_t par = items[qpos] & 1u;
+            uint32_t* d = &desc[qpos * DW];
+            d[0] = (uint32_t)i * (uint32_t)P;
+            d[1] = (uint32_t)i | (par << 31);
+            uint32_t jp[2] = {0u, 0u};
+            uint32_t nr[8];
+            for (int s8 = 0; s8 < c->plan.dclass; ++s8) {
+                int J = 0;
+                uint32_t r = ones_row;
+                if (s8 < (int)adj[i].size()) {
+                    J = adjJ[i][s8];
+                    r = (uint32_t)adj[i][s8] * (uint32_t)P;
+                } else if (s8 == (int)adj[i].size()) {
+                    J = inst->h[i];
+                }
+                nr[s8] = r;
+                jp[s8 / 4] |= (uint32_t)(uint8_t)(int8_t)J << (8 * (s8 % 4));
+            }
+            d[2] = jp[0];
+            d[3] = jp[1];
+            for (int s8 = 0; s8 < c->plan.dclass; ++s8) d[4 + s8] = nr[s8];
+        }
     }
 
     // overflow guard: |E| <= P * (sum|J| + sum|h|), |M| <= N*P; sum of squares stays in int64
@@ -322,7 +387,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
 
     // device memory
     cudaError_t e = cudaSuccess;
-    uint32_t *d_nbr, *d_items, *d_thr;
+    uint32_t *d_nbr, *d_items, *d_thr, *d_desc;
     int8_t* d_h;
     int32_t* d_loff;
     double* d_coef;
@@ -333,6 +398,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         (e = dev_alloc(c, &d_items, items.size())) != cudaSuccess ||
         (e = dev_alloc(c, &d_loff, level_off.size())) != cudaSuccess ||
         (e = dev_alloc(c, &d_thr, c->thr.size())) != cudaSuccess ||
+        (e = dev_alloc(c, &d_desc, desc.size())) != cudaSuccess ||
         (e = dev_alloc(c, &d_coef, c->coef.size())) != cudaSuccess ||
         (e = dev_alloc(c, &p.spins, (size_t)R * p.slot_stride)) != cudaSuccess ||
         (e = dev_alloc(c, &p.E, (size_t)R)) != cudaSuccess || (e = dev_alloc(c, &p.M, (size_t)R)) != cudaSuccess ||
@@ -352,6 +418,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     p.items = d_items;
     p.level_off = d_loff;
     p.thr = d_thr;
+    p.desc = d_desc;
     p.coef = d_coef;
 
     cudaStream_t s = c->stream;
@@ -369,6 +436,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     CREATE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s));
     CREATE_CUDA(cudaMemcpyAsync(d_loff, level_off.data(), level_off.size() * 4, cudaMemcpyHostToDevice, s));
     CREATE_CUDA(cudaMemcpyAsync(d_thr, c->thr.data(), c->thr.size() * 4, cudaMemcpyHostToDevice, s));
+    if (!desc.empty())
+        CREATE_CUDA(cudaMemcpyAsync(d_desc, desc.data(), desc.size() * 4, cudaMemcpyHostToDevice, s));
     CREATE_CUDA(cudaMemcpyAsync(d_coef, c->coef.data(), c->coef.size() * 8, cudaMemcpyHostToDevice, s));
     CREATE_CUDA(cudaMemsetAsync(p.spins, 0, (size_t)R * p.slot_stride, s));
     CREATE_CUDA(cudaMemsetAsync(p.acc, 0, (size_t)R * kAccCount * 8, s));
@@ -379,7 +448,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     CREATE_CUDA(launch_energy(p, s));
     c->launches += 2;
     c->h2d_bytes += (int64_t)(nbr.size() * 4 + (size_t)N + items.size() * 4 + level_off.size() * 4 +
-                              c->thr.size() * 4 + c->coef.size() * 8);
+                              c->thr.size() * 4 + c->coef.size() * 8 + desc.size() * 4);
     CREATE_CUDA(prepare_sweep_kernel(c->plan));
     CREATE_CUDA(cudaStreamSynchronize(s));
 #undef CREATE_CUDA
@@ -414,8 +483,8 @@ static int enqueue_sweeps(pt_ctx* c, long long n, int sps) {
         if (sps > 0) chunk = std::min<long long>(chunk, (long long)c->max_passes * sps);
         chunk = std::min<long long>(chunk, 1ll << 30);
         const int passes = sps > 0 ? (int)(chunk / sps) : 0;
-        CUDA_OR_FAIL(c, launch_sweeps(c->dp, c->plan, c->t, c->q, (int)chunk, sps, passes, c->timeout_ns,
-                                      sps > 0, c->stream));
+        CUDA_OR_FAIL(c, launch_sweeps(c->dp, c->plan, c->t, c->q, (int)chunk, sps, c->timeout_ns, sps > 0,
+                                      c->stream));
         c->launches += 1;
         c->t += chunk;
         c->q += passes;
@@ -565,6 +634,8 @@ extern "C" int pt_get_info(const pt_ctx* c, pt_info* o) {
     o->n_levels = c->dp.n_levels;
     o->threads_per_block = c->plan.threads;
     o->cooperative = c->cooperative ? 1 : 0;
+    o->kernel_path = c->plan.path;
+    o->producer_threads = c->plan.threads - c->plan.n_consumer;
     o->device_bytes = c->device_bytes;
     o->kernel_launches = c->launches;
     o->h2d_bytes = c->h2d_bytes;

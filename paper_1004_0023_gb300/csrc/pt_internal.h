@@ -31,6 +31,7 @@ struct DevProblem {
     const int8_t* h;           // [N]
     const uint32_t* items;     // [2N] (i << 1) | parity, grouped by dependency level
     const int32_t* level_off;  // [n_levels + 1]
+    const uint32_t* desc;      // [2N][8 or 16] packed-path unit descriptors (schedule order)
     const uint32_t* thr;       // [R][nL*3] Metropolis thresholds
     const double* coef;        // [2(R-1)] a_r then c_r
     // state
@@ -43,27 +44,34 @@ struct DevProblem {
     unsigned long long* swap_stats;  // [pair][2] attempts, accepts
     Mailbox* mbox;             // [max_passes][R]
     int* status;               // 0 or a PT_E* code set by a kernel
-    int N, P, R, Lmax, nL3, dmax, n_levels;
+    int N, P, R, Lmax, nL3, n_levels;
+    int dmax;                  // row stride of `nbr` (4, 8 or 32)
     int slot_stride;           // bytes between slots in `spins` (multiple of 16)
     int withhold_rung;         // test hook: rung whose chain never publishes (-1 = off)
     uint32_t key0, key1;
 };
 
+// Sweep kernel variants: byte-wise (any shape), packed with Philox inline, packed with the
+// random words produced one sweep ahead by dedicated warps.
+enum { kPathGeneric = 1, kPathPackedInline = 2, kPathPacked = 3 };
+
 struct LaunchPlan {
+    int path;            // kPath*
     int threads;         // threads per CTA
-    int dclass;          // 4, 8 or 32: padded neighbour count the kernel is built for
+    int n_consumer;      // threads running the levels (the rest produce random words)
+    int dclass;          // padded neighbour slots the kernel is built for
     size_t smem_bytes;   // dynamic shared memory per CTA
 };
 
-// Sizes of the dynamic shared-memory carve-up of the sweep kernel.
-size_t sweep_smem_bytes(const DevProblem& p);
+// Sizes of the dynamic shared-memory carve-up of the sweep kernel for a path.
+size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass);
 
 // Kernel launchers (pt_kernels.cu). Each returns a cudaError_t from the launch.
 cudaError_t launch_init(const DevProblem& p, cudaStream_t s);
 cudaError_t launch_energy(const DevProblem& p, cudaStream_t s);
 cudaError_t launch_sweeps(const DevProblem& p, const LaunchPlan& plan, long long t0,
-                          long long q0, int n_sweeps, int sweeps_per_swap, int n_passes,
-                          long long timeout_ns, bool cooperative, cudaStream_t s);
+                          long long q0, int n_sweeps, int sweeps_per_swap, long long timeout_ns,
+                          bool cooperative, cudaStream_t s);
 cudaError_t launch_swap(const DevProblem& p, long long q, cudaStream_t s);
 cudaError_t launch_gather_state(const DevProblem& p, int8_t* out, cudaStream_t s);
 cudaError_t launch_scatter_state(const DevProblem& p, const int8_t* in, cudaStream_t s);

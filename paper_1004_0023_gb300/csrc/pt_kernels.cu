@@ -111,15 +111,24 @@ __device__ __forceinline__ long long ld_relaxed_s64(const long long* p) {
 __device__ __forceinline__ void st_relaxed_s64(long long* p, long long v) {
     asm volatile("st.relaxed.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// prmt.b32 in its generic mode: a selector nibble with its top bit set replicates the
+// sign of the selected byte (used to sign-extend packed int8 spins).
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// ------------------------------------------------------------------------- smem layout
-struct SmemLayout {
+// ------------------------------------------------------------------------- smem layouts
+__host__ __device__ inline size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Byte-wise path (any even P, any degree up to 32).
+struct GenericLayout {
     size_t spins, nbr, h, items, loff, thr, red, ctl, total;
-    __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
-    __host__ __device__ SmemLayout(int N, int P, int dmax, int n_levels, int nL3) {
+    __host__ __device__ GenericLayout(int N, int P, int dmax, int n_levels, int nL3) {
         size_t o = 0;
         spins = o; o += up16((size_t)N * P);
         nbr = o;   o += up16((size_t)N * dmax * 4);
@@ -133,22 +142,107 @@ struct SmemLayout {
     }
 };
 
-size_t sweep_smem_bytes(const DevProblem& p) {
-    return SmemLayout(p.N, p.P, p.dmax, p.n_levels, p.nL3).total;
+// Packed path (P % 8 == 0, degree + 1 <= 8): spins, one row of +1 copies (the field's h
+// slot points at it), per-position unit descriptors, the schedule (read by the random-word
+// producer), level offsets, the threshold row, reduction scratch, control words and, when
+// the random words are produced ahead, two buffers of one sweep's words each.
+struct FastLayout {
+    size_t spins, ones, desc, items, loff, thr, red, ctl, rbuf, total;
+    __host__ __device__ FastLayout(int N, int P, int dc, int n_levels, int nL3, bool pre) {
+        size_t o = 0;
+        spins = o; o += up16((size_t)N * P);
+        ones = o;  o += up16((size_t)P);
+        desc = o;  o += (size_t)2 * N * (dc == 4 ? 32 : 64);
+        items = o; o += up16((size_t)2 * N * 4);
+        loff = o;  o += up16((size_t)(n_levels + 1) * 4);
+        thr = o;   o += up16((size_t)nL3 * 4);
+        red = o;   o += 32 * 3 * 8;
+        ctl = o;   o += 16;
+        rbuf = o;
+        if (pre) o += (size_t)2 * (2 * N) * (P / 8) * 16;
+        total = o;
+    }
+};
+
+size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass) {
+    if (path == kPathGeneric) return GenericLayout(p.N, p.P, p.dmax, p.n_levels, p.nL3).total;
+    return FastLayout(p.N, p.P, dclass, p.n_levels, p.nL3, path == kPathPacked).total;
 }
 
-// ------------------------------------------------------------------------- sweep kernel
-// One CTA per chain (slot). n_sweeps sweeps; when sweeps_per_swap > 0, a swap pass after
-// every sweeps_per_swap-th sweep (cooperative launch only).
+__device__ __forceinline__ void named_barrier(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// ------------------------------------------------------------------------- end of a sweep
+// Thread 0 of a chain's CTA, after the sweep's changes are reduced: update E and M, add the
+// statistics of the rung the chain sits on, and run the chain's side of swap pass q when
+// one follows this sweep. Returns the chain's rung for the next sweep; sets *abort when the
+// partner's mailbox never arrived within the time limit.
+__device__ int end_of_sweep(const DevProblem& p, int slot, int rung, long long& E, long long& M, long long dE,
+                            long long dM, long long nflip, int s, long long q0, int sweeps_per_swap,
+                            long long timeout_ns, const PhiloxKey& key, int* abort) {
+    E += dE;
+    M += dM;
+    unsigned long long* a = p.acc + (size_t)rung * kAccCount;
+    atomicAdd(a + kAccN, 1ull);
+    atomicAdd(a + kAccE, (unsigned long long)E);
+    atomicAdd(a + kAccE2, (unsigned long long)(E * E));
+    atomicAdd(a + kAccM, (unsigned long long)M);
+    atomicAdd(a + kAccM2, (unsigned long long)(M * M));
+    atomicAdd(a + kAccFlip, (unsigned long long)nflip);
+    *abort = 0;
+    if (sweeps_per_swap <= 0 || (s + 1) % sweeps_per_swap != 0) return rung;
+    const int R = p.R;
+    const int pass = (s + 1) / sweeps_per_swap - 1;
+    const long long q = q0 + pass;
+    Mailbox* mb = p.mbox + (size_t)pass * R;
+    if (rung != p.withhold_rung) {
+        st_relaxed_s64(&mb[rung].E, E);
+        st_relaxed_s64(&mb[rung].M, M);
+        __threadfence();
+        st_release_u64(&mb[rung].tag, (unsigned long long)(q + 1));
+    }
+    int rl, partner;
+    if ((rung & 1) == (int)(q & 1)) {
+        rl = rung;
+        partner = rung + 1;
+    } else {
+        rl = rung - 1;
+        partner = rung - 1;
+    }
+    if (rl < 0 || rl + 1 >= R) return rung;
+    const unsigned long long start = globaltimer_ns();
+    while (ld_acquire_u64(&mb[partner].tag) != (unsigned long long)(q + 1)) {
+        if ((long long)(globaltimer_ns() - start) > timeout_ns) {
+            atomicCAS(p.status, 0, PT_ETIMEDOUT);
+            *abort = 1;
+            return rung;
+        }
+    }
+    const long long pE = ld_relaxed_s64(&mb[partner].E);
+    const long long pM = ld_relaxed_s64(&mb[partner].M);
+    const bool lower = (rung == rl);
+    const bool acc = swap_accept(lower ? E : pE, lower ? pE : E, lower ? M : pM, lower ? pM : M, p.coef[rl],
+                                 p.coef[(R - 1) + rl], (uint32_t)q, (uint32_t)rl, key);
+    if (lower) {
+        atomicAdd(p.swap_stats + 2 * rl, 1ull);
+        if (acc) atomicAdd(p.swap_stats + 2 * rl + 1, 1ull);
+    }
+    return acc ? partner : rung;
+}
+
+// ------------------------------------------------------------------------- generic sweep
+// One CTA per chain (slot); byte-wise spins, Philox inline in each 4-copy unit. Used when
+// P is not a multiple of 8 or a site has more than 7 neighbours.
 template <int DCLASS>
 __global__ void __launch_bounds__(512, 1)
 sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
-             int n_passes, long long timeout_ns) {
+             long long timeout_ns, int n_consumer) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int N = p.N, P = p.P, R = p.R;
+    const int N = p.N, P = p.P;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int slot = blockIdx.x;
-    const SmemLayout L(N, P, DCLASS, p.n_levels, p.nL3);
+    const GenericLayout L(N, P, DCLASS, p.n_levels, p.nL3);
     int8_t* sp = reinterpret_cast<int8_t*>(smem + L.spins);
     uint32_t* s_nbr = reinterpret_cast<uint32_t*>(smem + L.nbr);
     int8_t* s_h = reinterpret_cast<int8_t*>(smem + L.h);
@@ -157,12 +251,12 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
     uint32_t* s_thr = reinterpret_cast<uint32_t*>(smem + L.thr);
     long long* s_red = reinterpret_cast<long long*>(smem + L.red);
     int* s_ctl = reinterpret_cast<int*>(smem + L.ctl);
+    (void)n_consumer;
 
-    // ---- load the chain and the instance into shared memory
     {
         const int4* src = reinterpret_cast<const int4*>(p.spins + (size_t)slot * p.slot_stride);
         int4* dst = reinterpret_cast<int4*>(sp);
-        const int n16 = (int)(SmemLayout::up16((size_t)N * P) / 16);
+        const int n16 = (int)(up16((size_t)N * P) / 16);
         for (int x = tid; x < n16; x += nt) dst[x] = src[x];
         for (int x = tid; x < N * DCLASS; x += nt) s_nbr[x] = p.nbr[x];
         for (int x = tid; x < N; x += nt) s_h[x] = p.h[x];
@@ -231,7 +325,6 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
             }
             __syncthreads();
         }
-        // ---- per-chain reduction of the sweep's energy / Trotter-term changes and flips
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             dE += __shfl_xor_sync(0xFFFFFFFFu, dE, o);
@@ -251,63 +344,9 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
                 sM += s_red[w * 3 + 1];
                 sF += s_red[w * 3 + 2];
             }
-            E += sE;
-            M += sM;
-            // statistics after every sweep, attributed to the rung the chain sits on
-            unsigned long long* a = p.acc + (size_t)rung * kAccCount;
-            atomicAdd(a + kAccN, 1ull);
-            atomicAdd(a + kAccE, (unsigned long long)E);
-            atomicAdd(a + kAccE2, (unsigned long long)(E * E));
-            atomicAdd(a + kAccM, (unsigned long long)M);
-            atomicAdd(a + kAccM2, (unsigned long long)(M * M));
-            atomicAdd(a + kAccFlip, (unsigned long long)sF);
-
             int abort_flag = 0;
-            const int new_rung_base = rung;
-            int new_rung = new_rung_base;
-            if (sweeps_per_swap > 0 && (s + 1) % sweeps_per_swap == 0) {
-                const int pass = (s + 1) / sweeps_per_swap - 1;
-                const long long q = q0 + pass;
-                Mailbox* mb = p.mbox + (size_t)pass * R;
-                if (rung != p.withhold_rung) {
-                    st_relaxed_s64(&mb[rung].E, E);
-                    st_relaxed_s64(&mb[rung].M, M);
-                    __threadfence();
-                    st_release_u64(&mb[rung].tag, (unsigned long long)(q + 1));
-                }
-                int rl, partner;
-                if ((rung & 1) == (int)(q & 1)) {
-                    rl = rung;
-                    partner = rung + 1;
-                } else {
-                    rl = rung - 1;
-                    partner = rung - 1;
-                }
-                if (rl >= 0 && rl + 1 < R) {
-                    const unsigned long long start = globaltimer_ns();
-                    while (ld_acquire_u64(&mb[partner].tag) != (unsigned long long)(q + 1)) {
-                        if ((long long)(globaltimer_ns() - start) > timeout_ns) {
-                            abort_flag = 1;
-                            atomicCAS(p.status, 0, PT_ETIMEDOUT);
-                            break;
-                        }
-                    }
-                    if (!abort_flag) {
-                        const long long pE = ld_relaxed_s64(&mb[partner].E);
-                        const long long pM = ld_relaxed_s64(&mb[partner].M);
-                        const bool lower = (rung == rl);
-                        const bool acc = swap_accept(lower ? E : pE, lower ? pE : E, lower ? M : pM,
-                                                     lower ? pM : M, p.coef[rl], p.coef[(R - 1) + rl],
-                                                     (uint32_t)q, (uint32_t)rl, key);
-                        if (lower) {
-                            atomicAdd(p.swap_stats + 2 * rl, 1ull);
-                            if (acc) atomicAdd(p.swap_stats + 2 * rl + 1, 1ull);
-                        }
-                        if (acc) new_rung = partner;
-                    }
-                }
-            }
-            s_ctl[0] = new_rung;
+            s_ctl[0] = end_of_sweep(p, slot, rung, E, M, sE, sM, sF, s, q0, sweeps_per_swap, timeout_ns, key,
+                                    &abort_flag);
             s_ctl[1] = abort_flag;
         }
         __syncthreads();
@@ -319,13 +358,243 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
         }
         __syncthreads();
     }
-    (void)n_passes;
 
-    // ---- write the chain back
     {
         int4* dst = reinterpret_cast<int4*>(p.spins + (size_t)slot * p.slot_stride);
         const int4* src = reinterpret_cast<const int4*>(sp);
-        const int n16 = (int)(SmemLayout::up16((size_t)N * P) / 16);
+        const int n16 = (int)(up16((size_t)N * P) / 16);
+        for (int x = tid; x < n16; x += nt) dst[x] = src[x];
+    }
+    if (tid == 0) {
+        p.E[slot] = E;
+        p.M[slot] = M;
+        p.rung_of_slot[slot] = rung;
+        p.slot_of_rung[rung] = slot;
+    }
+}
+
+// ------------------------------------------------------------------------- packed sweep
+// Random words of one sweep for the producer warps: word w of philox((t, i, slot,
+// p<<24 | g)) goes with copy 8g + p + 2w of site i (the same counter the update would use).
+__device__ __forceinline__ void produce_words(uint4* buf, uint32_t t, const uint32_t* s_items, int n_items, int G,
+                                              int lg, int gmask, int ptid, int np, uint32_t slot,
+                                              const PhiloxKey& key) {
+    const int total = n_items << lg;
+    for (int x = ptid; x < total; x += np) {
+        const int g = x & gmask;
+        if (g >= G) continue;
+        const int q = x >> lg;
+        const uint32_t it = s_items[q];
+        buf[q * G + g] = philox(make_uint4(t, it >> 1, slot, ((it & 1u) << 24) | (uint32_t)g), key);
+    }
+}
+
+// One 4-copy unit of the packed path: copies k = 8g + par + 2w (w = 0..3) of site i.
+// Each neighbour row contributes one 8-byte load; the field of the four copies comes from
+// a 4x4 byte transpose and dp4a (the site's h rides in a spare neighbour slot whose spins
+// are the constant +1 row); the Trotter column m/2+1 = 2 - [left differs] - [right differs]
+// is formed for all four copies at once from byte XORs.
+template <int DC, bool PRE>
+__device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* desc, const uint4* rb, int q, int g, int G,
+                                            int P, uint32_t t, uint32_t slot, const PhiloxKey& key,
+                                            const uint32_t* thr_c, int& sumL, int& sumC, int& nflip) {
+    const uint4 d0 = *reinterpret_cast<const uint4*>(desc);
+    const uint32_t row = d0.x;
+    const uint32_t par = d0.y >> 31;
+    const uint32_t c = 8u * (uint32_t)g;
+    uint32_t nrow[DC];
+    uint32_t jpack[DC / 4];
+    {
+        const uint4 d1 = *reinterpret_cast<const uint4*>(desc + 4);
+        nrow[0] = d1.x;
+        nrow[1] = d1.y;
+        nrow[2] = d1.z;
+        nrow[3] = d1.w;
+        jpack[0] = d0.z;
+        if (DC == 8) {
+            const uint4 d2 = *reinterpret_cast<const uint4*>(desc + 8);
+            nrow[DC > 4 ? 4 : 0] = d2.x;
+            nrow[DC > 5 ? 5 : 0] = d2.y;
+            nrow[DC > 6 ? 6 : 0] = d2.z;
+            nrow[DC > 7 ? 7 : 0] = d2.w;
+            jpack[DC > 4 ? 1 : 0] = d0.w;
+        }
+    }
+    const uint2 own = *reinterpret_cast<const uint2*>(sp + row + c);
+    const uint32_t el = (uint8_t)sp[row + (c == 0 ? (uint32_t)P - 1 : c - 1)];
+    const uint32_t er = (uint8_t)sp[row + (c + 8 == (uint32_t)P ? 0u : c + 8)];
+    uint2 nb[DC];
+#pragma unroll
+    for (int d = 0; d < DC; ++d) nb[d] = *reinterpret_cast<const uint2*>(sp + nrow[d] + c);
+    uint4 r4;
+    if (PRE) {
+        r4 = rb[q * G + g];
+    } else {
+        r4 = philox(make_uint4(t, d0.y & 0x7FFFFFFFu, slot, (par << 24) | (uint32_t)g), key);
+    }
+    const uint32_t u[4] = {r4.x, r4.y, r4.z, r4.w};
+
+    const uint32_t selS = par ? 0x7531u : 0x6420u;
+    const uint32_t S = __byte_perm(own.x, own.y, selS);
+    uint32_t Rn = __byte_perm(own.x, own.y, par ? 0x0642u : 0x7531u);
+    Rn = par ? __byte_perm(Rn, er, 0x4210u) : Rn;
+    uint32_t Ln = __byte_perm(own.x, own.y, par ? 0x6420u : 0x5310u);
+    Ln = par ? Ln : __byte_perm(Ln, el, 0x3214u);
+    const uint32_t X = (S ^ Ln) & 0x02020202u;
+    const uint32_t Y = (S ^ Rn) & 0x02020202u;
+    const uint32_t Z = 0x02020202u - ((X + Y) >> 1);
+
+    int f[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int b = 0; b < DC / 4; ++b) {
+        const uint32_t a0 = __byte_perm(nb[4 * b + 0].x, nb[4 * b + 0].y, selS);
+        const uint32_t a1 = __byte_perm(nb[4 * b + 1].x, nb[4 * b + 1].y, selS);
+        const uint32_t a2 = __byte_perm(nb[4 * b + 2].x, nb[4 * b + 2].y, selS);
+        const uint32_t a3 = __byte_perm(nb[4 * b + 3].x, nb[4 * b + 3].y, selS);
+        const uint32_t t0 = __byte_perm(a0, a1, 0x5140u), t1 = __byte_perm(a0, a1, 0x7362u);
+        const uint32_t t2 = __byte_perm(a2, a3, 0x5140u), t3 = __byte_perm(a2, a3, 0x7362u);
+        f[0] = __dp4a((int)__byte_perm(t0, t2, 0x5410u), (int)jpack[b], f[0]);
+        f[1] = __dp4a((int)__byte_perm(t0, t2, 0x7632u), (int)jpack[b], f[1]);
+        f[2] = __dp4a((int)__byte_perm(t1, t3, 0x5410u), (int)jpack[b], f[2]);
+        f[3] = __dp4a((int)__byte_perm(t1, t3, 0x7632u), (int)jpack[b], f[3]);
+    }
+    uint32_t F = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int sw = (int)prmt(S, 0u, 0x8880u | (0x1110u * (uint32_t)w) | (uint32_t)w);
+        const int Lw = sw * f[w];
+        const int col = (int)__byte_perm(Z, 0u, 0x4440u | (uint32_t)w);
+        const uint32_t th = thr_c[3 * Lw + col];
+        if (u[w] < th || th == 0xFFFFFFFFu) {
+            F |= 0xFEu << (8 * w);
+            sumL += Lw;
+            sumC += col;
+            nflip += 1;
+        }
+    }
+    if (F) {
+        const uint32_t lo = __byte_perm(F, 0u, par ? 0x1404u : 0x4140u);
+        const uint32_t hi = __byte_perm(F, 0u, par ? 0x3424u : 0x4342u);
+        *reinterpret_cast<uint2*>(sp + row + c) = make_uint2(own.x ^ lo, own.y ^ hi);
+    }
+}
+
+// One CTA per chain with the chain, the unit descriptors and the threshold row in shared
+// memory. PRE: the last (blockDim - n_consumer) threads are producer warps that write the
+// random words of sweep s+1 into one shared buffer while the consumer warps run the levels
+// of sweep s out of the other; consumers synchronise levels on named barrier 1 and both
+// groups meet once per sweep.
+template <int DC, bool PRE>
+__global__ void __launch_bounds__(512, 1)
+sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
+                    long long timeout_ns, int n_consumer) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = p.N, P = p.P;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int slot = blockIdx.x;
+    const FastLayout L(N, P, DC, p.n_levels, p.nL3, PRE);
+    int8_t* sp = reinterpret_cast<int8_t*>(smem + L.spins);
+    uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem + L.desc);
+    uint32_t* s_items = reinterpret_cast<uint32_t*>(smem + L.items);
+    int32_t* s_loff = reinterpret_cast<int32_t*>(smem + L.loff);
+    uint32_t* s_thr = reinterpret_cast<uint32_t*>(smem + L.thr);
+    long long* s_red = reinterpret_cast<long long*>(smem + L.red);
+    int* s_ctl = reinterpret_cast<int*>(smem + L.ctl);
+    uint4* rbuf = reinterpret_cast<uint4*>(smem + L.rbuf);
+    const int NC = PRE ? n_consumer : nt;
+    const bool consumer = tid < NC;
+    const int DW = (DC == 4) ? 8 : 16;
+
+    {
+        const int4* src = reinterpret_cast<const int4*>(p.spins + (size_t)slot * p.slot_stride);
+        int4* dst = reinterpret_cast<int4*>(sp);
+        const int n16 = (int)(up16((size_t)N * P) / 16);
+        for (int x = tid; x < n16; x += nt) dst[x] = src[x];
+        int8_t* ones = reinterpret_cast<int8_t*>(smem + L.ones);
+        for (int x = tid; x < P; x += nt) ones[x] = 1;
+        const int4* dsrc = reinterpret_cast<const int4*>(p.desc);
+        int4* ddst = reinterpret_cast<int4*>(s_desc);
+        for (int x = tid; x < 2 * N * DW / 4; x += nt) ddst[x] = dsrc[x];
+        for (int x = tid; x < 2 * N; x += nt) s_items[x] = p.items[x];
+        for (int x = tid; x <= p.n_levels; x += nt) s_loff[x] = p.level_off[x];
+    }
+    int rung = p.rung_of_slot[slot];
+    for (int x = tid; x < p.nL3; x += nt) s_thr[x] = p.thr[(size_t)rung * p.nL3 + x];
+    long long E = p.E[slot], M = p.M[slot];  // meaningful in thread 0 only
+
+    const PhiloxKey key = philox_schedule(p.key0, p.key1);
+    const int G = P >> 3;  // 8-copy chunks per row = 4-copy units per parity
+    int lg = 0;
+    while ((1 << lg) < G) ++lg;
+    const int gmask = (1 << lg) - 1;
+    const uint32_t* thr_c = s_thr + 3 * p.Lmax;
+    const int n_items = 2 * N;
+    const int lane = tid & 31, warp = tid >> 5;
+    __syncthreads();
+    if (PRE && !consumer)
+        produce_words(rbuf, (uint32_t)t0, s_items, n_items, G, lg, gmask, tid - NC, nt - NC, (uint32_t)slot, key);
+    if (PRE) __syncthreads();
+
+    for (int s = 0; s < n_sweeps; ++s) {
+        const uint32_t t = (uint32_t)(t0 + s);
+        if (consumer) {
+            const uint4* rb = rbuf + (size_t)(s & 1) * n_items * G;
+            int sumL = 0, sumC = 0, nf = 0;
+            for (int lev = 0; lev < p.n_levels; ++lev) {
+                const int base = s_loff[lev];
+                const int units = (s_loff[lev + 1] - base) << lg;
+                for (int u = tid; u < units; u += NC) {
+                    const int g = u & gmask;
+                    if (g >= G) continue;
+                    const int q = base + (u >> lg);
+                    packed_unit<DC, PRE>(sp, s_desc + (size_t)q * DW, rb, q, g, G, P, t, (uint32_t)slot, key, thr_c,
+                                         sumL, sumC, nf);
+                }
+                if (PRE) named_barrier(1, NC); else __syncthreads();
+            }
+            int dE = -2 * sumL, dM = -4 * (sumC - nf);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dE += __shfl_xor_sync(0xFFFFFFFFu, dE, o);
+                dM += __shfl_xor_sync(0xFFFFFFFFu, dM, o);
+                nf += __shfl_xor_sync(0xFFFFFFFFu, nf, o);
+            }
+            if (lane == 0) {
+                s_red[warp * 3 + 0] = dE;
+                s_red[warp * 3 + 1] = dM;
+                s_red[warp * 3 + 2] = nf;
+            }
+            if (PRE) named_barrier(1, NC); else __syncthreads();
+            if (tid == 0) {
+                long long sE = 0, sM = 0, sF = 0;
+                for (int w = 0; w < NC / 32; ++w) {
+                    sE += s_red[w * 3 + 0];
+                    sM += s_red[w * 3 + 1];
+                    sF += s_red[w * 3 + 2];
+                }
+                int abort_flag = 0;
+                s_ctl[2 * (s & 1)] = end_of_sweep(p, slot, rung, E, M, sE, sM, sF, s, q0, sweeps_per_swap,
+                                                  timeout_ns, key, &abort_flag);
+                s_ctl[2 * (s & 1) + 1] = abort_flag;
+            }
+            if (PRE) named_barrier(1, NC); else __syncthreads();
+            const int nr = s_ctl[2 * (s & 1)];
+            if (!s_ctl[2 * (s & 1) + 1] && nr != rung) {
+                rung = nr;
+                for (int x = tid; x < p.nL3; x += NC) s_thr[x] = p.thr[(size_t)rung * p.nL3 + x];
+            }
+        } else if (s + 1 < n_sweeps) {
+            produce_words(rbuf + (size_t)((s + 1) & 1) * n_items * G, t + 1u, s_items, n_items, G, lg, gmask,
+                          tid - NC, nt - NC, (uint32_t)slot, key);
+        }
+        __syncthreads();
+        if (s_ctl[2 * (s & 1) + 1]) return;  // a partner never arrived; status holds PT_ETIMEDOUT
+    }
+
+    {
+        int4* dst = reinterpret_cast<int4*>(p.spins + (size_t)slot * p.slot_stride);
+        const int4* src = reinterpret_cast<const int4*>(sp);
+        const int n16 = (int)(up16((size_t)N * P) / 16);
         for (int x = tid; x < n16; x += nt) dst[x] = src[x];
     }
     if (tid == 0) {
@@ -433,12 +702,17 @@ __global__ void scatter_kernel(DevProblem p, const int8_t* in) {
 }
 
 // ------------------------------------------------------------------------- launchers
-static const void* sweep_fn(int dclass) {
-    switch (dclass) {
-        case 4: return (const void*)sweep_kernel<4>;
-        case 8: return (const void*)sweep_kernel<8>;
-        default: return (const void*)sweep_kernel<32>;
+static const void* sweep_fn(const LaunchPlan& plan) {
+    if (plan.path == kPathGeneric) {
+        switch (plan.dclass) {
+            case 4: return (const void*)sweep_kernel<4>;
+            case 8: return (const void*)sweep_kernel<8>;
+            default: return (const void*)sweep_kernel<32>;
+        }
     }
+    const bool pre = plan.path == kPathPacked;
+    if (plan.dclass == 4) return pre ? (const void*)sweep_packed_kernel<4, true> : (const void*)sweep_packed_kernel<4, false>;
+    return pre ? (const void*)sweep_packed_kernel<8, true> : (const void*)sweep_packed_kernel<8, false>;
 }
 
 // The dynamic shared-memory limit is a per-function attribute shared by every context, so
@@ -448,21 +722,22 @@ cudaError_t prepare_sweep_kernel(const LaunchPlan& plan) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sweep_fn(plan.dclass), cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    return cudaFuncSetAttribute(sweep_fn(plan), cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
 }
 
 cudaError_t sweep_kernel_occupancy(const DevProblem& p, const LaunchPlan& plan, int* blocks_per_sm) {
     (void)p;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep_fn(plan.dclass), plan.threads,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep_fn(plan), plan.threads,
                                                          plan.smem_bytes);
 }
 
 cudaError_t launch_sweeps(const DevProblem& p, const LaunchPlan& plan, long long t0, long long q0,
-                          int n_sweeps, int sweeps_per_swap, int n_passes, long long timeout_ns,
-                          bool cooperative, cudaStream_t s) {
+                          int n_sweeps, int sweeps_per_swap, long long timeout_ns, bool cooperative,
+                          cudaStream_t s) {
     DevProblem pp = p;
-    void* args[] = {&pp, &t0, &q0, &n_sweeps, &sweeps_per_swap, &n_passes, &timeout_ns};
-    const void* fn = sweep_fn(plan.dclass);
+    int n_consumer = plan.n_consumer;
+    void* args[] = {&pp, &t0, &q0, &n_sweeps, &sweeps_per_swap, &timeout_ns, &n_consumer};
+    const void* fn = sweep_fn(plan);
     if (cooperative)
         return cudaLaunchCooperativeKernel(fn, dim3(p.R), dim3(plan.threads), args, plan.smem_bytes, s);
     return cudaLaunchKernel(fn, dim3(p.R), dim3(plan.threads), args, plan.smem_bytes, s);

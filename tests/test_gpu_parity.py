@@ -31,6 +31,7 @@ def assert_same(g, o, where=""):
 
 def both(prob, threads=THREADS, **kw):
     okw = {k: v for k, v in kw.items() if k in ("flip_thr", "swap_coef")}
+    # (the oracle takes no layout options)
     return pt.PT.from_problem(prob, **kw), Oracle.from_problem(prob, threads=threads, **okw)
 
 
@@ -47,6 +48,16 @@ TINY = {
     "prism_p10_r4": instances.tiny_problem(6, [(0, 1), (1, 2), (2, 0), (3, 4), (4, 5), (5, 3), (0, 3), (1, 4), (2, 5)],
                                            [1, -2, 1, 2, -1, -1, 1, -2, 2], [1, 0, -1, 0, 1, 0], 10,
                                            [0.6, 0.8, 1.1, 1.5], [0.4, 0.8, 1.4, 2.2], seed=14),
+    # packed path, 4 neighbour slots (degree 3 + h)
+    "prism_p8_r3": instances.tiny_problem(6, [(0, 1), (1, 2), (2, 0), (3, 4), (4, 5), (5, 3), (0, 3), (1, 4), (2, 5)],
+                                          [2, -1, 1, -2, 1, 1, -1, 2, -2], [0, 1, 0, -1, 1, 0], 8,
+                                          [0.5, 0.9, 1.6], [0.6, 1.0, 1.8], seed=16),
+    # packed path, 8 neighbour slots (degree 7 + h), P=16
+    "complete8_p16_r4": instances.tiny_problem(
+        8, [(i, j) for i in range(8) for j in range(i + 1, 8)],
+        [((i * 5 + j * 3) % 5) - 2 or 2 for i in range(8) for j in range(i + 1, 8)],
+        [1, 0, -1, 2, 0, -2, 1, 0], 16, [0.4, 0.7, 1.2, 2.0], [0.3, 0.7, 1.3, 2.4], seed=17),
+    # byte-wise path (degree 9)
     "complete10_p12_r5": instances.tiny_problem(
         10, [(i, j) for i in range(10) for j in range(i + 1, 10)],
         [((i * 7 + j * 3) % 5) - 2 or 1 for i in range(10) for j in range(i + 1, 10)],
@@ -103,7 +114,10 @@ def test_layouts_and_swap_modes_give_identical_bits():
     prob = instances.workload("regular3_n16_p32_r16", 2)
     ref = None
     for kw in (dict(threads_per_block=32), dict(threads_per_block=128), dict(threads_per_block=512),
-               dict(swap_mode=2), dict(swap_mode=1, threads_per_block=64)):
+               dict(swap_mode=2), dict(swap_mode=1, threads_per_block=64),
+               dict(kernel_path=1), dict(kernel_path=1, threads_per_block=96), dict(kernel_path=2),
+               dict(kernel_path=2, threads_per_block=64), dict(kernel_path=3), dict(kernel_path=3, producer_threads=32),
+               dict(kernel_path=3, threads_per_block=256, producer_threads=160), dict(kernel_path=3, swap_mode=2)):
         g = pt.PT.from_problem(prob, **kw)
         g.run(300, 1)
         g.run(77, 5)
@@ -114,6 +128,30 @@ def test_layouts_and_swap_modes_give_identical_bits():
             assert np.array_equal(cur[0], ref[0]), kw
             for k in ref[1]:
                 assert np.array_equal(np.asarray(cur[1][k]), np.asarray(ref[1][k])), (kw, k)
+
+
+@pytest.mark.parametrize("path", [1, 2, 3])
+def test_medium_workload_each_kernel_path(path):
+    prob = instances.workload("regular3_n256_p64_r64", 4)
+    g, o = both(prob, kernel_path=path)
+    assert g.info.kernel_path == path
+    g.run(150, 1)
+    o.run(150, 1)
+    assert_same(g, o, "path %d" % path)
+
+
+@pytest.mark.parametrize("path", [1, 2, 3])
+@pytest.mark.parametrize("name", ["prism_p8_r3", "complete8_p16_r4"])
+def test_tiny_packed_problems_each_path(name, path):
+    prob = TINY[name]
+    g, o = both(prob, kernel_path=path)
+    for s in range(30):
+        g.run(1, 1)
+        o.run(1, 1)
+        assert_same(g, o, "sweep %d" % (s + 1))
+    g.run(300, 2)
+    o.run(300, 2)
+    assert_same(g, o, "after 300 more")
 
 
 def test_run_equals_sweep_and_swap_calls():
