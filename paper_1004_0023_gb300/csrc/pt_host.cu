@@ -28,6 +28,7 @@ struct pt_ctx {
     long long t, q;
     long long sweep_limit;   // t never exceeds this (int64 statistics, 32-bit Philox counter)
     int max_passes;          // mailbox capacity of one launch
+    long long mbox_clear_q;  // pass index at which the mailboxes were last cleared
     bool cooperative;
     long long timeout_ns;
     int err;
@@ -225,6 +226,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     c->own_stream = false;
     c->stream = (cudaStream_t)cuda_stream;
     c->t = c->q = 0;
+    c->mbox_clear_q = 0;
     c->err = 0;
     c->msg[0] = 0;
     c->staging = nullptr;
@@ -296,16 +298,26 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         free_ctx(c);
         return create_fail(PT_EINVAL, "the packed kernel needs P %% 8 == 0 and degree <= 7");
     }
+    // statistics in shared memory for ladders up to 341 rungs (16 KB); all threshold rows in
+    // shared memory when they take at most 48 KB and the chosen layout still fits
+    p.acc_in_smem = (size_t)R * kAccCount * 8 <= 16384 ? 1 : 0;
+    p.tables_in_smem = (size_t)R * p.nL3 * 4 <= 49152 ? 1 : 0;
     int path = want_path;
+    const int want_threads = opt ? opt->threads_per_block : 0;
     if (path == 0) {
         path = kPathGeneric;
         if (packed_ok) {
-            if (sweep_smem_bytes(p, kPathPacked, packed_dc) <= (size_t)max_smem) path = kPathPacked;
+            // producer warps need a block of at least two warps
+            if ((want_threads == 0 || want_threads >= 64) &&
+                sweep_smem_bytes(p, kPathPacked, packed_dc) <= (size_t)max_smem)
+                path = kPathPacked;
             else if (sweep_smem_bytes(p, kPathPackedInline, packed_dc) <= (size_t)max_smem) path = kPathPackedInline;
         }
     }
     c->plan.path = path;
     c->plan.dclass = (path == kPathGeneric) ? dclass : packed_dc;
+    if (p.tables_in_smem && sweep_smem_bytes(p, path, c->plan.dclass) > (size_t)max_smem) p.tables_in_smem = 0;
+    if (p.acc_in_smem && sweep_smem_bytes(p, path, c->plan.dclass) > (size_t)max_smem) p.acc_in_smem = 0;
     c->plan.smem_bytes = sweep_smem_bytes(p, path, c->plan.dclass);
     if ((long long)c->plan.smem_bytes > (long long)max_smem) {
         free_ctx(c);
@@ -331,7 +343,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     }
     c->plan.n_consumer = c->plan.threads;
     if (path == kPathPacked) {
-        int prod = (opt && opt->producer_threads > 0) ? opt->producer_threads : c->plan.threads / 4;
+        int prod = (opt && opt->producer_threads > 0) ? opt->producer_threads
+                                                      : std::max(32, (c->plan.threads / 4) / 32 * 32);
         if (prod % 32 || prod >= c->plan.threads) {
             free_ctx(c);
             return create_fail(PT_EINVAL, "producer_threads must be a multiple of 32 below threads_per_block");
@@ -383,6 +396,11 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         const long long big = std::max(std::max(eb, mb), 1ll);
         const long long lim_sq = big > 3037000499ll ? 0 : (long long)(9223372036854775807ll / (big * big));
         c->sweep_limit = std::min<long long>(lim_sq, 0xFFFFFFFFll);
+        // the swap mailbox packs E into 40 bits and M into 32 bits
+        if (eb >= (1ll << 39) || mb >= (1ll << 31)) {
+            free_ctx(c);
+            return create_fail(PT_EINVAL, "energy or Trotter sum too large for this library");
+        }
     }
 
     // device memory
@@ -483,6 +501,12 @@ static int enqueue_sweeps(pt_ctx* c, long long n, int sps) {
         if (sps > 0) chunk = std::min<long long>(chunk, (long long)c->max_passes * sps);
         chunk = std::min<long long>(chunk, 1ll << 30);
         const int passes = sps > 0 ? (int)(chunk / sps) : 0;
+        if (passes > 0 && c->q + passes - c->mbox_clear_q >= kTagPeriod - 1) {
+            // a mailbox tag is q mod (2^24 - 1) + 1: clear before any tag value could repeat
+            CUDA_OR_FAIL(c, cudaMemsetAsync(c->dp.mbox, 0, (size_t)c->max_passes * c->dp.R * sizeof(Mailbox),
+                                            c->stream));
+            c->mbox_clear_q = c->q;
+        }
         CUDA_OR_FAIL(c, launch_sweeps(c->dp, c->plan, c->t, c->q, (int)chunk, sps, c->timeout_ns, sps > 0,
                                       c->stream));
         c->launches += 1;

@@ -12,14 +12,17 @@ constexpr uint32_t kTagFlip = 0u;
 constexpr uint32_t kTagSwap = 1u;
 constexpr uint32_t kTagInit = 2u;
 
-// One (pass, rung) mailbox of the in-kernel swap: the chain on rung r publishes its
-// (E, M) after the sweep that precedes pass q, then sets tag = q + 1 (release).
-struct alignas(32) Mailbox {
-    long long E;
-    long long M;
-    unsigned long long tag;
-    long long pad;
+// One (pass, rung) mailbox of the in-kernel swap: two self-validating 64-bit words that the
+// chain on rung r writes after the sweep preceding pass q,
+//   a = E << 24 | tag,   b = (uint32)M << 32 | tag,   tag = q mod (2^24 - 1) + 1 (never 0),
+// so a partner that sees the pass's tag in both words has a consistent (E, M) from one round
+// trip of two relaxed loads. |E| < 2^39 and |M| < 2^31 are checked at create; the host
+// clears the mailboxes before a tag value could repeat.
+struct alignas(16) Mailbox {
+    unsigned long long a;
+    unsigned long long b;
 };
+constexpr long long kTagPeriod = 16777215ll;
 
 // Per-rung statistics, in this order, as unsigned 64-bit two's-complement sums.
 enum { kAccN = 0, kAccE, kAccE2, kAccM, kAccM2, kAccFlip, kAccCount };
@@ -48,6 +51,8 @@ struct DevProblem {
     int dmax;                  // row stride of `nbr` (4, 8 or 32)
     int slot_stride;           // bytes between slots in `spins` (multiple of 16)
     int withhold_rung;         // test hook: rung whose chain never publishes (-1 = off)
+    int acc_in_smem;           // 1: per-rung statistics gathered in shared memory per launch
+    int tables_in_smem;        // 1: every rung's threshold row resident in shared memory
     uint32_t key0, key1;
 };
 

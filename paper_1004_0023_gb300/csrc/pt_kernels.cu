@@ -60,13 +60,10 @@ __device__ __forceinline__ double det_exp(double x) {
     const double LN2_HI = 0x1.62e42ff000000p-1;
     const double LN2_LO = -0x1.718432a1b0e26p-35;
     const double INV_LN2 = 0x1.71547652b82fep+0;
-    double inv_fact[14];
-    double fact = 1.0;
-#pragma unroll
-    for (int k = 0; k < 14; ++k) {
-        if (k > 0) fact = __dmul_rn(fact, (double)k);
-        inv_fact[k] = __ddiv_rn(1.0, fact);
-    }
+    // 1/k! rounded to nearest (k! is exact in double for k <= 13); folded at compile time
+    const double inv_fact[14] = {1.0, 1.0, 1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0,
+                                 1.0 / 5040.0, 1.0 / 40320.0, 1.0 / 362880.0, 1.0 / 3628800.0,
+                                 1.0 / 39916800.0, 1.0 / 479001600.0, 1.0 / 6227020800.0};
     const double nd = rint(__dmul_rn(x, INV_LN2));
     const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(nd, LN2_HI)), __dmul_rn(nd, LN2_LO));
     double poly = inv_fact[13];
@@ -108,6 +105,14 @@ __device__ __forceinline__ long long ld_relaxed_s64(const long long* p) {
     asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ void st_relaxed_s64(long long* p, long long v) {
     asm volatile("st.relaxed.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -126,16 +131,26 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 __host__ __device__ inline size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Byte-wise path (any even P, any degree up to 32).
+// Threshold rows and per-rung statistics in shared memory (when they fit).
+__host__ __device__ inline size_t thr_bytes(const DevProblem& p) {
+    return up16((size_t)(p.tables_in_smem ? p.R : 1) * p.nL3 * 4);
+}
+__host__ __device__ inline size_t acc_bytes(const DevProblem& p) {
+    return p.acc_in_smem ? (size_t)p.R * kAccCount * 8 : 0;
+}
+
 struct GenericLayout {
-    size_t spins, nbr, h, items, loff, thr, red, ctl, total;
-    __host__ __device__ GenericLayout(int N, int P, int dmax, int n_levels, int nL3) {
+    size_t spins, nbr, h, items, loff, thr, acc, red, ctl, total;
+    __host__ __device__ explicit GenericLayout(const DevProblem& p) {
+        const int N = p.N, P = p.P;
         size_t o = 0;
         spins = o; o += up16((size_t)N * P);
-        nbr = o;   o += up16((size_t)N * dmax * 4);
+        nbr = o;   o += up16((size_t)N * p.dmax * 4);
         h = o;     o += up16((size_t)N);
         items = o; o += up16((size_t)2 * N * 4);
-        loff = o;  o += up16((size_t)(n_levels + 1) * 4);
-        thr = o;   o += up16((size_t)nL3 * 4);
+        loff = o;  o += up16((size_t)(p.n_levels + 1) * 4);
+        thr = o;   o += thr_bytes(p);
+        acc = o;   o += acc_bytes(p);
         red = o;   o += 32 * 3 * 8;
         ctl = o;   o += 16;
         total = o;
@@ -147,15 +162,17 @@ struct GenericLayout {
 // producer), level offsets, the threshold row, reduction scratch, control words and, when
 // the random words are produced ahead, two buffers of one sweep's words each.
 struct FastLayout {
-    size_t spins, ones, desc, items, loff, thr, red, ctl, rbuf, total;
-    __host__ __device__ FastLayout(int N, int P, int dc, int n_levels, int nL3, bool pre) {
+    size_t spins, ones, desc, items, loff, thr, acc, red, ctl, rbuf, total;
+    __host__ __device__ FastLayout(const DevProblem& p, int dc, bool pre) {
+        const int N = p.N, P = p.P;
         size_t o = 0;
         spins = o; o += up16((size_t)N * P);
         ones = o;  o += up16((size_t)P);
         desc = o;  o += (size_t)2 * N * (dc == 4 ? 32 : 64);
         items = o; o += up16((size_t)2 * N * 4);
-        loff = o;  o += up16((size_t)(n_levels + 1) * 4);
-        thr = o;   o += up16((size_t)nL3 * 4);
+        loff = o;  o += up16((size_t)(p.n_levels + 1) * 4);
+        thr = o;   o += thr_bytes(p);
+        acc = o;   o += acc_bytes(p);
         red = o;   o += 32 * 3 * 8;
         ctl = o;   o += 16;
         rbuf = o;
@@ -165,8 +182,8 @@ struct FastLayout {
 };
 
 size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass) {
-    if (path == kPathGeneric) return GenericLayout(p.N, p.P, p.dmax, p.n_levels, p.nL3).total;
-    return FastLayout(p.N, p.P, dclass, p.n_levels, p.nL3, path == kPathPacked).total;
+    if (path == kPathGeneric) return GenericLayout(p).total;
+    return FastLayout(p, dclass, path == kPathPacked).total;
 }
 
 __device__ __forceinline__ void named_barrier(int id, int count) {
@@ -174,33 +191,45 @@ __device__ __forceinline__ void named_barrier(int id, int count) {
 }
 
 // ------------------------------------------------------------------------- end of a sweep
+__device__ __forceinline__ unsigned long long mbox_tag(long long q) {
+    return (unsigned long long)(q % kTagPeriod) + 1ull;
+}
+
 // Thread 0 of a chain's CTA, after the sweep's changes are reduced: update E and M, add the
-// statistics of the rung the chain sits on, and run the chain's side of swap pass q when
-// one follows this sweep. Returns the chain's rung for the next sweep; sets *abort when the
-// partner's mailbox never arrived within the time limit.
-__device__ int end_of_sweep(const DevProblem& p, int slot, int rung, long long& E, long long& M, long long dE,
-                            long long dM, long long nflip, int s, long long q0, int sweeps_per_swap,
+// statistics of the rung the chain sits on (to `acc`, shared or global), and run the chain's
+// side of swap pass q when one follows this sweep. Returns the chain's rung for the next
+// sweep; sets *abort when the partner's mailbox never arrived within the time limit.
+__device__ int end_of_sweep(const DevProblem& p, unsigned long long* acc, int rung, long long& E, long long& M,
+                            long long dE, long long dM, long long nflip, int s, long long q0, int sweeps_per_swap,
                             long long timeout_ns, const PhiloxKey& key, int* abort) {
     E += dE;
     M += dM;
-    unsigned long long* a = p.acc + (size_t)rung * kAccCount;
-    atomicAdd(a + kAccN, 1ull);
-    atomicAdd(a + kAccE, (unsigned long long)E);
-    atomicAdd(a + kAccE2, (unsigned long long)(E * E));
-    atomicAdd(a + kAccM, (unsigned long long)M);
-    atomicAdd(a + kAccM2, (unsigned long long)(M * M));
-    atomicAdd(a + kAccFlip, (unsigned long long)nflip);
+    unsigned long long* a = acc + (size_t)rung * kAccCount;
+    if (p.acc_in_smem) {
+        a[kAccN] += 1ull;
+        a[kAccE] += (unsigned long long)E;
+        a[kAccE2] += (unsigned long long)(E * E);
+        a[kAccM] += (unsigned long long)M;
+        a[kAccM2] += (unsigned long long)(M * M);
+        a[kAccFlip] += (unsigned long long)nflip;
+    } else {
+        atomicAdd(a + kAccN, 1ull);
+        atomicAdd(a + kAccE, (unsigned long long)E);
+        atomicAdd(a + kAccE2, (unsigned long long)(E * E));
+        atomicAdd(a + kAccM, (unsigned long long)M);
+        atomicAdd(a + kAccM2, (unsigned long long)(M * M));
+        atomicAdd(a + kAccFlip, (unsigned long long)nflip);
+    }
     *abort = 0;
     if (sweeps_per_swap <= 0 || (s + 1) % sweeps_per_swap != 0) return rung;
     const int R = p.R;
     const int pass = (s + 1) / sweeps_per_swap - 1;
     const long long q = q0 + pass;
+    const unsigned long long tag = mbox_tag(q);
     Mailbox* mb = p.mbox + (size_t)pass * R;
     if (rung != p.withhold_rung) {
-        st_relaxed_s64(&mb[rung].E, E);
-        st_relaxed_s64(&mb[rung].M, M);
-        __threadfence();
-        st_release_u64(&mb[rung].tag, (unsigned long long)(q + 1));
+        st_relaxed_u64(&mb[rung].a, ((unsigned long long)E << 24) | tag);
+        st_relaxed_u64(&mb[rung].b, ((unsigned long long)(uint32_t)(int32_t)M << 32) | tag);
     }
     int rl, partner;
     if ((rung & 1) == (int)(q & 1)) {
@@ -211,24 +240,49 @@ __device__ int end_of_sweep(const DevProblem& p, int slot, int rung, long long& 
         partner = rung - 1;
     }
     if (rl < 0 || rl + 1 >= R) return rung;
+    long long pE, pM;
     const unsigned long long start = globaltimer_ns();
-    while (ld_acquire_u64(&mb[partner].tag) != (unsigned long long)(q + 1)) {
+    for (;;) {
+        const unsigned long long wa = ld_relaxed_u64(&mb[partner].a);
+        const unsigned long long wb = ld_relaxed_u64(&mb[partner].b);
+        if ((wa & 0xFFFFFFull) == tag && (wb & 0xFFFFFFull) == tag) {
+            pE = (long long)wa >> 24;
+            pM = (long long)(int32_t)(uint32_t)(wb >> 32);
+            break;
+        }
         if ((long long)(globaltimer_ns() - start) > timeout_ns) {
             atomicCAS(p.status, 0, PT_ETIMEDOUT);
             *abort = 1;
             return rung;
         }
     }
-    const long long pE = ld_relaxed_s64(&mb[partner].E);
-    const long long pM = ld_relaxed_s64(&mb[partner].M);
     const bool lower = (rung == rl);
-    const bool acc = swap_accept(lower ? E : pE, lower ? pE : E, lower ? M : pM, lower ? pM : M, p.coef[rl],
-                                 p.coef[(R - 1) + rl], (uint32_t)q, (uint32_t)rl, key);
+    const bool acc_swap = swap_accept(lower ? E : pE, lower ? pE : E, lower ? M : pM, lower ? pM : M, p.coef[rl],
+                                      p.coef[(R - 1) + rl], (uint32_t)q, (uint32_t)rl, key);
     if (lower) {
         atomicAdd(p.swap_stats + 2 * rl, 1ull);
-        if (acc) atomicAdd(p.swap_stats + 2 * rl + 1, 1ull);
+        if (acc_swap) atomicAdd(p.swap_stats + 2 * rl + 1, 1ull);
     }
-    return acc ? partner : rung;
+    return acc_swap ? partner : rung;
+}
+
+// Shared-memory threshold rows: every rung's row when they fit, else the current one.
+__device__ __forceinline__ void load_thr(const DevProblem& p, uint32_t* s_thr, int rung, int tid, int nt) {
+    if (p.tables_in_smem) {
+        for (int x = tid; x < p.R * p.nL3; x += nt) s_thr[x] = p.thr[x];
+    } else {
+        for (int x = tid; x < p.nL3; x += nt) s_thr[x] = p.thr[(size_t)rung * p.nL3 + x];
+    }
+}
+__device__ __forceinline__ const uint32_t* thr_row(const DevProblem& p, const uint32_t* s_thr, int rung) {
+    return p.tables_in_smem ? s_thr + (size_t)rung * p.nL3 : s_thr;
+}
+
+// Per-launch statistics gathered in shared memory are added to the global rows once.
+__device__ __forceinline__ void flush_acc(const DevProblem& p, const unsigned long long* s_acc, int tid, int nt) {
+    if (!p.acc_in_smem) return;
+    for (int x = tid; x < p.R * kAccCount; x += nt)
+        if (s_acc[x]) atomicAdd(p.acc + x, s_acc[x]);
 }
 
 // ------------------------------------------------------------------------- generic sweep
@@ -242,7 +296,7 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
     const int N = p.N, P = p.P;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int slot = blockIdx.x;
-    const GenericLayout L(N, P, DCLASS, p.n_levels, p.nL3);
+    const GenericLayout L(p);
     int8_t* sp = reinterpret_cast<int8_t*>(smem + L.spins);
     uint32_t* s_nbr = reinterpret_cast<uint32_t*>(smem + L.nbr);
     int8_t* s_h = reinterpret_cast<int8_t*>(smem + L.h);
@@ -251,6 +305,7 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
     uint32_t* s_thr = reinterpret_cast<uint32_t*>(smem + L.thr);
     long long* s_red = reinterpret_cast<long long*>(smem + L.red);
     int* s_ctl = reinterpret_cast<int*>(smem + L.ctl);
+    unsigned long long* s_acc = reinterpret_cast<unsigned long long*>(smem + L.acc);
     (void)n_consumer;
 
     {
@@ -264,9 +319,12 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
         for (int x = tid; x <= p.n_levels; x += nt) s_loff[x] = p.level_off[x];
     }
     int rung = p.rung_of_slot[slot];
-    for (int x = tid; x < p.nL3; x += nt) s_thr[x] = p.thr[(size_t)rung * p.nL3 + x];
+    load_thr(p, s_thr, rung, tid, nt);
+    if (p.acc_in_smem)
+        for (int x = tid; x < p.R * kAccCount; x += nt) s_acc[x] = 0ull;
     long long E = p.E[slot], M = p.M[slot];  // meaningful in thread 0 only
     __syncthreads();
+    const uint32_t* thr = thr_row(p, s_thr, rung);
 
     const PhiloxKey key = philox_schedule(p.key0, p.key1);
     const int half = P >> 1;
@@ -313,7 +371,7 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
                         const int km1 = (k == 0) ? P - 1 : k - 1;
                         const int kp1 = (k + 1 == P) ? 0 : k + 1;
                         const int m = sk * ((int)row[km1] + (int)row[kp1]);
-                        const uint32_t th = s_thr[(Lf + Lmax) * 3 + (m >> 1) + 1];
+                        const uint32_t th = thr[(Lf + Lmax) * 3 + (m >> 1) + 1];
                         if (th == 0xFFFFFFFFu || rw[w] < th) {
                             row[k] = (int8_t)(-sk);
                             dE -= 2 * Lf;
@@ -345,8 +403,8 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
                 sF += s_red[w * 3 + 2];
             }
             int abort_flag = 0;
-            s_ctl[0] = end_of_sweep(p, slot, rung, E, M, sE, sM, sF, s, q0, sweeps_per_swap, timeout_ns, key,
-                                    &abort_flag);
+            s_ctl[0] = end_of_sweep(p, p.acc_in_smem ? s_acc : p.acc, rung, E, M, sE, sM, sF, s, q0,
+                                    sweeps_per_swap, timeout_ns, key, &abort_flag);
             s_ctl[1] = abort_flag;
         }
         __syncthreads();
@@ -354,10 +412,12 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
         const int nr = s_ctl[0];
         if (nr != rung) {
             rung = nr;
-            for (int x = tid; x < p.nL3; x += nt) s_thr[x] = p.thr[(size_t)rung * p.nL3 + x];
+            if (!p.tables_in_smem) load_thr(p, s_thr, rung, tid, nt);
+            thr = thr_row(p, s_thr, rung);
         }
         __syncthreads();
     }
+    flush_acc(p, s_acc, tid, nt);
 
     {
         int4* dst = reinterpret_cast<int4*>(p.spins + (size_t)slot * p.slot_stride);
@@ -492,7 +552,7 @@ sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int 
     const int N = p.N, P = p.P;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int slot = blockIdx.x;
-    const FastLayout L(N, P, DC, p.n_levels, p.nL3, PRE);
+    const FastLayout L(p, DC, PRE);
     int8_t* sp = reinterpret_cast<int8_t*>(smem + L.spins);
     uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem + L.desc);
     uint32_t* s_items = reinterpret_cast<uint32_t*>(smem + L.items);
@@ -501,6 +561,7 @@ sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int 
     long long* s_red = reinterpret_cast<long long*>(smem + L.red);
     int* s_ctl = reinterpret_cast<int*>(smem + L.ctl);
     uint4* rbuf = reinterpret_cast<uint4*>(smem + L.rbuf);
+    unsigned long long* s_acc = reinterpret_cast<unsigned long long*>(smem + L.acc);
     const int NC = PRE ? n_consumer : nt;
     const bool consumer = tid < NC;
     const int DW = (DC == 4) ? 8 : 16;
@@ -519,7 +580,9 @@ sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int 
         for (int x = tid; x <= p.n_levels; x += nt) s_loff[x] = p.level_off[x];
     }
     int rung = p.rung_of_slot[slot];
-    for (int x = tid; x < p.nL3; x += nt) s_thr[x] = p.thr[(size_t)rung * p.nL3 + x];
+    load_thr(p, s_thr, rung, tid, nt);
+    if (p.acc_in_smem)
+        for (int x = tid; x < p.R * kAccCount; x += nt) s_acc[x] = 0ull;
     long long E = p.E[slot], M = p.M[slot];  // meaningful in thread 0 only
 
     const PhiloxKey key = philox_schedule(p.key0, p.key1);
@@ -527,7 +590,7 @@ sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int 
     int lg = 0;
     while ((1 << lg) < G) ++lg;
     const int gmask = (1 << lg) - 1;
-    const uint32_t* thr_c = s_thr + 3 * p.Lmax;
+    const uint32_t* thr_c = thr_row(p, s_thr, rung) + 3 * p.Lmax;
     const int n_items = 2 * N;
     const int lane = tid & 31, warp = tid >> 5;
     __syncthreads();
@@ -573,15 +636,16 @@ sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int 
                     sF += s_red[w * 3 + 2];
                 }
                 int abort_flag = 0;
-                s_ctl[2 * (s & 1)] = end_of_sweep(p, slot, rung, E, M, sE, sM, sF, s, q0, sweeps_per_swap,
-                                                  timeout_ns, key, &abort_flag);
+                s_ctl[2 * (s & 1)] = end_of_sweep(p, p.acc_in_smem ? s_acc : p.acc, rung, E, M, sE, sM, sF, s,
+                                                  q0, sweeps_per_swap, timeout_ns, key, &abort_flag);
                 s_ctl[2 * (s & 1) + 1] = abort_flag;
             }
             if (PRE) named_barrier(1, NC); else __syncthreads();
             const int nr = s_ctl[2 * (s & 1)];
             if (!s_ctl[2 * (s & 1) + 1] && nr != rung) {
                 rung = nr;
-                for (int x = tid; x < p.nL3; x += NC) s_thr[x] = p.thr[(size_t)rung * p.nL3 + x];
+                if (!p.tables_in_smem) load_thr(p, s_thr, rung, tid, NC);
+                thr_c = thr_row(p, s_thr, rung) + 3 * p.Lmax;
             }
         } else if (s + 1 < n_sweeps) {
             produce_words(rbuf + (size_t)((s + 1) & 1) * n_items * G, t + 1u, s_items, n_items, G, lg, gmask,
@@ -590,6 +654,7 @@ sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int 
         __syncthreads();
         if (s_ctl[2 * (s & 1) + 1]) return;  // a partner never arrived; status holds PT_ETIMEDOUT
     }
+    flush_acc(p, s_acc, tid, nt);
 
     {
         int4* dst = reinterpret_cast<int4*>(p.spins + (size_t)slot * p.slot_stride);
