@@ -78,7 +78,9 @@ typedef struct {
                                    words, 3 = packed with random words produced one sweep
                                    ahead by dedicated warps (needs P % 8 == 0, degree <= 7) */
     int32_t producer_threads;   /* path 3: threads producing random words (0 = auto) */
-    int32_t reserved[2];
+    int32_t test_exact_swaps;   /* test hook: 1 = skip the FP32 pre-decision of swaps and always
+                                   evaluate the FP64 rule (results are identical either way) */
+    int32_t reserved[1];
 } pt_options;
 
 /* Statistics (Fig. 4 "gather statistics"; Sec. 5 accumulates in high precision).

@@ -280,6 +280,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     p.n_levels = (int)level_off.size() - 1;
     p.slot_stride = (int)(((size_t)N * P + 15) & ~(size_t)15);
     p.withhold_rung = (opt && opt->test_withhold_rung > 0) ? opt->test_withhold_rung - 1 : -1;
+    p.exact_swaps = (opt && opt->test_exact_swaps) ? 1 : 0;
     p.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
     p.key1 = (uint32_t)(seed >> 32);
 

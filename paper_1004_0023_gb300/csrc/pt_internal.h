@@ -53,6 +53,7 @@ struct DevProblem {
     int withhold_rung;         // test hook: rung whose chain never publishes (-1 = off)
     int acc_in_smem;           // 1: per-rung statistics gathered in shared memory per launch
     int tables_in_smem;        // 1: every rung's threshold row resident in shared memory
+    int exact_swaps;           // test hook: 1 = always take the FP64 swap decision
     uint32_t key0, key1;
 };
 

@@ -89,6 +89,39 @@ __device__ __forceinline__ bool swap_accept(long long EX, long long EY, long lon
     return u.x < ts;
 }
 
+// The same decision without FP64 in the common case. GB300's FP64 pipe makes the ~40
+// dependent FP64 operations of swap_accept cost over a microsecond, so Delta and exp(Delta)
+// are first estimated in FP32 with an error bound:
+//   |D - Delta| <= err = 5*2^-24 * (|a dE| + |c dM|)   (conversions of a, c, dE, dM, two
+//   products, one sum, and the FP64 roundings of Delta itself, with room to spare), and
+//   2^32 exp(D) within a relative 1e-5 + 1.01 err of 2^32 exp(Delta) (expf is within 2 ulp).
+// The estimate decides only when u is farther than that margin (plus float rounding of u)
+// from the threshold, or Delta's sign and the -23 cut are certain; otherwise swap_accept
+// decides. Either way the result equals swap_accept's.
+__device__ __forceinline__ bool swap_accept_fast(long long EX, long long EY, long long MX, long long MY,
+                                                 double a, double c, uint32_t q, uint32_t rl,
+                                                 const PhiloxKey& key, bool exact_only) {
+    if (!exact_only) {
+        const float pa = (float)a * (float)(EX - EY);
+        const float pc = (float)c * (float)(MX - MY);
+        const float D = pa + pc;
+        const float err = (fabsf(pa) + fabsf(pc)) * 2.99e-7f + 1e-30f;
+        if (D >= 2.0f * err) return true;                       // Delta >= 0
+        if (err < 0.25f) {
+            if (D < -23.5f) return false;                         // Delta <= -23
+            if (D + 2.0f * err < 0.0f && D > -22.5f) {
+                const uint4 r4 = philox(make_uint4(q, rl, 0u, kTagSwap << 28), key);
+                const float v = 4294967296.0f * expf(D);
+                const float margin = v * (1.0e-5f + 1.01f * err) + 512.0f;
+                const float uf = (float)r4.x;
+                if (uf + margin < v) return true;
+                if (uf - margin > v) return false;
+            }
+        }
+    }
+    return swap_accept(EX, EY, MX, MY, a, c, q, rl, key);
+}
+
 // ------------------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -257,8 +290,9 @@ __device__ int end_of_sweep(const DevProblem& p, unsigned long long* acc, int ru
         }
     }
     const bool lower = (rung == rl);
-    const bool acc_swap = swap_accept(lower ? E : pE, lower ? pE : E, lower ? M : pM, lower ? pM : M, p.coef[rl],
-                                      p.coef[(R - 1) + rl], (uint32_t)q, (uint32_t)rl, key);
+    const bool acc_swap = swap_accept_fast(lower ? E : pE, lower ? pE : E, lower ? M : pM, lower ? pM : M,
+                                           p.coef[rl], p.coef[(R - 1) + rl], (uint32_t)q, (uint32_t)rl, key,
+                                           p.exact_swaps != 0);
     if (lower) {
         atomicAdd(p.swap_stats + 2 * rl, 1ull);
         if (acc_swap) atomicAdd(p.swap_stats + 2 * rl + 1, 1ull);
@@ -481,8 +515,9 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* desc, co
         }
     }
     const uint2 own = *reinterpret_cast<const uint2*>(sp + row + c);
-    const uint32_t el = (uint8_t)sp[row + (c == 0 ? (uint32_t)P - 1 : c - 1)];
-    const uint32_t er = (uint8_t)sp[row + (c + 8 == (uint32_t)P ? 0u : c + 8)];
+    // the one Trotter neighbour outside the chunk: copy c-1 for even copies, c+8 for odd
+    const uint32_t eoff = par ? (c + 8 == (uint32_t)P ? 0u : c + 8) : (c == 0 ? (uint32_t)P - 1 : c - 1);
+    const uint32_t edge = (uint8_t)sp[row + eoff];
     uint2 nb[DC];
 #pragma unroll
     for (int d = 0; d < DC; ++d) nb[d] = *reinterpret_cast<const uint2*>(sp + nrow[d] + c);
@@ -497,9 +532,9 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* desc, co
     const uint32_t selS = par ? 0x7531u : 0x6420u;
     const uint32_t S = __byte_perm(own.x, own.y, selS);
     uint32_t Rn = __byte_perm(own.x, own.y, par ? 0x0642u : 0x7531u);
-    Rn = par ? __byte_perm(Rn, er, 0x4210u) : Rn;
+    Rn = par ? __byte_perm(Rn, edge, 0x4210u) : Rn;
     uint32_t Ln = __byte_perm(own.x, own.y, par ? 0x6420u : 0x5310u);
-    Ln = par ? Ln : __byte_perm(Ln, el, 0x3214u);
+    Ln = par ? Ln : __byte_perm(Ln, edge, 0x3214u);
     const uint32_t X = (S ^ Ln) & 0x02020202u;
     const uint32_t Y = (S ^ Rn) & 0x02020202u;
     const uint32_t Z = 0x02020202u - ((X + Y) >> 1);
@@ -518,20 +553,20 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* desc, co
         f[2] = __dp4a((int)__byte_perm(t1, t3, 0x5410u), (int)jpack[b], f[2]);
         f[3] = __dp4a((int)__byte_perm(t1, t3, 0x7632u), (int)jpack[b], f[3]);
     }
-    uint32_t F = 0;
+    uint32_t F = 0;  // 0xFE in byte w when copy w flips (XOR turns +1 <-> -1)
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
         const int sw = (int)prmt(S, 0u, 0x8880u | (0x1110u * (uint32_t)w) | (uint32_t)w);
         const int Lw = sw * f[w];
         const int col = (int)__byte_perm(Z, 0u, 0x4440u | (uint32_t)w);
         const uint32_t th = thr_c[3 * Lw + col];
-        if (u[w] < th || th == 0xFFFFFFFFu) {
-            F |= 0xFEu << (8 * w);
-            sumL += Lw;
-            sumC += col;
-            nflip += 1;
-        }
+        const bool acc = (u[w] < th) | (th == 0xFFFFFFFFu);
+        F |= acc ? (0xFEu << (8 * w)) : 0u;
+        sumL += acc ? Lw : 0;
     }
+    // flips and their Trotter columns from the packed flip mask
+    nflip += __popc(F & 0x02020202u);
+    sumC = __dp4a((int)(Z & (F >> 1)), 0x01010101, sumC);
     if (F) {
         const uint32_t lo = __byte_perm(F, 0u, par ? 0x1404u : 0x4140u);
         const uint32_t hi = __byte_perm(F, 0u, par ? 0x3424u : 0x4342u);
@@ -739,8 +774,8 @@ __global__ void swap_kernel(DevProblem p, long long q) {
     const PhiloxKey key = philox_schedule(p.key0, p.key1);
     for (int rl = (int)(q & 1) + 2 * (int)threadIdx.x; rl + 1 < p.R; rl += 2 * (int)blockDim.x) {
         const int X = p.slot_of_rung[rl], Y = p.slot_of_rung[rl + 1];
-        const bool acc = swap_accept(p.E[X], p.E[Y], p.M[X], p.M[Y], p.coef[rl], p.coef[(p.R - 1) + rl],
-                                     (uint32_t)q, (uint32_t)rl, key);
+        const bool acc = swap_accept_fast(p.E[X], p.E[Y], p.M[X], p.M[Y], p.coef[rl], p.coef[(p.R - 1) + rl],
+                                          (uint32_t)q, (uint32_t)rl, key, p.exact_swaps != 0);
         p.swap_stats[2 * rl] += 1ull;
         if (acc) {
             p.swap_stats[2 * rl + 1] += 1ull;

@@ -117,7 +117,8 @@ def test_layouts_and_swap_modes_give_identical_bits():
                dict(swap_mode=2), dict(swap_mode=1, threads_per_block=64),
                dict(kernel_path=1), dict(kernel_path=1, threads_per_block=96), dict(kernel_path=2),
                dict(kernel_path=2, threads_per_block=64), dict(kernel_path=3), dict(kernel_path=3, producer_threads=32),
-               dict(kernel_path=3, threads_per_block=256, producer_threads=160), dict(kernel_path=3, swap_mode=2)):
+               dict(kernel_path=3, threads_per_block=256, producer_threads=160), dict(kernel_path=3, swap_mode=2),
+               dict(test_exact_swaps=1), dict(test_exact_swaps=1, swap_mode=2)):
         g = pt.PT.from_problem(prob, **kw)
         g.run(300, 1)
         g.run(77, 5)
@@ -152,6 +153,19 @@ def test_tiny_packed_problems_each_path(name, path):
     g.run(300, 2)
     o.run(300, 2)
     assert_same(g, o, "after 300 more")
+
+
+def test_exact_swap_rule_and_fast_pre_decision_agree_on_the_medium_workload():
+    """Every swap decided by the FP32 pre-decision equals the FP64 rule (both vs the oracle)."""
+    prob = instances.workload("regular3_n256_p64_r64", 5)
+    a = pt.PT.from_problem(prob)
+    b = pt.PT.from_problem(prob, test_exact_swaps=1)
+    o = Oracle.from_problem(prob, threads=THREADS)
+    for x in (a, b):
+        x.run(400, 1)
+    o.run(400, 1)
+    assert_same(a, o, "pre-decided swaps")
+    assert_same(b, o, "exact swaps")
 
 
 def test_run_equals_sweep_and_swap_calls():
