@@ -326,9 +326,10 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                            c->plan.smem_bytes, max_smem);
     }
     if (opt && opt->threads_per_block > 0) {
-        if (opt->threads_per_block % 32 || opt->threads_per_block > 512) {
+        const int tmax = (path == kPathGeneric) ? 512 : 1024;
+        if (opt->threads_per_block % 32 || opt->threads_per_block > tmax) {
             free_ctx(c);
-            return create_fail(PT_EINVAL, "threads_per_block must be a multiple of 32 <= 512");
+            return create_fail(PT_EINVAL, "threads_per_block must be a multiple of 32 <= %d for this kernel", tmax);
         }
         c->plan.threads = opt->threads_per_block;
     } else if (path == kPathPacked) {

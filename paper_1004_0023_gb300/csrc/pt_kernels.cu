@@ -579,8 +579,8 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* desc, co
 // random words of sweep s+1 into one shared buffer while the consumer warps run the levels
 // of sweep s out of the other; consumers synchronise levels on named barrier 1 and both
 // groups meet once per sweep.
-template <int DC, bool PRE>
-__global__ void __launch_bounds__(512, 1)
+template <int DC, bool PRE, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
 sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
                     long long timeout_ns, int n_consumer) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -811,8 +811,14 @@ static const void* sweep_fn(const LaunchPlan& plan) {
         }
     }
     const bool pre = plan.path == kPathPacked;
-    if (plan.dclass == 4) return pre ? (const void*)sweep_packed_kernel<4, true> : (const void*)sweep_packed_kernel<4, false>;
-    return pre ? (const void*)sweep_packed_kernel<8, true> : (const void*)sweep_packed_kernel<8, false>;
+    if (plan.threads > 512) {
+        if (plan.dclass == 4)
+            return pre ? (const void*)sweep_packed_kernel<4, true, 1024> : (const void*)sweep_packed_kernel<4, false, 1024>;
+        return pre ? (const void*)sweep_packed_kernel<8, true, 1024> : (const void*)sweep_packed_kernel<8, false, 1024>;
+    }
+    if (plan.dclass == 4)
+        return pre ? (const void*)sweep_packed_kernel<4, true, 512> : (const void*)sweep_packed_kernel<4, false, 512>;
+    return pre ? (const void*)sweep_packed_kernel<8, true, 512> : (const void*)sweep_packed_kernel<8, false, 512>;
 }
 
 // The dynamic shared-memory limit is a per-function attribute shared by every context, so
