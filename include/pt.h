@@ -178,6 +178,60 @@ int pt_make_tables(int32_t P, const pt_rung* ladder, int32_t R, int32_t lmax, ui
 int pt_make_schedule(const pt_instance* inst, uint32_t* items, int32_t* level_off,
                      int32_t* n_levels);
 
+/* ---- Running on caller-owned device memory, without allocating ----------------------
+ * The paper has no counterpart to this entry point. It is for callers that cannot allocate
+ * device memory, neither themselves nor through this library: work recorded into a CUDA
+ * graph by stream capture (allocations are not captured), latency-critical loops that must
+ * not enter the allocator, and embedding runtimes that hand out device memory only from
+ * their own pool. pt_create allocates; such a caller instead builds the problem with
+ * pt_make_tables and pt_make_schedule, copies it into device memory it owns, and calls
+ * pt_run_noalloc, which allocates nothing (no cudaMalloc, no cudaFree, no library routine
+ * that allocates).
+ *
+ * The only scratch memory the kernel needs, the swap mailboxes, is one fixed array of
+ * PT_NOALLOC_MAILBOXES 16-byte entries (256 KiB) that every GPU loading this library holds
+ * until the process exits. All calls share it and it keeps the last call's contents; each
+ * launch clears the entries it uses. Calls that overlap on the GPU (other streams, other
+ * threads) race on it: serialise them. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture. */
+#define PT_NOALLOC_MAILBOXES 16384  /* swap passes x rungs one launch can hold */
+
+typedef struct {
+    int32_t n, P, R;            /* sites, Trotter copies (even), rungs (R <= PT_NOALLOC_MAILBOXES) */
+    int32_t lmax;               /* max_i(|h_i| + sum_j |J_ij|) <= 127 */
+    int32_t row_stride;         /* entries per row of nbr: 4, 8 or 32, >= the largest degree */
+    int32_t n_levels;           /* level count returned by pt_make_schedule */
+    const uint32_t* nbr;        /* [n][row_stride]: (j << 8) | (uint8_t)J_ij; unused entries (i << 8) */
+    const int8_t* h;            /* [n] */
+    const uint32_t* items;      /* [2n] from pt_make_schedule */
+    const int32_t* level_off;   /* [n_levels + 1] from pt_make_schedule */
+    const uint32_t* thr;        /* [R][(2*lmax+1)*3] from pt_make_tables */
+    const double* coef;         /* [2(R-1)] from pt_make_tables (read only when R > 1) */
+    int8_t* spins;              /* in/out [R][n*P rounded up to 16] by replica, copy index fastest;
+                                   16-byte aligned */
+    int64_t* E;                 /* in/out [R] by replica: sum_k E(s^k) of its spins */
+    int64_t* M;                 /* in/out [R] by replica: M(X) of its spins */
+    int32_t* rung_of_slot;      /* in/out [R] rung of each replica */
+    int32_t* slot_of_rung;      /* in/out [R] replica on each rung (inverse permutation) */
+    uint64_t* stats;            /* in/out [R][6] per rung: count, sum E, sum E^2, sum M, sum M^2,
+                                   accepted flips (added to) */
+    uint64_t* swap_stats;       /* in/out [R][2] per pair r: attempts, accepts (added to) */
+    int32_t* status;            /* in/out: 0, or PT_ETIMEDOUT if a swap wait gave up */
+    uint64_t seed;              /* Philox key */
+    int64_t t0;                 /* sweeps done so far (the caller advances it by n_sweeps) */
+    int64_t q0;                 /* swap passes done so far (advance by n_sweeps/sweeps_per_swap) */
+} pt_device_problem;
+
+/* Same arithmetic and bits as pt_run(n_sweeps, sweeps_per_swap) on a context in the same
+ * state, launched on cuda_stream (asynchronous). All pointers are device pointers owned by
+ * the caller. Returns PT_EINVAL (message in pt_noalloc_last_error) for sizes beyond the
+ * fixed mailbox array or the shared memory of one CTA, PT_EOVERFLOW for counters past
+ * 2^32 - 1, PT_ECUDA if a launch fails. */
+int pt_run_noalloc(const pt_device_problem* prob, int64_t n_sweeps, int32_t sweeps_per_swap,
+                   int32_t wait_timeout_ms, void* cuda_stream);
+const char* pt_noalloc_last_error(void);
+
 /* Wait for all queued work of the context. */
 int pt_sync(pt_ctx* ctx);
 

@@ -52,6 +52,13 @@ class pt_info(ctypes.Structure):
                 ("kernel_path", _i32), ("producer_threads", _i32), ("device_bytes", _i64), ("kernel_launches", _i64), ("h2d_bytes", _i64)]
 
 
+class pt_device_problem(ctypes.Structure):
+    _fields_ = [("n", _i32), ("P", _i32), ("R", _i32), ("lmax", _i32), ("row_stride", _i32), ("n_levels", _i32),
+                ("nbr", _vp), ("h", _vp), ("items", _vp), ("level_off", _vp), ("thr", _vp), ("coef", _vp),
+                ("spins", _vp), ("E", _vp), ("M", _vp), ("rung_of_slot", _vp), ("slot_of_rung", _vp),
+                ("stats", _vp), ("swap_stats", _vp), ("status", _vp), ("seed", _u64), ("t0", _i64), ("q0", _i64)]
+
+
 class PTError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s: %s" % (_NAMES.get(code, code), msg))
@@ -85,6 +92,8 @@ def load(path: str = LIB_PATH):
     lib.pt_last_error.restype = ctypes.c_char_p
     lib.pt_make_tables.argtypes = [_i32, ctypes.POINTER(pt_rung), _i32, _i32, _vp, _vp]
     lib.pt_make_schedule.argtypes = [ctypes.POINTER(pt_instance), _vp, _vp, _p_i32]
+    lib.pt_run_noalloc.argtypes = [ctypes.POINTER(pt_device_problem), _i64, _i32, _i32, _vp]
+    lib.pt_noalloc_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -93,7 +102,8 @@ def exported_symbols():
     """Names of the entry points declared in include/pt.h."""
     return ["pt_create", "pt_sweep", "pt_swap", "pt_run", "pt_read_state", "pt_write_state",
             "pt_read_observables", "pt_read_tables", "pt_get_info", "pt_sync", "pt_destroy",
-            "pt_last_error", "pt_make_tables", "pt_make_schedule"]
+            "pt_last_error", "pt_make_tables", "pt_make_schedule", "pt_run_noalloc",
+            "pt_noalloc_last_error"]
 
 
 def _instance(n, ei, ej, J, h, keep):
@@ -134,6 +144,15 @@ def make_schedule(n, ei, ej):
 
 def _ptr(a):
     return a.ctypes.data_as(_vp)
+
+
+def run_noalloc(problem, n_sweeps, sweeps_per_swap, wait_timeout_ms=0, stream=None):
+    """pt_run_noalloc on a filled pt_device_problem (device pointers owned by the caller)."""
+    lib = load()
+    rc = lib.pt_run_noalloc(ctypes.byref(problem), int(n_sweeps), int(sweeps_per_swap), int(wait_timeout_ms),
+                            None if stream is None else _vp(int(stream)))
+    if rc != PT_OK:
+        raise PTError(rc, lib.pt_noalloc_last_error().decode())
 
 
 class PT:
