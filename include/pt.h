@@ -80,7 +80,8 @@ typedef struct {
     int32_t producer_threads;   /* path 3: threads producing random words (0 = auto) */
     int32_t test_exact_swaps;   /* test hook: 1 = skip the FP32 pre-decision of swaps and always
                                    evaluate the FP64 rule (results are identical either way) */
-    int32_t reserved[1];
+    int32_t cluster_size;       /* batched launches: CTAs per thread-block cluster (0 = 4) */
+    int32_t reserved[4];
 } pt_options;
 
 /* Statistics (Fig. 4 "gather statistics"; Sec. 5 accumulates in high precision).
@@ -177,6 +178,48 @@ int pt_make_tables(int32_t P, const pt_rung* ladder, int32_t R, int32_t lmax, ui
                    double* coef);
 int pt_make_schedule(const pt_instance* inst, uint32_t* items, int32_t* level_off,
                      int32_t* n_levels);
+
+/* ---- Many independent problems in one launch ----------------------------------------
+ * The paper solves many problem instances (Sec. 1) one application run at a time; here a
+ * batch of independent requests shares one persistent launch. A thread-block cluster takes
+ * one request at a time (largest first) and runs all of its sweeps and swap passes; each
+ * request gets exactly the bits pt_create + pt_run would give it alone. Batched requests
+ * need P % 8 == 0, degree <= 7, R <= 1024 and one chain's spins plus its instance data
+ * within one CTA's shared memory. */
+typedef struct {
+    pt_instance inst;            /* copied at pt_batch_create */
+    int32_t P;                   /* Trotter copies */
+    const pt_rung* ladder;       /* R rungs (copied) */
+    int32_t R;
+    uint64_t seed;               /* Philox key of this request */
+    int64_t n_sweeps;            /* sweeps per pt_batch_run (<= 2^30) */
+    int32_t sweeps_per_swap;     /* a swap pass after every sweeps_per_swap-th sweep (0 = none) */
+} pt_request;
+
+typedef struct pt_batch pt_batch;
+
+typedef struct {
+    int32_t count;              /* requests */
+    int32_t cluster;            /* CTAs per cluster */
+    int32_t n_clusters;         /* clusters in the persistent grid */
+    int32_t threads_per_block;
+    int64_t smem_bytes;         /* dynamic shared memory per CTA */
+    int64_t device_bytes;
+    int64_t kernel_launches;
+    int64_t h2d_bytes;
+} pt_batch_info;
+
+/* Copy and prepare every request (tables, schedules, initial spins as in pt_create). */
+int pt_batch_create(const pt_request* reqs, int32_t count, const pt_options* opt, void* cuda_stream,
+                    pt_batch** out);
+/* One persistent launch running every request's n_sweeps (with its swap passes). Async. */
+int pt_batch_run(pt_batch* b);
+int pt_batch_read_state(pt_batch* b, int32_t index, int8_t* out, size_t bytes);   /* syncs */
+int pt_batch_read_observables(pt_batch* b, int32_t index, pt_observables* out);  /* syncs */
+int pt_batch_get_info(const pt_batch* b, pt_batch_info* out);
+int pt_batch_sync(pt_batch* b);
+int pt_batch_destroy(pt_batch* b);
+const char* pt_batch_last_error(const pt_batch* b);
 
 /* ---- Running on caller-owned device memory, without allocating ----------------------
  * The paper has no counterpart to this entry point. It is for callers that cannot allocate

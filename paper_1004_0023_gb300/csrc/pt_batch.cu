@@ -1,0 +1,826 @@
+// pt_batch.cu -- many independent PT-QMC problems in one persistent launch.
+//
+// Each thread-block cluster pulls a whole problem from a work counter (problems sorted by
+// work, largest first) and owns it until every sweep is done: CTA r of the cluster sweeps
+// chains [r*C, (r+1)*C), C = ceil(R / cluster). Within a CTA the chains are "packed" onto
+// groups of threads (the paper's chain packing, Sec. 5): a group sweeps one chain at a time
+// with the same level schedule, random-number counters and 4-copy update unit as the
+// single-problem kernel, so every problem gets exactly the bits it would get alone. For a
+// swap pass the CTAs publish (E, M) of their chains in shared memory, meet at one cluster
+// barrier, and each CTA evaluates every pair's decision from the peers' shared memory
+// (the same inputs everywhere give the same rung permutation everywhere). No CTA ever waits
+// for another cluster, so the persistent launch needs no co-residency guarantee beyond
+// the cluster's own.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pt.h"
+#include "pt_device.cuh"
+#include "pt_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace ptq {
+
+// Shared memory of one CTA while it owns problem I.
+struct BatchLayout {
+    size_t sdesc, items, loff, rung, slot, E, M, pub, thr, red, chains, total;
+    int C, ngroups, chain_stride, nbufs, DW, thr_words;
+    __host__ __device__ BatchLayout(const BatchInstance& I, int K, int threads) {
+        DW = I.dc == 4 ? 8 : 12;
+        C = (I.R + K - 1) / K;
+        ngroups = threads / I.group_threads;
+        chain_stride = (int)(up16((size_t)I.slot_stride) + up16((size_t)I.P));
+        nbufs = I.resident ? C : ngroups;
+        thr_words = (int)(up16((size_t)I.nL3 * 4) / 4);
+        size_t o = 0;
+        sdesc = o;  o += (size_t)I.N * DW * 4;
+        items = o;  o += up16((size_t)2 * I.N * 4);
+        loff = o;   o += up16((size_t)(I.n_levels + 1) * 4);
+        rung = o;   o += up16((size_t)I.R * 4);
+        slot = o;   o += up16((size_t)I.R * 4);
+        E = o;      o += up16((size_t)C * 8);
+        M = o;      o += up16((size_t)C * 8);
+        pub = o;    o += (size_t)2 * C * 16;
+        thr = o;    o += (size_t)ngroups * thr_words * 4;
+        red = o;    o += up16((size_t)ngroups * (I.group_threads / 32) * 3 * 8);
+        chains = o; o += (size_t)nbufs * chain_stride;
+        total = o;
+    }
+};
+
+size_t batch_smem_bytes(const BatchInstance& I, int cluster, int threads) {
+    return BatchLayout(I, cluster, threads).total;
+}
+
+template <int DC>
+__device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::cluster_group& cluster, int rank,
+                            int K) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const BatchLayout L(I, K, nt);
+    uint32_t* s_sdesc = reinterpret_cast<uint32_t*>(smem + L.sdesc);
+    uint32_t* s_items = reinterpret_cast<uint32_t*>(smem + L.items);
+    int32_t* s_loff = reinterpret_cast<int32_t*>(smem + L.loff);
+    int32_t* s_rung = reinterpret_cast<int32_t*>(smem + L.rung);
+    int32_t* s_slot = reinterpret_cast<int32_t*>(smem + L.slot);
+    long long* s_E = reinterpret_cast<long long*>(smem + L.E);
+    long long* s_M = reinterpret_cast<long long*>(smem + L.M);
+    longlong2* s_pub = reinterpret_cast<longlong2*>(smem + L.pub);
+    uint32_t* s_thr = reinterpret_cast<uint32_t*>(smem + L.thr);
+    long long* s_red = reinterpret_cast<long long*>(smem + L.red);
+    unsigned char* s_chains = smem + L.chains;
+
+    const int N = I.N, P = I.P, R = I.R, C = L.C;
+    const int c_begin = rank * C;
+    const int c_count = max(0, min(C, R - c_begin));
+    const int gsize = I.group_threads, ngroups = L.ngroups;
+    const int grp = tid / gsize, gtid = tid - grp * gsize;
+
+    // ---- the problem's schedule, descriptors and rung permutation; this CTA's chains
+    {
+        const int4* src = reinterpret_cast<const int4*>(I.sdesc);
+        int4* dst = reinterpret_cast<int4*>(s_sdesc);
+        for (int x = tid; x < N * L.DW / 4; x += nt) dst[x] = src[x];
+        for (int x = tid; x < 2 * N; x += nt) s_items[x] = I.items[x];
+        for (int x = tid; x <= I.n_levels; x += nt) s_loff[x] = I.level_off[x];
+        for (int x = tid; x < R; x += nt) {
+            s_rung[x] = I.rung_of_slot[x];
+            s_slot[x] = I.slot_of_rung[x];
+        }
+        for (int x = tid; x < c_count; x += nt) {
+            s_E[x] = I.E[c_begin + x];
+            s_M[x] = I.M[c_begin + x];
+        }
+        for (int b = 0; b < L.nbufs; ++b) {
+            int8_t* ones = reinterpret_cast<int8_t*>(s_chains + (size_t)b * L.chain_stride + I.slot_stride);
+            for (int x = tid; x < P; x += nt) ones[x] = 1;
+        }
+        if (I.resident) {
+            const int n16 = I.slot_stride / 16;
+            for (int lc = 0; lc < c_count; ++lc) {
+                const int4* cs = reinterpret_cast<const int4*>(I.spins + (size_t)(c_begin + lc) * I.slot_stride);
+                int4* cd = reinterpret_cast<int4*>(s_chains + (size_t)lc * L.chain_stride);
+                for (int x = tid; x < n16; x += nt) cd[x] = cs[x];
+            }
+        }
+    }
+    __syncthreads();
+
+    const PhiloxKey key = philox_schedule(I.key0, I.key1);
+    const int G = P >> 3;
+    int lg = 0;
+    while ((1 << lg) < G) ++lg;
+    const int gmask = (1 << lg) - 1;
+    const int bar = 1 + grp;
+    uint32_t* thr_g = s_thr + (size_t)grp * L.thr_words;
+    long long* red_g = s_red + (size_t)grp * (gsize / 32) * 3;
+    const int lane = tid & 31, gwarp = gtid >> 5;
+
+    for (int s = 0; s < I.n_sweeps; ++s) {
+        const uint32_t t = (uint32_t)(I.t0 + s);
+        for (int lc = grp; lc < c_count; lc += ngroups) {
+            const int rho = c_begin + lc;
+            int8_t* buf = reinterpret_cast<int8_t*>(s_chains + (size_t)(I.resident ? lc : grp) * L.chain_stride);
+            if (!I.resident) {
+                const int4* cs = reinterpret_cast<const int4*>(I.spins + (size_t)rho * I.slot_stride);
+                int4* cd = reinterpret_cast<int4*>(buf);
+                for (int x = gtid; x < I.slot_stride / 16; x += gsize) cd[x] = cs[x];
+            }
+            const int rung = s_rung[rho];
+            for (int x = gtid; x < I.nL3; x += gsize) thr_g[x] = I.thr[(size_t)rung * I.nL3 + x];
+            named_barrier(bar, gsize);
+            const uint32_t* thr_c = thr_g + 3 * I.Lmax;
+            int sumL = 0, sumC = 0, nf = 0;
+            for (int lev = 0; lev < I.n_levels; ++lev) {
+                const int base = s_loff[lev];
+                const int units = (s_loff[lev + 1] - base) << lg;
+                for (int u = gtid; u < units; u += gsize) {
+                    const int g = u & gmask;
+                    if (g >= G) continue;
+                    const int q = base + (u >> lg);
+                    packed_unit<DC, false>(buf, s_sdesc, s_items[q], nullptr, q, g, G, P, t, (uint32_t)rho, key,
+                                           thr_c, sumL, sumC, nf);
+                }
+                named_barrier(bar, gsize);
+            }
+            int dE = -2 * sumL, dM = -4 * (sumC - nf);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dE += __shfl_xor_sync(0xFFFFFFFFu, dE, o);
+                dM += __shfl_xor_sync(0xFFFFFFFFu, dM, o);
+                nf += __shfl_xor_sync(0xFFFFFFFFu, nf, o);
+            }
+            if (lane == 0) {
+                red_g[gwarp * 3 + 0] = dE;
+                red_g[gwarp * 3 + 1] = dM;
+                red_g[gwarp * 3 + 2] = nf;
+            }
+            if (!I.resident) {
+                int4* cd = reinterpret_cast<int4*>(I.spins + (size_t)rho * I.slot_stride);
+                const int4* cs = reinterpret_cast<const int4*>(buf);
+                for (int x = gtid; x < I.slot_stride / 16; x += gsize) cd[x] = cs[x];
+            }
+            named_barrier(bar, gsize);
+            if (gtid == 0) {
+                long long sE = 0, sM = 0, sF = 0;
+                for (int w = 0; w < gsize / 32; ++w) {
+                    sE += red_g[w * 3 + 0];
+                    sM += red_g[w * 3 + 1];
+                    sF += red_g[w * 3 + 2];
+                }
+                const long long E = s_E[lc] + sE, M = s_M[lc] + sM;
+                s_E[lc] = E;
+                s_M[lc] = M;
+                unsigned long long* a = I.acc + (size_t)rung * kAccCount;
+                atomicAdd(a + kAccN, 1ull);
+                atomicAdd(a + kAccE, (unsigned long long)E);
+                atomicAdd(a + kAccE2, (unsigned long long)(E * E));
+                atomicAdd(a + kAccM, (unsigned long long)M);
+                atomicAdd(a + kAccM2, (unsigned long long)(M * M));
+                atomicAdd(a + kAccFlip, (unsigned long long)sF);
+            }
+            named_barrier(bar, gsize);
+        }
+        __syncthreads();
+        if (I.sweeps_per_swap > 0 && (s + 1) % I.sweeps_per_swap == 0) {
+            const int pass = (s + 1) / I.sweeps_per_swap - 1;
+            const long long q = I.q0 + pass;
+            const int pb = pass & 1;
+            for (int lc = tid; lc < c_count; lc += nt) s_pub[pb * C + lc] = make_longlong2(s_E[lc], s_M[lc]);
+            cluster.sync();
+            for (int rl = (int)(q & 1) + 2 * tid; rl + 1 < R; rl += 2 * nt) {
+                const int X = s_slot[rl], Y = s_slot[rl + 1];
+                const longlong2 px = cluster.map_shared_rank(s_pub, X / C)[pb * C + X % C];
+                const longlong2 py = cluster.map_shared_rank(s_pub, Y / C)[pb * C + Y % C];
+                const bool acc = swap_accept_fast(px.x, py.x, px.y, py.y, I.coef[rl], I.coef[(R - 1) + rl],
+                                                  (uint32_t)q, (uint32_t)rl, key, false);
+                if (rank == 0) {
+                    atomicAdd(I.swap_stats + 2 * rl, 1ull);
+                    if (acc) atomicAdd(I.swap_stats + 2 * rl + 1, 1ull);
+                }
+                if (acc) {
+                    s_slot[rl] = Y;
+                    s_slot[rl + 1] = X;
+                    s_rung[X] = rl + 1;
+                    s_rung[Y] = rl;
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- write the problem back
+    for (int x = tid; x < c_count; x += nt) {
+        I.E[c_begin + x] = s_E[x];
+        I.M[c_begin + x] = s_M[x];
+    }
+    if (I.resident) {
+        const int n16 = I.slot_stride / 16;
+        for (int lc = 0; lc < c_count; ++lc) {
+            int4* cd = reinterpret_cast<int4*>(I.spins + (size_t)(c_begin + lc) * I.slot_stride);
+            const int4* cs = reinterpret_cast<const int4*>(s_chains + (size_t)lc * L.chain_stride);
+            for (int x = tid; x < n16; x += nt) cd[x] = cs[x];
+        }
+    }
+    if (rank == 0) {
+        for (int x = tid; x < R; x += nt) {
+            I.rung_of_slot[x] = s_rung[x];
+            I.slot_of_rung[x] = s_slot[x];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(512, 1) batch_kernel(BatchParams bp) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_job;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int K = (int)cluster.num_blocks();
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) s_job = atomicAdd(bp.next_job, 1);
+        cluster.sync();
+        const int job = *cluster.map_shared_rank(&s_job, 0);
+        cluster.sync();  // every CTA has read the job before rank 0 may reuse or release s_job
+        if (job >= bp.count) break;
+        const BatchInstance I = bp.inst[bp.order[job]];
+        if (I.dc == 4)
+            run_problem<4>(I, smem, cluster, rank, K);
+        else
+            run_problem<8>(I, smem, cluster, rank, K);
+        cluster.sync();  // peers are done reading this CTA's published (E, M)
+    }
+}
+
+// Initial spins and (E, M) of every chain of every problem: block b handles chain map[b].
+__global__ void batch_init_kernel(const BatchInstance* inst, const int2* map) {
+    __shared__ long long red[2][32];
+    const int2 m = map[blockIdx.x];
+    const BatchInstance& I = inst[m.x];
+    const int rho = m.y;
+    const PhiloxKey key = philox_schedule(I.key0, I.key1);
+    int8_t* sp = I.spins + (size_t)rho * I.slot_stride;
+    const int P4 = (I.P + 3) >> 2;
+    for (int x = threadIdx.x; x < I.N * P4; x += blockDim.x) {
+        const int i = x / P4, g4 = x - i * P4;
+        const uint4 u = philox(make_uint4(0u, (uint32_t)i, (uint32_t)rho, (kTagInit << 28) | (uint32_t)g4), key);
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int k = 4 * g4 + b;
+            if (k < I.P) sp[(size_t)i * I.P + k] = (w[b] >> 31) ? (int8_t)-1 : (int8_t)1;
+        }
+    }
+    if (threadIdx.x == 0) {
+        I.rung_of_slot[rho] = rho;
+        I.slot_of_rung[rho] = rho;
+    }
+    __syncthreads();
+    // E from the site descriptors: each edge once (neighbour row > own row), h once (the
+    // slot whose row is the constant +1 row)
+    const int DW = I.dc == 4 ? 8 : 12;
+    const uint32_t np = (uint32_t)I.N * (uint32_t)I.P;
+    long long e = 0, mm = 0;
+    for (int x = threadIdx.x; x < I.N * I.P; x += blockDim.x) {
+        const int i = x / I.P, k = x - i * I.P;
+        const uint32_t* d = I.sdesc + (size_t)i * DW;
+        const int si = sp[x];
+        int f = 0;
+        for (int sl = 0; sl < I.dc; ++sl) {
+            const uint32_t row = d[4 + sl];
+            if (row <= d[0]) continue;
+            const int J = (int)(int8_t)((d[2 + (sl >> 2)] >> (8 * (sl & 3))) & 0xFFu);
+            f += J * (row >= np ? 1 : (int)sp[row + k]);
+        }
+        e += (long long)si * f;
+        mm += (long long)si * sp[(size_t)i * I.P + ((k + 1 == I.P) ? 0 : k + 1)];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+        mm += __shfl_xor_sync(0xFFFFFFFFu, mm, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = e;
+        red[1][threadIdx.x >> 5] = mm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long se = 0, sm = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            se += red[0][w];
+            sm += red[1][w];
+        }
+        I.E[rho] = se;
+        I.M[rho] = sm;
+    }
+}
+
+cudaError_t launch_batch(const BatchParams& bp, int cluster, int n_clusters, int threads, size_t smem,
+                         cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster * n_clusters);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    BatchParams p = bp;
+    return cudaLaunchKernelEx(&cfg, batch_kernel, p);
+}
+
+cudaError_t batch_max_clusters(int cluster, int threads, size_t smem, int* n_clusters) {
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(n_clusters, (void*)batch_kernel, &cfg);
+}
+
+cudaError_t launch_batch_init(const BatchInstance* inst, const int2* map, int n_chains, cudaStream_t s) {
+    batch_init_kernel<<<n_chains, 256, 0, s>>>(inst, map);
+    return cudaGetLastError();
+}
+
+}  // namespace ptq
+
+// ===================================================================================== host
+using namespace ptq;
+
+struct pt_batch {
+    int count;
+    cudaStream_t stream;
+    bool own_stream;
+    int cluster, threads, n_clusters;
+    size_t smem;
+    std::vector<void*> allocs;
+    int64_t device_bytes, launches, h2d_bytes;
+    BatchInstance* d_inst;
+    int32_t* d_order;
+    int* d_counter;
+    int* d_status;
+    int8_t* d_staging;
+    std::vector<BatchInstance> h_inst;
+    std::vector<long long> sweep_limit;
+    int err;
+    char msg[256];
+};
+
+static thread_local char g_batch_create_msg[256] = "";
+
+static int bfail(pt_batch* b, int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b ? b->msg : g_batch_create_msg, 256, fmt, ap);
+    va_end(ap);
+    if (b && (code == PT_ECUDA || code == PT_ETIMEDOUT)) b->err = code;
+    return code;
+}
+
+static void free_batch(pt_batch* b) {
+    for (void* p : b->allocs) cudaFree(p);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+template <typename T>
+static cudaError_t balloc(pt_batch* b, T** ptr, size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return e;
+    b->allocs.push_back(p);
+    b->device_bytes += (int64_t)std::max<size_t>(bytes, 16);
+    *ptr = (T*)p;
+    return cudaSuccess;
+}
+
+namespace {
+// Host-side preparation of one request, in the packed layout of the batched kernel.
+struct Prepared {
+    int N, P, R, Lmax, dc, n_levels, slot_stride;
+    std::vector<uint32_t> sdesc, items, thr;
+    std::vector<int32_t> level_off;
+    std::vector<double> coef;
+    size_t off_sdesc, off_items, off_loff, off_thr, off_coef, off_spins, off_E, off_M, off_rung, off_slot, off_acc,
+        off_sw;
+    long long sweep_limit;
+};
+
+int prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len) {
+    const pt_instance* inst = &r.inst;
+    const int N = inst->n, nE = inst->n_edges, P = r.P, R = r.R;
+    if (N < 1 || N > 65535 || nE < 0 || !inst->h || (nE > 0 && (!inst->ei || !inst->ej || !inst->J))) {
+        snprintf(why, why_len, "bad instance arrays");
+        return PT_EINVAL;
+    }
+    if (P < 8 || P % 8 || P > 4096) {
+        snprintf(why, why_len, "batched problems need P %% 8 == 0 and 8 <= P <= 4096");
+        return PT_EINVAL;
+    }
+    if (R < 1 || R > 1024 || !r.ladder) {
+        snprintf(why, why_len, "batched problems need 1 <= R <= 1024 rungs");
+        return PT_EINVAL;
+    }
+    if (r.n_sweeps < 0 || r.n_sweeps > (1ll << 30) || r.sweeps_per_swap < 0) {
+        snprintf(why, why_len, "n_sweeps must be in [0, 2^30] and sweeps_per_swap >= 0");
+        return PT_EINVAL;
+    }
+    for (int q = 0; q < R; ++q)
+        if (!(r.ladder[q].T > 0.0) || !(r.ladder[q].gamma > 0.0)) {
+            snprintf(why, why_len, "rung %d: T and gamma must be > 0", q);
+            return PT_EINVAL;
+        }
+    std::vector<std::vector<int>> adj(N), adjJ(N);
+    long long eb = 0;
+    for (int b = 0; b < nE; ++b) {
+        const int u = inst->ei[b], v = inst->ej[b], J = inst->J[b];
+        if (u < 0 || u >= N || v < 0 || v >= N || u == v || J == 0 || J < -127 || J > 127) {
+            snprintf(why, why_len, "edge %d invalid", b);
+            return PT_EINVAL;
+        }
+        adj[u].push_back(v);
+        adjJ[u].push_back(J);
+        adj[v].push_back(u);
+        adjJ[v].push_back(J);
+        eb += abs(J);
+    }
+    int dmax = 0, Lmax = 0;
+    for (int i = 0; i < N; ++i) {
+        std::vector<int> sorted = adj[i];
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+            snprintf(why, why_len, "duplicate edge at site %d", i);
+            return PT_EINVAL;
+        }
+        dmax = std::max(dmax, (int)adj[i].size());
+        int l = abs(inst->h[i]);
+        for (int J : adjJ[i]) l += abs(J);
+        if (l > 127) {
+            snprintf(why, why_len, "site %d: |h| + sum |J| > 127", i);
+            return PT_EINVAL;
+        }
+        Lmax = std::max(Lmax, l);
+        eb += abs(inst->h[i]);
+    }
+    if (dmax + 1 > 8) {
+        snprintf(why, why_len, "batched problems need degree <= 7");
+        return PT_EINVAL;
+    }
+    eb *= P;
+    const long long mb = (long long)N * P;
+    if (eb >= (1ll << 39) || mb >= (1ll << 31)) {
+        snprintf(why, why_len, "energy or Trotter sum too large");
+        return PT_EINVAL;
+    }
+    const long long big = std::max(std::max(eb, mb), 1ll);
+    pr.sweep_limit = std::min<long long>(big > 3037000499ll ? 0 : 9223372036854775807ll / (big * big), 0xFFFFFFFFll);
+    pr.N = N;
+    pr.P = P;
+    pr.R = R;
+    pr.Lmax = Lmax;
+    pr.dc = (dmax + 1 <= 4) ? 4 : 8;
+    pr.slot_stride = (int)(((size_t)N * P + 15) & ~(size_t)15);
+    build_tables(R, P, Lmax, r.ladder, pr.thr, pr.coef);
+    if (pr.coef.size() < 2) pr.coef.assign(2, 0.0);
+    level_schedule(N, adj, pr.items, pr.level_off);
+    pr.n_levels = (int)pr.level_off.size() - 1;
+    build_site_desc(N, P, pr.dc, adj, adjJ, inst->h, pr.sdesc);
+    return PT_OK;
+}
+}  // namespace
+
+extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_options* opt, void* cuda_stream,
+                               pt_batch** out) {
+    if (!reqs || !out || count < 1) return bfail(nullptr, PT_EINVAL, "need at least one request");
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) return bfail(nullptr, PT_ENODEV, "no CUDA device");
+    std::vector<Prepared> pr(count);
+    char why[200];
+    for (int k = 0; k < count; ++k) {
+        const int rc = prepare_request(reqs[k], pr[k], why, sizeof(why));
+        if (rc) return bfail(nullptr, rc, "request %d: %s", k, why);
+    }
+    pt_batch* b = new pt_batch();
+    b->count = count;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->own_stream = false;
+    b->device_bytes = b->launches = b->h2d_bytes = 0;
+    b->err = 0;
+    b->msg[0] = 0;
+    if (!b->stream) {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return bfail(nullptr, PT_ECUDA, "cudaStreamCreate failed");
+        }
+        b->own_stream = true;
+    }
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t smem_cap = (size_t)max_smem - 1024;  // room for the kernel's static shared memory
+    b->threads = 512;
+    b->cluster = (opt && opt->cluster_size > 0) ? opt->cluster_size : 4;
+    if (b->cluster > 16) {
+        free_batch(b);
+        return bfail(nullptr, PT_EINVAL, "cluster_size must be <= 16");
+    }
+
+    // device layout of every request in one arena: constants first, then state
+    b->h_inst.resize(count);
+    b->sweep_limit.resize(count);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    size_t max_state = 0, smem = 0;
+    for (int k = 0; k < count; ++k) {
+        Prepared& p = pr[k];
+        p.off_sdesc = take(p.sdesc.size() * 4);
+        p.off_items = take(p.items.size() * 4);
+        p.off_loff = take(p.level_off.size() * 4);
+        p.off_thr = take(p.thr.size() * 4);
+        p.off_coef = take(p.coef.size() * 8);
+    }
+    const size_t const_bytes = off;
+    for (int k = 0; k < count; ++k) {
+        Prepared& p = pr[k];
+        p.off_spins = take((size_t)p.R * p.slot_stride);
+        p.off_E = take((size_t)p.R * 8);
+        p.off_M = take((size_t)p.R * 8);
+        p.off_rung = take((size_t)p.R * 4);
+        p.off_slot = take((size_t)p.R * 4);
+        p.off_acc = take((size_t)p.R * kAccCount * 8);
+        p.off_sw = take((size_t)p.R * 16);
+        max_state = std::max(max_state, (size_t)p.R * p.N * p.P);
+        BatchInstance& I = b->h_inst[k];
+        memset(&I, 0, sizeof(I));
+        I.N = p.N;
+        I.P = p.P;
+        I.R = p.R;
+        I.Lmax = p.Lmax;
+        I.nL3 = (2 * p.Lmax + 1) * 3;
+        I.n_levels = p.n_levels;
+        I.dc = p.dc;
+        I.slot_stride = p.slot_stride;
+        I.key0 = (uint32_t)(reqs[k].seed & 0xFFFFFFFFu);
+        I.key1 = (uint32_t)(reqs[k].seed >> 32);
+        I.n_sweeps = (int)reqs[k].n_sweeps;
+        I.sweeps_per_swap = reqs[k].sweeps_per_swap;
+        b->sweep_limit[k] = p.sweep_limit;
+        // threads per chain: about one 4-copy unit per thread in an average level, at
+        // least two warps, and no more groups than this CTA has chains
+        const long long units = 2ll * p.N * (p.P / 8);
+        const long long avg = (units + p.n_levels - 1) / p.n_levels;
+        const int C = (p.R + b->cluster - 1) / b->cluster;
+        int g = 64;
+        while (g < 512 && g < avg) g <<= 1;
+        while (g < 512 && b->threads / g > C) g <<= 1;
+        I.group_threads = g;
+        I.resident = 1;
+        if (batch_smem_bytes(I, b->cluster, b->threads) > smem_cap) I.resident = 0;
+        const size_t need = batch_smem_bytes(I, b->cluster, b->threads);
+        if (need > smem_cap) {
+            free_batch(b);
+            return bfail(nullptr, PT_EINVAL, "request %d needs %zu bytes of shared memory per CTA (device: %zu)", k,
+                         need, smem_cap);
+        }
+        smem = std::max(smem, need);
+    }
+    b->smem = smem;
+
+    unsigned char* arena = nullptr;
+    cudaError_t e;
+    if ((e = balloc(b, &arena, off)) != cudaSuccess || (e = balloc(b, &b->d_inst, sizeof(BatchInstance) * count)) ||
+        (e = balloc(b, &b->d_order, sizeof(int32_t) * count)) || (e = balloc(b, &b->d_counter, 16)) ||
+        (e = balloc(b, &b->d_status, 16)) || (e = balloc(b, &b->d_staging, max_state))) {
+        free_batch(b);
+        return bfail(nullptr, e == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA, "cudaMalloc: %s",
+                     cudaGetErrorString(e));
+    }
+    std::vector<unsigned char> host_const(const_bytes, 0);
+    std::vector<int2> map;
+    for (int k = 0; k < count; ++k) {
+        Prepared& p = pr[k];
+        memcpy(&host_const[p.off_sdesc], p.sdesc.data(), p.sdesc.size() * 4);
+        memcpy(&host_const[p.off_items], p.items.data(), p.items.size() * 4);
+        memcpy(&host_const[p.off_loff], p.level_off.data(), p.level_off.size() * 4);
+        memcpy(&host_const[p.off_thr], p.thr.data(), p.thr.size() * 4);
+        memcpy(&host_const[p.off_coef], p.coef.data(), p.coef.size() * 8);
+        BatchInstance& I = b->h_inst[k];
+        I.sdesc = (const uint32_t*)(arena + p.off_sdesc);
+        I.items = (const uint32_t*)(arena + p.off_items);
+        I.level_off = (const int32_t*)(arena + p.off_loff);
+        I.thr = (const uint32_t*)(arena + p.off_thr);
+        I.coef = (const double*)(arena + p.off_coef);
+        I.spins = (int8_t*)(arena + p.off_spins);
+        I.E = (long long*)(arena + p.off_E);
+        I.M = (long long*)(arena + p.off_M);
+        I.rung_of_slot = (int32_t*)(arena + p.off_rung);
+        I.slot_of_rung = (int32_t*)(arena + p.off_slot);
+        I.acc = (unsigned long long*)(arena + p.off_acc);
+        I.swap_stats = (unsigned long long*)(arena + p.off_sw);
+        for (int rho = 0; rho < p.R; ++rho) map.push_back(make_int2(k, rho));
+    }
+    // requests with the most work first, so the last ones to finish are small
+    std::vector<int32_t> order(count);
+    for (int k = 0; k < count; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        const double wa = (double)pr[a].N * pr[a].P * pr[a].R * (double)reqs[a].n_sweeps;
+        const double wc = (double)pr[c].N * pr[c].P * pr[c].R * (double)reqs[c].n_sweeps;
+        return wa > wc;
+    });
+    int2* d_map = nullptr;
+    cudaStream_t s = b->stream;
+    if ((e = balloc(b, &d_map, map.size() * sizeof(int2))) != cudaSuccess ||
+        (e = cudaMemcpyAsync(arena, host_const.data(), const_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(arena + const_bytes, 0, off - const_bytes, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(BatchInstance) * count, cudaMemcpyHostToDevice,
+                             s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->d_order, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(d_map, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(b->d_status, 0, 16, s)) != cudaSuccess ||
+        (e = launch_batch_init(b->d_inst, d_map, (int)map.size(), s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        free_batch(b);
+        return bfail(nullptr, PT_ECUDA, "batch setup: %s", cudaGetErrorString(e));
+    }
+    b->launches += 1;
+    b->h2d_bytes += (int64_t)(const_bytes + sizeof(BatchInstance) * count + sizeof(int32_t) * count +
+                              map.size() * sizeof(int2));
+    int ncl = 0;
+    if ((e = batch_max_clusters(b->cluster, b->threads, b->smem, &ncl)) != cudaSuccess || ncl < 1) {
+        free_batch(b);
+        return bfail(nullptr, PT_EINVAL, "no cluster of %d CTAs with %zu bytes of shared memory fits (%s)", b->cluster,
+                     b->smem, cudaGetErrorString(e));
+    }
+    b->n_clusters = std::min(ncl, count);
+    *out = b;
+    return PT_OK;
+}
+
+static int bguard(pt_batch* b) {
+    if (!b) return PT_EINVAL;
+    return b->err;
+}
+
+static int bcheck(pt_batch* b) {
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, PT_ECUDA, "CUDA error: %s", cudaGetErrorString(e));
+    if (st) return bfail(b, PT_ECUDA, "device status %d", st);
+    return PT_OK;
+}
+
+extern "C" int pt_batch_run(pt_batch* b) {
+    int g = bguard(b);
+    if (g) return g;
+    for (int k = 0; k < b->count; ++k) {
+        const BatchInstance& I = b->h_inst[k];
+        const long long passes = I.sweeps_per_swap > 0 ? I.n_sweeps / I.sweeps_per_swap : 0;
+        if (I.t0 + I.n_sweeps > b->sweep_limit[k] || I.q0 + passes > 0xFFFFFFFFll)
+            return bfail(b, PT_EOVERFLOW, "request %d: sweep or pass counter would overflow", k);
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(BatchInstance) * b->count, cudaMemcpyHostToDevice,
+                             b->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream)) != cudaSuccess)
+        return bfail(b, PT_ECUDA, "%s", cudaGetErrorString(e));
+    BatchParams bp;
+    bp.inst = b->d_inst;
+    bp.order = b->d_order;
+    bp.count = b->count;
+    bp.next_job = b->d_counter;
+    bp.status = b->d_status;
+    if ((e = launch_batch(bp, b->cluster, b->n_clusters, b->threads, b->smem, b->stream)) != cudaSuccess)
+        return bfail(b, PT_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+    b->launches += 1;
+    b->h2d_bytes += (int64_t)(sizeof(BatchInstance) * b->count);
+    for (int k = 0; k < b->count; ++k) {
+        BatchInstance& I = b->h_inst[k];
+        I.t0 += I.n_sweeps;
+        if (I.sweeps_per_swap > 0) I.q0 += I.n_sweeps / I.sweeps_per_swap;
+    }
+    // the host copy changes only after the asynchronous upload above has been consumed
+    // by cudaMemcpyAsync (pageable source: copied before the call returns)
+    return PT_OK;
+}
+
+extern "C" int pt_batch_sync(pt_batch* b) {
+    int g = bguard(b);
+    if (g) return g;
+    return bcheck(b);
+}
+
+extern "C" int pt_batch_read_state(pt_batch* b, int32_t index, int8_t* out, size_t bytes) {
+    int g = bguard(b);
+    if (g) return g;
+    if (index < 0 || index >= b->count) return bfail(b, PT_EINVAL, "index out of range");
+    const BatchInstance& I = b->h_inst[index];
+    const size_t need = (size_t)I.R * I.N * I.P;
+    if (!out || bytes < need) return bfail(b, PT_EINVAL, "state buffer needs %zu bytes", need);
+    DevProblem p;
+    memset(&p, 0, sizeof(p));
+    p.spins = I.spins;
+    p.slot_of_rung = I.slot_of_rung;
+    p.N = I.N;
+    p.P = I.P;
+    p.R = I.R;
+    p.slot_stride = I.slot_stride;
+    cudaError_t e;
+    if ((e = launch_gather_state(p, b->d_staging, b->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(out, b->d_staging, need, cudaMemcpyDeviceToHost, b->stream)) != cudaSuccess)
+        return bfail(b, PT_ECUDA, "%s", cudaGetErrorString(e));
+    b->launches += 1;
+    return bcheck(b);
+}
+
+extern "C" int pt_batch_read_observables(pt_batch* b, int32_t index, pt_observables* o) {
+    int g = bguard(b);
+    if (g) return g;
+    if (index < 0 || index >= b->count || !o) return bfail(b, PT_EINVAL, "bad index or null observables");
+    const BatchInstance& I = b->h_inst[index];
+    const int R = I.R;
+    std::vector<long long> E(R), M(R);
+    std::vector<int32_t> slot_of(R);
+    std::vector<unsigned long long> acc((size_t)R * kAccCount), sw(2 * (size_t)R);
+    cudaStream_t s = b->stream;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(E.data(), I.E, R * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(M.data(), I.M, R * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(slot_of.data(), I.slot_of_rung, R * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(acc.data(), I.acc, acc.size() * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(sw.data(), I.swap_stats, sw.size() * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return bfail(b, PT_ECUDA, "%s", cudaGetErrorString(e));
+    int rc = bcheck(b);
+    if (rc) return rc;
+    o->t = I.t0;
+    o->q = I.q0;
+    for (int r = 0; r < R; ++r) {
+        const int slot = slot_of[r];
+        if (o->E) o->E[r] = E[slot];
+        if (o->M) o->M[r] = M[slot];
+        const unsigned long long* a = &acc[(size_t)r * kAccCount];
+        if (o->n_meas) o->n_meas[r] = (int64_t)a[kAccN];
+        if (o->sum_E) o->sum_E[r] = (int64_t)a[kAccE];
+        if (o->sum_E2) o->sum_E2[r] = (int64_t)a[kAccE2];
+        if (o->sum_M) o->sum_M[r] = (int64_t)a[kAccM];
+        if (o->sum_M2) o->sum_M2[r] = (int64_t)a[kAccM2];
+        if (o->flip_acc) o->flip_acc[r] = (int64_t)a[kAccFlip];
+        if (o->replica_at) o->replica_at[r] = slot;
+    }
+    for (int r = 0; r + 1 < R; ++r) {
+        if (o->swap_att) o->swap_att[r] = (int64_t)sw[2 * r];
+        if (o->swap_acc) o->swap_acc[r] = (int64_t)sw[2 * r + 1];
+    }
+    return PT_OK;
+}
+
+extern "C" int pt_batch_get_info(const pt_batch* b, pt_batch_info* o) {
+    if (!b || !o) return PT_EINVAL;
+    o->count = b->count;
+    o->cluster = b->cluster;
+    o->n_clusters = b->n_clusters;
+    o->threads_per_block = b->threads;
+    o->smem_bytes = (int64_t)b->smem;
+    o->device_bytes = b->device_bytes;
+    o->kernel_launches = b->launches;
+    o->h2d_bytes = b->h2d_bytes;
+    return PT_OK;
+}
+
+extern "C" int pt_batch_destroy(pt_batch* b) {
+    if (!b) return PT_OK;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    return PT_OK;
+}
+
+extern "C" const char* pt_batch_last_error(const pt_batch* b) { return b ? b->msg : g_batch_create_msg; }

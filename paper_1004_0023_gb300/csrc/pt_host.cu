@@ -68,7 +68,7 @@ static int create_fail(int code, const char* fmt, ...) {
 // min(floor(exp(x)*2^32), 0xFFFFFFFF); for swaps a_r = beta_r/P - beta_{r+1}/P and
 // c_r = K_{r+1} - K_r. Flipping copy k of site i changes the action S by
 // -(2 beta/P) L + 2 K m, with L = s(h + sum J s_j) and m = s(s^{k-1} + s^{k+1}).
-static void build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vector<uint32_t>& thr,
+void ptq::build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vector<uint32_t>& thr,
                          std::vector<double>& coef) {
     const int nL = 2 * Lmax + 1;
     thr.assign((size_t)R * nL * 3, 0u);
@@ -107,7 +107,7 @@ static void build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vec
 // where (i, p) updates every copy of parity p of site i. Two updates conflict only if
 // they are (i,0) and (i,1), or (i,p) and (j,p) with i, j adjacent; the level of an update
 // is one more than the largest level of the earlier updates it conflicts with.
-static void level_schedule(int N, const std::vector<std::vector<int>>& adj, std::vector<uint32_t>& items,
+void ptq::level_schedule(int N, const std::vector<std::vector<int>>& adj, std::vector<uint32_t>& items,
                            std::vector<int32_t>& level_off) {
     std::vector<int> l0(N), l1(N);
     int nlev = 0;
@@ -138,6 +138,34 @@ static void level_schedule(int N, const std::vector<std::vector<int>>& adj, std:
 }
 
 // ---------------------------------------------------------------------------------
+// Packed-path site descriptors (see SiteDesc in pt_kernels.cu).
+void ptq::build_site_desc(int N, int P, int dclass, const std::vector<std::vector<int>>& adj,
+                            const std::vector<std::vector<int>>& adjJ, const int32_t* h, std::vector<uint32_t>& desc) {
+    const int DW = dclass == 4 ? 8 : 12;
+    const uint32_t ones_row = (uint32_t)(((size_t)N * P + 15) & ~(size_t)15);
+    desc.assign((size_t)N * DW, 0u);
+    for (int i = 0; i < N; ++i) {
+        uint32_t* d = &desc[(size_t)i * DW];
+        d[0] = (uint32_t)i * (uint32_t)P;
+        d[1] = (uint32_t)i;
+        uint32_t jp[2] = {0u, 0u};
+        for (int s8 = 0; s8 < dclass; ++s8) {
+            int J = 0;
+            uint32_t r = ones_row;
+            if (s8 < (int)adj[i].size()) {
+                J = adjJ[i][s8];
+                r = (uint32_t)adj[i][s8] * (uint32_t)P;
+            } else if (s8 == (int)adj[i].size()) {
+                J = h[i];
+            }
+            d[4 + s8] = r;
+            jp[s8 / 4] |= (uint32_t)(uint8_t)(int8_t)J << (8 * (s8 % 4));
+        }
+        d[2] = jp[0];
+        d[3] = jp[1];
+    }
+}
+
 template <typename T>
 static cudaError_t dev_alloc(pt_ctx* c, T** ptr, size_t count) {
     void* p = nullptr;
@@ -354,39 +382,12 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         c->plan.n_consumer = c->plan.threads - prod;
     }
 
-    // packed-path unit descriptors, one per schedule position q: row offset of site i,
-    // i | parity << 31, packed J bytes, then the row offsets of the neighbours; the slot
-    // after the last neighbour carries h against a constant row of +1 copies.
+    // packed-path site descriptors: row offset i*P, i, packed J bytes (two words), then the
+    // row offsets of the neighbour slots; the slot after the last neighbour carries h
+    // against a constant row of +1 copies, the remaining slots have J = 0.
     std::vector<uint32_t> desc;
-    if (path != kPathGeneric) {
-        const int DW = c->plan.dclass == 4 ? 8 : 16;
-        const uint32_t ones_row = (uint32_t)(((size_t)N * P + 15) & ~(size_t)15);
-        desc.assign((size_t)2 * N * DW, 0u);
-        for (size_t qpos = 0; qpos < items.size(); ++qpos) {
-            const int i = (int)(items[qpos] >> 1);
-            const uint32_t par = items[qpos] & 1u;
-            uint32_t* d = &desc[qpos * DW];
-            d[0] = (uint32_t)i * (uint32_t)P;
-            d[1] = (uint32_t)i | (par << 31);
-            uint32_t jp[2] = {0u, 0u};
-            uint32_t nr[8];
-            for (int s8 = 0; s8 < c->plan.dclass; ++s8) {
-                int J = 0;
-                uint32_t r = ones_row;
-                if (s8 < (int)adj[i].size()) {
-                    J = adjJ[i][s8];
-                    r = (uint32_t)adj[i][s8] * (uint32_t)P;
-                } else if (s8 == (int)adj[i].size()) {
-                    J = inst->h[i];
-                }
-                nr[s8] = r;
-                jp[s8 / 4] |= (uint32_t)(uint8_t)(int8_t)J << (8 * (s8 % 4));
-            }
-            d[2] = jp[0];
-            d[3] = jp[1];
-            for (int s8 = 0; s8 < c->plan.dclass; ++s8) d[4 + s8] = nr[s8];
-        }
-    }
+    if (path != kPathGeneric)
+        build_site_desc(N, P, c->plan.dclass, adj, adjJ, inst->h, desc);
 
     // overflow guard: |E| <= P * (sum|J| + sum|h|), |M| <= N*P; sum of squares stays in int64
     {

@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
+#include "pt.h"
+
 namespace ptq {
 
 // Stream tags in the top nibble of Philox counter word 3.
@@ -72,6 +76,38 @@ struct LaunchPlan {
 // Sizes of the dynamic shared-memory carve-up of the sweep kernel for a path.
 size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass);
 
+// One request of a batched launch (device view). Every chain of the request is swept by
+// one CTA of the thread-block cluster that takes the request; the cluster's CTAs split the
+// chains and exchange (E, M) through distributed shared memory for the swap passes.
+struct BatchInstance {
+    const uint32_t* sdesc;     // [N][DW] packed-path site descriptors
+    const uint32_t* items;     // [2N] schedule, grouped by level
+    const int32_t* level_off;  // [n_levels + 1]
+    const uint32_t* thr;       // [R][nL3]
+    const double* coef;        // [2(R-1)] (at least 2 entries)
+    int8_t* spins;             // [R][slot_stride]
+    long long* E;              // [R] by replica
+    long long* M;
+    int32_t* rung_of_slot;     // [R]
+    int32_t* slot_of_rung;     // [R]
+    unsigned long long* acc;   // [R][kAccCount] by rung
+    unsigned long long* swap_stats;  // [R][2] by pair
+    int N, P, R, Lmax, nL3, n_levels, dc, slot_stride;
+    int group_threads;         // threads sweeping one chain (a divisor of the CTA size)
+    int resident;              // 1: a CTA keeps all its chains in shared memory for the run
+    uint32_t key0, key1;
+    long long t0, q0;          // counters before this run
+    int n_sweeps, sweeps_per_swap;
+};
+
+struct BatchParams {
+    const BatchInstance* inst;  // [count]
+    const int32_t* order;       // [count] request indices, most work first
+    int count;
+    int* next_job;              // work counter, zero at launch
+    int* status;
+};
+
 // Kernel launchers (pt_kernels.cu). Each returns a cudaError_t from the launch.
 cudaError_t launch_init(const DevProblem& p, cudaStream_t s);
 cudaError_t launch_energy(const DevProblem& p, cudaStream_t s);
@@ -83,5 +119,20 @@ cudaError_t launch_gather_state(const DevProblem& p, int8_t* out, cudaStream_t s
 cudaError_t launch_scatter_state(const DevProblem& p, const int8_t* in, cudaStream_t s);
 cudaError_t sweep_kernel_occupancy(const DevProblem& p, const LaunchPlan& plan, int* blocks_per_sm);
 cudaError_t prepare_sweep_kernel(const LaunchPlan& plan);
+
+// Host-side preparation shared by single and batched problems (pt_host.cu).
+void build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vector<uint32_t>& thr,
+                  std::vector<double>& coef);
+void level_schedule(int N, const std::vector<std::vector<int>>& adj, std::vector<uint32_t>& items,
+                    std::vector<int32_t>& level_off);
+void build_site_desc(int N, int P, int dclass, const std::vector<std::vector<int>>& adj,
+                     const std::vector<std::vector<int>>& adjJ, const int32_t* h, std::vector<uint32_t>& desc);
+
+// Batched launchers (pt_batch.cu).
+size_t batch_smem_bytes(const BatchInstance& I, int cluster, int threads);
+cudaError_t launch_batch(const BatchParams& bp, int cluster, int n_clusters, int threads, size_t smem,
+                         cudaStream_t s);
+cudaError_t batch_max_clusters(int cluster, int threads, size_t smem, int* n_clusters);
+cudaError_t launch_batch_init(const BatchInstance* inst, const int2* map, int n_chains, cudaStream_t s);
 
 }  // namespace ptq

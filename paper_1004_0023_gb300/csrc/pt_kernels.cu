@@ -18,152 +18,13 @@
 #include <stdint.h>
 
 #include "pt.h"
+#include "pt_device.cuh"
 #include "pt_internal.h"
 
 namespace ptq {
 
-// ------------------------------------------------------------------------- Philox4x32-10
-// Salmon, Moraes, Dror, Shaw, SC'11: round (c0,c1,c2,c3) -> (hi(M1 c2)^c1^k0, lo(M1 c2),
-// hi(M0 c0)^c3^k1, lo(M0 c0)); the round-r key is (k0 + r W0, k1 + r W1).
-struct PhiloxKey {
-    uint32_t k0[10];
-    uint32_t k1[10];
-};
-
-__device__ __forceinline__ PhiloxKey philox_schedule(uint32_t key0, uint32_t key1) {
-    PhiloxKey k;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        k.k0[r] = key0 + (uint32_t)r * 0x9E3779B9u;
-        k.k1[r] = key1 + (uint32_t)r * 0xBB67AE85u;
-    }
-    return k;
-}
-
-__device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKey& k) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
-        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.k0[r], (uint32_t)p1,
-                       (uint32_t)(p0 >> 32) ^ c.w ^ k.k1[r], (uint32_t)p0);
-    }
-    return c;
-}
-
-// ------------------------------------------------------------------------- det_exp
-// exp(x) for x in (-23, 0] from IEEE round-to-nearest basic operations only (Cody & Waite
-// argument reduction with a two-part ln 2, then the degree-13 Taylor series of exp by
-// Horner's rule, then an exact scaling by 2^n). Each operation is an explicit _rn
-// intrinsic so no multiply-add is fused; the host computes the same sequence.
-__device__ __forceinline__ double det_exp(double x) {
-    const double LN2_HI = 0x1.62e42ff000000p-1;
-    const double LN2_LO = -0x1.718432a1b0e26p-35;
-    const double INV_LN2 = 0x1.71547652b82fep+0;
-    // 1/k! rounded to nearest (k! is exact in double for k <= 13); folded at compile time
-    const double inv_fact[14] = {1.0, 1.0, 1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0,
-                                 1.0 / 5040.0, 1.0 / 40320.0, 1.0 / 362880.0, 1.0 / 3628800.0,
-                                 1.0 / 39916800.0, 1.0 / 479001600.0, 1.0 / 6227020800.0};
-    const double nd = rint(__dmul_rn(x, INV_LN2));
-    const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(nd, LN2_HI)), __dmul_rn(nd, LN2_LO));
-    double poly = inv_fact[13];
-#pragma unroll
-    for (int k = 12; k >= 0; --k) poly = __dadd_rn(__dmul_rn(poly, r), inv_fact[k]);
-    const int n = (int)nd;  // in [-34, 0]
-    const double scale = __hiloint2double((1023 + n) << 20, 0);
-    return __dmul_rn(poly, scale);
-}
-
-// Swap decision for X on rung rl and Y on rung rl + 1 at pass q.
-__device__ __forceinline__ bool swap_accept(long long EX, long long EY, long long MX, long long MY,
-                                            double a, double c, uint32_t q, uint32_t rl,
-                                            const PhiloxKey& key) {
-    const double dE = __ll2double_rn(EX - EY);
-    const double dM = __ll2double_rn(MX - MY);
-    const double delta = __dadd_rn(__dmul_rn(a, dE), __dmul_rn(c, dM));
-    if (delta >= 0.0) return true;
-    if (!(delta > -23.0)) return false;
-    const uint4 u = philox(make_uint4(q, rl, 0u, kTagSwap << 28), key);
-    const double v = floor(__dmul_rn(det_exp(delta), 4294967296.0));
-    const uint32_t ts = (v >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)v;
-    return u.x < ts;
-}
-
-// The same decision without FP64 in the common case. GB300's FP64 pipe makes the ~40
-// dependent FP64 operations of swap_accept cost over a microsecond, so Delta and exp(Delta)
-// are first estimated in FP32 with an error bound:
-//   |D - Delta| <= err = 5*2^-24 * (|a dE| + |c dM|)   (conversions of a, c, dE, dM, two
-//   products, one sum, and the FP64 roundings of Delta itself, with room to spare), and
-//   2^32 exp(D) within a relative 1e-5 + 1.01 err of 2^32 exp(Delta) (expf is within 2 ulp).
-// The estimate decides only when u is farther than that margin (plus float rounding of u)
-// from the threshold, or Delta's sign and the -23 cut are certain; otherwise swap_accept
-// decides. Either way the result equals swap_accept's.
-__device__ __forceinline__ bool swap_accept_fast(long long EX, long long EY, long long MX, long long MY,
-                                                 double a, double c, uint32_t q, uint32_t rl,
-                                                 const PhiloxKey& key, bool exact_only) {
-    if (!exact_only) {
-        const float pa = (float)a * (float)(EX - EY);
-        const float pc = (float)c * (float)(MX - MY);
-        const float D = pa + pc;
-        const float err = (fabsf(pa) + fabsf(pc)) * 2.99e-7f + 1e-30f;
-        if (D >= 2.0f * err) return true;                       // Delta >= 0
-        if (err < 0.25f) {
-            if (D < -23.5f) return false;                         // Delta <= -23
-            if (D + 2.0f * err < 0.0f && D > -22.5f) {
-                const uint4 r4 = philox(make_uint4(q, rl, 0u, kTagSwap << 28), key);
-                const float v = 4294967296.0f * expf(D);
-                const float margin = v * (1.0e-5f + 1.01f * err) + 512.0f;
-                const float uf = (float)r4.x;
-                if (uf + margin < v) return true;
-                if (uf - margin > v) return false;
-            }
-        }
-    }
-    return swap_accept(EX, EY, MX, MY, a, c, q, rl, key);
-}
-
-// ------------------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ long long ld_relaxed_s64(const long long* p) {
-    long long v;
-    asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void st_relaxed_s64(long long* p, long long v) {
-    asm volatile("st.relaxed.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-// prmt.b32 in its generic mode: a selector nibble with its top bit set replicates the
-// sign of the selected byte (used to sign-extend packed int8 spins).
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 // ------------------------------------------------------------------------- smem layouts
-__host__ __device__ inline size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Byte-wise path (any even P, any degree up to 32).
 // Threshold rows and per-rung statistics in shared memory (when they fit).
 __host__ __device__ inline size_t thr_bytes(const DevProblem& p) {
     return up16((size_t)(p.tables_in_smem ? p.R : 1) * p.nL3 * 4);
@@ -172,6 +33,7 @@ __host__ __device__ inline size_t acc_bytes(const DevProblem& p) {
     return p.acc_in_smem ? (size_t)p.R * kAccCount * 8 : 0;
 }
 
+// Byte-wise path (any even P, any degree up to 32).
 struct GenericLayout {
     size_t spins, nbr, h, items, loff, thr, acc, red, ctl, total;
     __host__ __device__ explicit GenericLayout(const DevProblem& p) {
@@ -191,8 +53,8 @@ struct GenericLayout {
 };
 
 // Packed path (P % 8 == 0, degree + 1 <= 8): spins, one row of +1 copies (the field's h
-// slot points at it), per-position unit descriptors, the schedule (read by the random-word
-// producer), level offsets, the threshold row, reduction scratch, control words and, when
+// slot points at it), per-site descriptors, the schedule, level offsets, the threshold
+// row(s), statistics, reduction scratch, control words and, when
 // the random words are produced ahead, two buffers of one sweep's words each.
 struct FastLayout {
     size_t spins, ones, desc, items, loff, thr, acc, red, ctl, rbuf, total;
@@ -201,7 +63,7 @@ struct FastLayout {
         size_t o = 0;
         spins = o; o += up16((size_t)N * P);
         ones = o;  o += up16((size_t)P);
-        desc = o;  o += (size_t)2 * N * (dc == 4 ? 32 : 64);
+        desc = o;  o += (size_t)N * (dc == 4 ? 32 : 48);
         items = o; o += up16((size_t)2 * N * 4);
         loff = o;  o += up16((size_t)(p.n_levels + 1) * 4);
         thr = o;   o += thr_bytes(p);
@@ -219,9 +81,6 @@ size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass) {
     return FastLayout(p, dclass, path == kPathPacked).total;
 }
 
-__device__ __forceinline__ void named_barrier(int id, int count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
 
 // ------------------------------------------------------------------------- end of a sweep
 __device__ __forceinline__ unsigned long long mbox_tag(long long q) {
@@ -483,97 +342,6 @@ __device__ __forceinline__ void produce_words(uint4* buf, uint32_t t, const uint
     }
 }
 
-// One 4-copy unit of the packed path: copies k = 8g + par + 2w (w = 0..3) of site i.
-// Each neighbour row contributes one 8-byte load; the field of the four copies comes from
-// a 4x4 byte transpose and dp4a (the site's h rides in a spare neighbour slot whose spins
-// are the constant +1 row); the Trotter column m/2+1 = 2 - [left differs] - [right differs]
-// is formed for all four copies at once from byte XORs.
-template <int DC, bool PRE>
-__device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* desc, const uint4* rb, int q, int g, int G,
-                                            int P, uint32_t t, uint32_t slot, const PhiloxKey& key,
-                                            const uint32_t* thr_c, int& sumL, int& sumC, int& nflip) {
-    const uint4 d0 = *reinterpret_cast<const uint4*>(desc);
-    const uint32_t row = d0.x;
-    const uint32_t par = d0.y >> 31;
-    const uint32_t c = 8u * (uint32_t)g;
-    uint32_t nrow[DC];
-    uint32_t jpack[DC / 4];
-    {
-        const uint4 d1 = *reinterpret_cast<const uint4*>(desc + 4);
-        nrow[0] = d1.x;
-        nrow[1] = d1.y;
-        nrow[2] = d1.z;
-        nrow[3] = d1.w;
-        jpack[0] = d0.z;
-        if (DC == 8) {
-            const uint4 d2 = *reinterpret_cast<const uint4*>(desc + 8);
-            nrow[DC > 4 ? 4 : 0] = d2.x;
-            nrow[DC > 5 ? 5 : 0] = d2.y;
-            nrow[DC > 6 ? 6 : 0] = d2.z;
-            nrow[DC > 7 ? 7 : 0] = d2.w;
-            jpack[DC > 4 ? 1 : 0] = d0.w;
-        }
-    }
-    const uint2 own = *reinterpret_cast<const uint2*>(sp + row + c);
-    // the one Trotter neighbour outside the chunk: copy c-1 for even copies, c+8 for odd
-    const uint32_t eoff = par ? (c + 8 == (uint32_t)P ? 0u : c + 8) : (c == 0 ? (uint32_t)P - 1 : c - 1);
-    const uint32_t edge = (uint8_t)sp[row + eoff];
-    uint2 nb[DC];
-#pragma unroll
-    for (int d = 0; d < DC; ++d) nb[d] = *reinterpret_cast<const uint2*>(sp + nrow[d] + c);
-    uint4 r4;
-    if (PRE) {
-        r4 = rb[q * G + g];
-    } else {
-        r4 = philox(make_uint4(t, d0.y & 0x7FFFFFFFu, slot, (par << 24) | (uint32_t)g), key);
-    }
-    const uint32_t u[4] = {r4.x, r4.y, r4.z, r4.w};
-
-    const uint32_t selS = par ? 0x7531u : 0x6420u;
-    const uint32_t S = __byte_perm(own.x, own.y, selS);
-    uint32_t Rn = __byte_perm(own.x, own.y, par ? 0x0642u : 0x7531u);
-    Rn = par ? __byte_perm(Rn, edge, 0x4210u) : Rn;
-    uint32_t Ln = __byte_perm(own.x, own.y, par ? 0x6420u : 0x5310u);
-    Ln = par ? Ln : __byte_perm(Ln, edge, 0x3214u);
-    const uint32_t X = (S ^ Ln) & 0x02020202u;
-    const uint32_t Y = (S ^ Rn) & 0x02020202u;
-    const uint32_t Z = 0x02020202u - ((X + Y) >> 1);
-
-    int f[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int b = 0; b < DC / 4; ++b) {
-        const uint32_t a0 = __byte_perm(nb[4 * b + 0].x, nb[4 * b + 0].y, selS);
-        const uint32_t a1 = __byte_perm(nb[4 * b + 1].x, nb[4 * b + 1].y, selS);
-        const uint32_t a2 = __byte_perm(nb[4 * b + 2].x, nb[4 * b + 2].y, selS);
-        const uint32_t a3 = __byte_perm(nb[4 * b + 3].x, nb[4 * b + 3].y, selS);
-        const uint32_t t0 = __byte_perm(a0, a1, 0x5140u), t1 = __byte_perm(a0, a1, 0x7362u);
-        const uint32_t t2 = __byte_perm(a2, a3, 0x5140u), t3 = __byte_perm(a2, a3, 0x7362u);
-        f[0] = __dp4a((int)__byte_perm(t0, t2, 0x5410u), (int)jpack[b], f[0]);
-        f[1] = __dp4a((int)__byte_perm(t0, t2, 0x7632u), (int)jpack[b], f[1]);
-        f[2] = __dp4a((int)__byte_perm(t1, t3, 0x5410u), (int)jpack[b], f[2]);
-        f[3] = __dp4a((int)__byte_perm(t1, t3, 0x7632u), (int)jpack[b], f[3]);
-    }
-    uint32_t F = 0;  // 0xFE in byte w when copy w flips (XOR turns +1 <-> -1)
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        const int sw = (int)prmt(S, 0u, 0x8880u | (0x1110u * (uint32_t)w) | (uint32_t)w);
-        const int Lw = sw * f[w];
-        const int col = (int)__byte_perm(Z, 0u, 0x4440u | (uint32_t)w);
-        const uint32_t th = thr_c[3 * Lw + col];
-        const bool acc = (u[w] < th) | (th == 0xFFFFFFFFu);
-        F |= acc ? (0xFEu << (8 * w)) : 0u;
-        sumL += acc ? Lw : 0;
-    }
-    // flips and their Trotter columns from the packed flip mask
-    nflip += __popc(F & 0x02020202u);
-    sumC = __dp4a((int)(Z & (F >> 1)), 0x01010101, sumC);
-    if (F) {
-        const uint32_t lo = __byte_perm(F, 0u, par ? 0x1404u : 0x4140u);
-        const uint32_t hi = __byte_perm(F, 0u, par ? 0x3424u : 0x4342u);
-        *reinterpret_cast<uint2*>(sp + row + c) = make_uint2(own.x ^ lo, own.y ^ hi);
-    }
-}
-
 // One CTA per chain with the chain, the unit descriptors and the threshold row in shared
 // memory. PRE: the last (blockDim - n_consumer) threads are producer warps that write the
 // random words of sweep s+1 into one shared buffer while the consumer warps run the levels
@@ -599,7 +367,7 @@ sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int 
     unsigned long long* s_acc = reinterpret_cast<unsigned long long*>(smem + L.acc);
     const int NC = PRE ? n_consumer : nt;
     const bool consumer = tid < NC;
-    const int DW = (DC == 4) ? 8 : 16;
+    const int DW = SiteDesc<DC>::DW;
 
     {
         const int4* src = reinterpret_cast<const int4*>(p.spins + (size_t)slot * p.slot_stride);
@@ -610,7 +378,7 @@ sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int 
         for (int x = tid; x < P; x += nt) ones[x] = 1;
         const int4* dsrc = reinterpret_cast<const int4*>(p.desc);
         int4* ddst = reinterpret_cast<int4*>(s_desc);
-        for (int x = tid; x < 2 * N * DW / 4; x += nt) ddst[x] = dsrc[x];
+        for (int x = tid; x < N * DW / 4; x += nt) ddst[x] = dsrc[x];
         for (int x = tid; x < 2 * N; x += nt) s_items[x] = p.items[x];
         for (int x = tid; x <= p.n_levels; x += nt) s_loff[x] = p.level_off[x];
     }
@@ -645,8 +413,8 @@ sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int 
                     const int g = u & gmask;
                     if (g >= G) continue;
                     const int q = base + (u >> lg);
-                    packed_unit<DC, PRE>(sp, s_desc + (size_t)q * DW, rb, q, g, G, P, t, (uint32_t)slot, key, thr_c,
-                                         sumL, sumC, nf);
+                    packed_unit<DC, PRE>(sp, s_desc, s_items[q], rb, q, g, G, P, t, (uint32_t)slot, key, thr_c, sumL,
+                                         sumC, nf);
                 }
                 if (PRE) named_barrier(1, NC); else __syncthreads();
             }

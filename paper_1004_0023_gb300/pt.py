@@ -36,7 +36,7 @@ class pt_rung(ctypes.Structure):
 class pt_options(ctypes.Structure):
     _fields_ = [("threads_per_block", _i32), ("wait_timeout_ms", _i32), ("swap_mode", _i32),
                 ("test_withhold_rung", _i32), ("kernel_path", _i32), ("producer_threads", _i32),
-                ("test_exact_swaps", _i32), ("reserved", _i32 * 1)]
+                ("test_exact_swaps", _i32), ("cluster_size", _i32), ("reserved", _i32 * 4)]
 
 
 class pt_observables(ctypes.Structure):
@@ -50,6 +50,16 @@ class pt_info(ctypes.Structure):
     _fields_ = [("n", _i32), ("P", _i32), ("R", _i32), ("lmax", _i32), ("max_degree", _i32),
                 ("n_levels", _i32), ("threads_per_block", _i32), ("cooperative", _i32),
                 ("kernel_path", _i32), ("producer_threads", _i32), ("device_bytes", _i64), ("kernel_launches", _i64), ("h2d_bytes", _i64)]
+
+
+class pt_request(ctypes.Structure):
+    _fields_ = [("inst", pt_instance), ("P", _i32), ("ladder", ctypes.POINTER(pt_rung)), ("R", _i32),
+                ("seed", _u64), ("n_sweeps", _i64), ("sweeps_per_swap", _i32)]
+
+
+class pt_batch_info(ctypes.Structure):
+    _fields_ = [("count", _i32), ("cluster", _i32), ("n_clusters", _i32), ("threads_per_block", _i32),
+                ("smem_bytes", _i64), ("device_bytes", _i64), ("kernel_launches", _i64), ("h2d_bytes", _i64)]
 
 
 class pt_device_problem(ctypes.Structure):
@@ -93,6 +103,16 @@ def load(path: str = LIB_PATH):
     lib.pt_make_tables.argtypes = [_i32, ctypes.POINTER(pt_rung), _i32, _i32, _vp, _vp]
     lib.pt_make_schedule.argtypes = [ctypes.POINTER(pt_instance), _vp, _vp, _p_i32]
     lib.pt_run_noalloc.argtypes = [ctypes.POINTER(pt_device_problem), _i64, _i32, _i32, _vp]
+    lib.pt_batch_create.argtypes = [ctypes.POINTER(pt_request), _i32, ctypes.POINTER(pt_options), _vp,
+                                    ctypes.POINTER(_vp)]
+    lib.pt_batch_run.argtypes = [_vp]
+    lib.pt_batch_sync.argtypes = [_vp]
+    lib.pt_batch_read_state.argtypes = [_vp, _i32, _vp, _sz]
+    lib.pt_batch_read_observables.argtypes = [_vp, _i32, ctypes.POINTER(pt_observables)]
+    lib.pt_batch_get_info.argtypes = [_vp, ctypes.POINTER(pt_batch_info)]
+    lib.pt_batch_destroy.argtypes = [_vp]
+    lib.pt_batch_last_error.argtypes = [_vp]
+    lib.pt_batch_last_error.restype = ctypes.c_char_p
     lib.pt_noalloc_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
@@ -103,7 +123,9 @@ def exported_symbols():
     return ["pt_create", "pt_sweep", "pt_swap", "pt_run", "pt_read_state", "pt_write_state",
             "pt_read_observables", "pt_read_tables", "pt_get_info", "pt_sync", "pt_destroy",
             "pt_last_error", "pt_make_tables", "pt_make_schedule", "pt_run_noalloc",
-            "pt_noalloc_last_error"]
+            "pt_noalloc_last_error", "pt_batch_create", "pt_batch_run", "pt_batch_read_state",
+            "pt_batch_read_observables", "pt_batch_get_info", "pt_batch_sync", "pt_batch_destroy",
+            "pt_batch_last_error"]
 
 
 def _instance(n, ei, ej, J, h, keep):
@@ -228,21 +250,7 @@ class PT:
         self._check(self.lib.pt_write_state(self.ctx, _ptr(xa), xa.nbytes))
 
     def obs(self):
-        R = self.R
-        arr = {k: np.zeros(R, np.int64) for k in
-               ("E", "M", "n_meas", "sum_E", "sum_E2", "sum_M", "sum_M2", "flip_acc")}
-        att = np.zeros(max(R - 1, 1), np.int64)
-        acc = np.zeros(max(R - 1, 1), np.int64)
-        at = np.zeros(R, np.int32)
-        o = pt_observables(0, 0, *(arr[k].ctypes.data_as(_p_i64) for k in
-                                   ("E", "M", "n_meas", "sum_E", "sum_E2", "sum_M", "sum_M2", "flip_acc")),
-                           att.ctypes.data_as(_p_i64), acc.ctypes.data_as(_p_i64), at.ctypes.data_as(_p_i32))
-        self._check(self.lib.pt_read_observables(self.ctx, ctypes.byref(o)))
-        d = dict(arr)
-        d["t"], d["q"] = int(o.t), int(o.q)
-        d["swap_att"], d["swap_acc"] = att[: R - 1], acc[: R - 1]
-        d["replica_at"] = at
-        return d
+        return _read_obs(self.R, lambda o: self.lib.pt_read_observables(self.ctx, ctypes.byref(o)), self._check)
 
     def tables(self):
         info = self.info
@@ -255,3 +263,77 @@ class PT:
         i = pt_info()
         self._check(self.lib.pt_get_info(self.ctx, ctypes.byref(i)))
         return i
+
+
+def _read_obs(R, call, check):
+    arr = {k: np.zeros(R, np.int64) for k in
+           ("E", "M", "n_meas", "sum_E", "sum_E2", "sum_M", "sum_M2", "flip_acc")}
+    att = np.zeros(max(R - 1, 1), np.int64)
+    acc = np.zeros(max(R - 1, 1), np.int64)
+    at = np.zeros(R, np.int32)
+    o = pt_observables(0, 0, *(arr[k].ctypes.data_as(_p_i64) for k in
+                               ("E", "M", "n_meas", "sum_E", "sum_E2", "sum_M", "sum_M2", "flip_acc")),
+                       att.ctypes.data_as(_p_i64), acc.ctypes.data_as(_p_i64), at.ctypes.data_as(_p_i32))
+    check(call(o))
+    d = dict(arr)
+    d["t"], d["q"] = int(o.t), int(o.q)
+    d["swap_att"], d["swap_acc"] = att[: R - 1], acc[: R - 1]
+    d["replica_at"] = at
+    return d
+
+
+class Batch:
+    """Many independent problems in one persistent launch (include/pt.h, pt_batch_*)."""
+
+    def __init__(self, problems, cluster_size=0, stream=None):
+        self.lib = load()
+        self.problems = list(problems)
+        keep = []
+        reqs = (pt_request * len(self.problems))()
+        for k, prob in enumerate(self.problems):
+            inst = _instance(prob.n, prob.ei, prob.ej, prob.J, prob.h, keep)
+            ladder = (pt_rung * prob.R)(*[pt_rung(float(a), float(b)) for a, b in zip(prob.T, prob.gamma)])
+            keep.append(ladder)
+            reqs[k] = pt_request(inst, int(prob.P), ladder, int(prob.R),
+                                 int(prob.seed) & 0xFFFFFFFFFFFFFFFF, int(prob.n_sweeps), int(prob.sweeps_per_swap))
+        opt = pt_options()
+        opt.cluster_size = int(cluster_size)
+        h = _vp()
+        rc = self.lib.pt_batch_create(reqs, len(self.problems), ctypes.byref(opt),
+                                      None if stream is None else _vp(int(stream)), ctypes.byref(h))
+        if rc != PT_OK:
+            raise PTError(rc, self.lib.pt_batch_last_error(None).decode())
+        self.handle = h
+
+    def _check(self, rc):
+        if rc != PT_OK:
+            raise PTError(rc, self.lib.pt_batch_last_error(self.handle).decode())
+
+    def run(self):
+        self._check(self.lib.pt_batch_run(self.handle))
+
+    def sync(self):
+        self._check(self.lib.pt_batch_sync(self.handle))
+
+    def read_state(self, k):
+        prob = self.problems[k]
+        out = np.empty((prob.R, prob.n, prob.P), np.int8)
+        self._check(self.lib.pt_batch_read_state(self.handle, int(k), _ptr(out), out.nbytes))
+        return out
+
+    def obs(self, k):
+        return _read_obs(self.problems[k].R,
+                         lambda o: self.lib.pt_batch_read_observables(self.handle, int(k), ctypes.byref(o)),
+                         self._check)
+
+    def info(self):
+        i = pt_batch_info()
+        self._check(self.lib.pt_batch_get_info(self.handle, ctypes.byref(i)))
+        return i
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.pt_batch_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close

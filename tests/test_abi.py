@@ -103,3 +103,31 @@ def test_schedule_respects_sequential_order():
     assert nlev == n + 1
     # no edges: everything in two levels
     assert _check_schedule(5, [], []) == 2
+
+
+def test_ctypes_structs_match_the_c_header(tmp_path):
+    """Sizes and field offsets of every ABI struct agree between include/pt.h and pt.py."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"pt_instance": pt.pt_instance, "pt_rung": pt.pt_rung, "pt_options": pt.pt_options,
+               "pt_observables": pt.pt_observables, "pt_info": pt.pt_info, "pt_request": pt.pt_request,
+               "pt_batch_info": pt.pt_batch_info, "pt_device_problem": pt.pt_device_problem}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pt.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines.append("return 0; }")
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert int(out["%s.%s" % (name, f[0])]) == getattr(cls, f[0]).offset, (name, f[0])
