@@ -341,7 +341,13 @@ cudaError_t launch_batch(const BatchParams& bp, int cluster, int n_clusters, int
 }
 
 cudaError_t batch_max_clusters(int cluster, int threads, size_t smem, int* n_clusters) {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the limit is a per-function attribute shared by every batch, so it is raised once to
+    // the device's opt-in maximum (less this kernel's static shared memory)
+    int dev = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 1024);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
