@@ -221,6 +221,46 @@ int pt_batch_sync(pt_batch* b);
 int pt_batch_destroy(pt_batch* b);
 const char* pt_batch_last_error(const pt_batch* b);
 
+/* ---- Serving: continuous batching ----------------------------------------------------
+ * A request (pt_request) is copied and queued by pt_server_submit. pt_server_step admits
+ * queued requests in arrival order while a slot (max_active) and room in the device arena
+ * are free, then runs one batched launch in which every admitted request advances by up
+ * to quantum_sweeps sweeps (whole swap intervals) with its state and counters resident in
+ * the arena; it reports the ids of requests that have finished. Results are read with
+ * pt_server_read_result and the arena room is returned by pt_server_release. Each result
+ * equals pt_create + pt_run of that request alone. Same request limits as pt_batch. */
+typedef struct pt_server pt_server;
+
+typedef struct {
+    int64_t arena_bytes;    /* device memory for admitted requests (0 = half of the free memory) */
+    int32_t max_active;     /* requests on the device at once (0 = 512) */
+    int32_t quantum_sweeps; /* sweeps per request per step (0 = 100) */
+    int32_t cluster_size;   /* CTAs per cluster (0 = 2) */
+    int32_t reserved[3];
+} pt_server_options;
+
+typedef struct {
+    int32_t active;         /* requests on the device */
+    int32_t queued;         /* requests waiting for a slot or arena room */
+    int64_t arena_bytes;
+    int64_t arena_used;
+    int64_t steps;
+    int64_t kernel_launches;
+} pt_server_info;
+
+int pt_server_create(const pt_server_options* opt, void* cuda_stream, pt_server** out);
+/* PT_EINVAL for an invalid request, PT_ENOMEM if it could never fit the arena. */
+int pt_server_submit(pt_server* s, const pt_request* req, int64_t* id);
+/* Admit, run one step, and write up to max_done finished ids (the rest come next call). */
+int pt_server_step(pt_server* s, int64_t* done_ids, int32_t max_done, int32_t* n_done);
+/* For a finished request: state (rung order, may be NULL) and statistics (may be NULL). */
+int pt_server_read_result(pt_server* s, int64_t id, int8_t* state, size_t bytes, pt_observables* obs);
+/* Forget a queued or finished request (PT_EBUSY while it runs). */
+int pt_server_release(pt_server* s, int64_t id);
+int pt_server_get_info(const pt_server* s, pt_server_info* out);
+int pt_server_destroy(pt_server* s);
+const char* pt_server_last_error(const pt_server* s);
+
 /* ---- Running on caller-owned device memory, without allocating ----------------------
  * The paper has no counterpart to this entry point. It is for callers that cannot allocate
  * device memory, neither themselves nor through this library: work recorded into a CUDA

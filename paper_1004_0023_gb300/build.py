@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpt.so")
-SOURCES = ["pt_host.cu", "pt_kernels.cu", "pt_batch.cu", "pt_noalloc.cu"]
+SOURCES = ["pt_host.cu", "pt_kernels.cu", "pt_batch.cu", "pt_serve.cu", "pt_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -422,19 +422,7 @@ static cudaError_t balloc(pt_batch* b, T** ptr, size_t bytes) {
     return cudaSuccess;
 }
 
-namespace {
-// Host-side preparation of one request, in the packed layout of the batched kernel.
-struct Prepared {
-    int N, P, R, Lmax, dc, n_levels, slot_stride;
-    std::vector<uint32_t> sdesc, items, thr;
-    std::vector<int32_t> level_off;
-    std::vector<double> coef;
-    size_t off_sdesc, off_items, off_loff, off_thr, off_coef, off_spins, off_E, off_M, off_rung, off_slot, off_acc,
-        off_sw;
-    long long sweep_limit;
-};
-
-int prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len) {
+int ptq::prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len) {
     const pt_instance* inst = &r.inst;
     const int N = inst->n, nE = inst->n_edges, P = r.P, R = r.R;
     if (N < 1 || N > 65535 || nE < 0 || !inst->h || (nE > 0 && (!inst->ei || !inst->ej || !inst->J))) {
@@ -515,7 +503,71 @@ int prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len
     build_site_desc(N, P, pr.dc, adj, adjJ, inst->h, pr.sdesc);
     return PT_OK;
 }
-}  // namespace
+
+// Offsets of one request's data inside a block of its own (constants, then state).
+size_t ptq::request_block_layout(Prepared& p) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    p.off_sdesc = take(p.sdesc.size() * 4);
+    p.off_items = take(p.items.size() * 4);
+    p.off_loff = take(p.level_off.size() * 4);
+    p.off_thr = take(p.thr.size() * 4);
+    p.off_coef = take(p.coef.size() * 8);
+    p.off_spins = take((size_t)p.R * p.slot_stride);
+    p.off_E = take((size_t)p.R * 8);
+    p.off_M = take((size_t)p.R * 8);
+    p.off_rung = take((size_t)p.R * 4);
+    p.off_slot = take((size_t)p.R * 4);
+    p.off_acc = take((size_t)p.R * kAccCount * 8);
+    p.off_sw = take((size_t)p.R * 16);
+    return off;
+}
+
+void ptq::fill_instance(BatchInstance& I, const Prepared& p, unsigned char* base, const pt_request& r) {
+    memset(&I, 0, sizeof(I));
+    I.N = p.N;
+    I.P = p.P;
+    I.R = p.R;
+    I.Lmax = p.Lmax;
+    I.nL3 = (2 * p.Lmax + 1) * 3;
+    I.n_levels = p.n_levels;
+    I.dc = p.dc;
+    I.slot_stride = p.slot_stride;
+    I.key0 = (uint32_t)(r.seed & 0xFFFFFFFFu);
+    I.key1 = (uint32_t)(r.seed >> 32);
+    I.n_sweeps = (int)r.n_sweeps;
+    I.sweeps_per_swap = r.sweeps_per_swap;
+    I.sdesc = (const uint32_t*)(base + p.off_sdesc);
+    I.items = (const uint32_t*)(base + p.off_items);
+    I.level_off = (const int32_t*)(base + p.off_loff);
+    I.thr = (const uint32_t*)(base + p.off_thr);
+    I.coef = (const double*)(base + p.off_coef);
+    I.spins = (int8_t*)(base + p.off_spins);
+    I.E = (long long*)(base + p.off_E);
+    I.M = (long long*)(base + p.off_M);
+    I.rung_of_slot = (int32_t*)(base + p.off_rung);
+    I.slot_of_rung = (int32_t*)(base + p.off_slot);
+    I.acc = (unsigned long long*)(base + p.off_acc);
+    I.swap_stats = (unsigned long long*)(base + p.off_sw);
+}
+
+void ptq::choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_cap) {
+    // threads per chain: about one 4-copy unit per thread in an average level, at least two
+    // warps, and no more groups than a CTA has chains; chains stay resident when they fit
+    const long long units = 2ll * I.N * (I.P / 8);
+    const long long avg = (units + I.n_levels - 1) / I.n_levels;
+    const int C = (I.R + cluster - 1) / cluster;
+    int g = 64;
+    while (g < 512 && g < avg) g <<= 1;
+    while (g < 512 && threads / g > C) g <<= 1;
+    I.group_threads = g;
+    I.resident = 1;
+    if (batch_smem_bytes(I, cluster, threads) > smem_cap) I.resident = 0;
+}
 
 extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_options* opt, void* cuda_stream,
                                pt_batch** out) {
@@ -597,17 +649,7 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
         I.n_sweeps = (int)reqs[k].n_sweeps;
         I.sweeps_per_swap = reqs[k].sweeps_per_swap;
         b->sweep_limit[k] = p.sweep_limit;
-        // threads per chain: about one 4-copy unit per thread in an average level, at
-        // least two warps, and no more groups than this CTA has chains
-        const long long units = 2ll * p.N * (p.P / 8);
-        const long long avg = (units + p.n_levels - 1) / p.n_levels;
-        const int C = (p.R + b->cluster - 1) / b->cluster;
-        int g = 64;
-        while (g < 512 && g < avg) g <<= 1;
-        while (g < 512 && b->threads / g > C) g <<= 1;
-        I.group_threads = g;
-        I.resident = 1;
-        if (batch_smem_bytes(I, b->cluster, b->threads) > smem_cap) I.resident = 0;
+        choose_groups(I, b->cluster, b->threads, smem_cap);
         const size_t need = batch_smem_bytes(I, b->cluster, b->threads);
         if (need > smem_cap) {
             free_batch(b);

@@ -128,6 +128,21 @@ void level_schedule(int N, const std::vector<std::vector<int>>& adj, std::vector
 void build_site_desc(int N, int P, int dclass, const std::vector<std::vector<int>>& adj,
                      const std::vector<std::vector<int>>& adjJ, const int32_t* h, std::vector<uint32_t>& desc);
 
+// Host-side preparation of one batched request (pt_batch.cu).
+struct Prepared {
+    int N, P, R, Lmax, dc, n_levels, slot_stride;
+    std::vector<uint32_t> sdesc, items, thr;
+    std::vector<int32_t> level_off;
+    std::vector<double> coef;
+    size_t off_sdesc, off_items, off_loff, off_thr, off_coef, off_spins, off_E, off_M, off_rung, off_slot, off_acc,
+        off_sw;
+    long long sweep_limit;
+};
+int prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len);
+size_t request_block_layout(Prepared& p);
+void fill_instance(BatchInstance& I, const Prepared& p, unsigned char* base, const pt_request& r);
+void choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_cap);
+
 // Batched launchers (pt_batch.cu).
 size_t batch_smem_bytes(const BatchInstance& I, int cluster, int threads);
 cudaError_t launch_batch(const BatchParams& bp, int cluster, int n_clusters, int threads, size_t smem,

@@ -1,0 +1,454 @@
+// pt_serve.cu -- continuous batching of PT-QMC requests.
+//
+// Requests arrive at any time (pt_server_submit) and wait in a FIFO until a slot and room
+// in a preallocated device arena are free; then their data and initial state are placed
+// in the arena, where their spins, (E, M), rung permutation, statistics and sweep / pass
+// counters stay until they finish. Every pt_server_step is one batched launch in which
+// each admitted request advances by up to `quantum` sweeps (whole swap intervals), so the
+// work of requests that arrived at different times overlaps on the device; requests that
+// complete are reported and admission runs again. A request's arithmetic never depends
+// on what else is in the launch: its result equals pt_create + pt_run on it alone.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <deque>
+#include <map>
+#include <vector>
+
+#include "pt.h"
+#include "pt_internal.h"
+
+using namespace ptq;
+
+namespace {
+
+// First-fit allocator over [0, size) of the device arena, 256-byte granules.
+class ArenaAllocator {
+   public:
+    explicit ArenaAllocator(size_t size) : size_(size) { free_.push_back({0, size}); }
+    bool alloc(size_t bytes, size_t* off) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        for (size_t k = 0; k < free_.size(); ++k) {
+            if (free_[k].size >= bytes) {
+                *off = free_[k].off;
+                free_[k].off += bytes;
+                free_[k].size -= bytes;
+                if (free_[k].size == 0) free_.erase(free_.begin() + k);
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        used_ -= bytes;
+        auto it = std::lower_bound(free_.begin(), free_.end(), off,
+                                   [](const Range& r, size_t o) { return r.off < o; });
+        it = free_.insert(it, {off, bytes});
+        // merge with the next and the previous free range
+        if (it + 1 != free_.end() && it->off + it->size == (it + 1)->off) {
+            it->size += (it + 1)->size;
+            free_.erase(it + 1);
+        }
+        if (it != free_.begin() && (it - 1)->off + (it - 1)->size == it->off) {
+            (it - 1)->size += it->size;
+            free_.erase(it);
+        }
+    }
+    size_t used() const { return used_; }
+    size_t size() const { return size_; }
+
+   private:
+    struct Range {
+        size_t off, size;
+    };
+    std::vector<Range> free_;
+    size_t size_, used_ = 0;
+};
+
+struct ServeReq {
+    int64_t id;
+    pt_request req;  // pointers cleared after preparation
+    Prepared prep;
+    size_t block_off = 0, block_bytes = 0;
+    BatchInstance inst;
+    int64_t remaining = 0;
+    int state = 0;  // 0 queued, 1 on the device, 2 finished
+};
+
+}  // namespace
+
+struct pt_server {
+    cudaStream_t stream;
+    bool own_stream;
+    unsigned char* arena;
+    ArenaAllocator* alloc;
+    int max_active, quantum, cluster, threads, n_clusters;
+    size_t smem_cap;
+    std::map<int64_t, ServeReq*> reqs;
+    std::deque<int64_t> queued;
+    std::vector<int64_t> active;
+    std::deque<int64_t> finished_unreported;
+    int64_t next_id, steps, launches;
+    BatchInstance* d_inst;
+    int32_t* d_order;
+    int* d_counter;
+    int* d_status;
+    int2* d_map;
+    int map_capacity;
+    std::vector<void*> allocs;
+    int err;
+    char msg[256];
+};
+
+static thread_local char g_srv_create_msg[256] = "";
+
+static int sfail(pt_server* s, int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(s ? s->msg : g_srv_create_msg, 256, fmt, ap);
+    va_end(ap);
+    if (s && (code == PT_ECUDA || code == PT_ETIMEDOUT)) s->err = code;
+    return code;
+}
+
+static void free_server(pt_server* s) {
+    for (auto& kv : s->reqs) delete kv.second;
+    for (void* p : s->allocs) cudaFree(p);
+    delete s->alloc;
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream, pt_server** out) {
+    if (!out) return sfail(nullptr, PT_EINVAL, "null output");
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) return sfail(nullptr, PT_ENODEV, "no CUDA device");
+    pt_server* s = new pt_server();
+    s->stream = (cudaStream_t)cuda_stream;
+    s->own_stream = false;
+    s->arena = nullptr;
+    s->alloc = nullptr;
+    s->next_id = 1;
+    s->steps = s->launches = 0;
+    s->err = 0;
+    s->msg[0] = 0;
+    s->max_active = (opt && opt->max_active > 0) ? opt->max_active : 512;
+    s->quantum = (opt && opt->quantum_sweeps > 0) ? opt->quantum_sweeps : 100;
+    s->cluster = (opt && opt->cluster_size > 0) ? opt->cluster_size : 2;
+    s->threads = 512;
+    if (s->cluster > 16 || s->max_active > 65536) {
+        delete s;
+        return sfail(nullptr, PT_EINVAL, "cluster_size <= 16 and max_active <= 65536");
+    }
+    if (!s->stream) {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            return sfail(nullptr, PT_ECUDA, "cudaStreamCreate failed");
+        }
+        s->own_stream = true;
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    size_t arena_bytes = (opt && opt->arena_bytes > 0) ? (size_t)opt->arena_bytes : free_b / 2;
+    arena_bytes &= ~(size_t)255;
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    s->smem_cap = (size_t)max_smem - 1024;
+    s->map_capacity = 1 << 16;
+    void* p = nullptr;
+    cudaError_t e;
+    auto grab = [&](size_t bytes) -> void* {
+        void* q = nullptr;
+        if (cudaMalloc(&q, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+        s->allocs.push_back(q);
+        return q;
+    };
+    s->arena = (unsigned char*)grab(arena_bytes);
+    s->d_inst = (BatchInstance*)grab(sizeof(BatchInstance) * s->max_active);
+    s->d_order = (int32_t*)grab(sizeof(int32_t) * s->max_active);
+    s->d_counter = (int*)grab(16);
+    s->d_status = (int*)grab(16);
+    s->d_map = (int2*)grab(sizeof(int2) * s->map_capacity);
+    if (!s->arena || !s->d_inst || !s->d_order || !s->d_counter || !s->d_status || !s->d_map) {
+        free_server(s);
+        return sfail(nullptr, PT_ENOMEM, "could not allocate the serving arena (%zu bytes)", arena_bytes);
+    }
+    (void)p;
+    s->alloc = new ArenaAllocator(arena_bytes);
+    if ((e = cudaMemsetAsync(s->d_status, 0, 16, s->stream)) != cudaSuccess) {
+        free_server(s);
+        return sfail(nullptr, PT_ECUDA, "%s", cudaGetErrorString(e));
+    }
+    int ncl = 0;
+    if ((e = batch_max_clusters(s->cluster, s->threads, s->smem_cap, &ncl)) != cudaSuccess || ncl < 1) {
+        free_server(s);
+        return sfail(nullptr, PT_EINVAL, "no cluster of %d CTAs fits (%s)", s->cluster, cudaGetErrorString(e));
+    }
+    s->n_clusters = ncl;
+    *out = s;
+    return PT_OK;
+}
+
+extern "C" int pt_server_submit(pt_server* s, const pt_request* r, int64_t* id) {
+    if (!s || !r || !id) return PT_EINVAL;
+    if (s->err) return s->err;
+    ServeReq* q = new ServeReq();
+    char why[200];
+    const int rc = prepare_request(*r, q->prep, why, sizeof(why));
+    if (rc) {
+        delete q;
+        return sfail(s, rc, "%s", why);
+    }
+    q->block_bytes = request_block_layout(q->prep);
+    if (q->block_bytes > s->alloc->size()) {
+        delete q;
+        return sfail(s, PT_ENOMEM, "request needs %zu bytes, the arena holds %zu", q->block_bytes, s->alloc->size());
+    }
+    if (q->prep.R > s->map_capacity) {
+        delete q;
+        return sfail(s, PT_EINVAL, "too many rungs");
+    }
+    q->req = *r;
+    q->req.inst.ei = q->req.inst.ej = q->req.inst.J = q->req.inst.h = nullptr;
+    q->req.ladder = nullptr;
+    q->remaining = r->n_sweeps;
+    q->id = s->next_id++;
+    // the request's shared-memory plan must fit one CTA
+    fill_instance(q->inst, q->prep, nullptr, q->req);
+    choose_groups(q->inst, s->cluster, s->threads, s->smem_cap);
+    if (batch_smem_bytes(q->inst, s->cluster, s->threads) > s->smem_cap) {
+        delete q;
+        return sfail(s, PT_EINVAL, "request does not fit one CTA's shared memory");
+    }
+    if (q->prep.sweep_limit < r->n_sweeps) {
+        delete q;
+        return sfail(s, PT_EOVERFLOW, "request's statistics could overflow int64");
+    }
+    s->reqs[q->id] = q;
+    s->queued.push_back(q->id);
+    *id = q->id;
+    return PT_OK;
+}
+
+// Admit queued requests in arrival order while a slot and arena room are free.
+static int admit(pt_server* s) {
+    std::vector<ServeReq*> fresh;
+    while (!s->queued.empty() && (int)s->active.size() < s->max_active) {
+        ServeReq* q = s->reqs[s->queued.front()];
+        size_t off = 0;
+        if (!s->alloc->alloc(q->block_bytes, &off)) break;
+        q->block_off = off;
+        unsigned char* base = s->arena + off;
+        const Prepared& p = q->prep;
+        const int gthreads = q->inst.group_threads, resident = q->inst.resident;
+        fill_instance(q->inst, p, base, q->req);
+        q->inst.group_threads = gthreads;
+        q->inst.resident = resident;
+        std::vector<unsigned char> host(p.off_spins, 0);
+        memcpy(&host[p.off_sdesc], p.sdesc.data(), p.sdesc.size() * 4);
+        memcpy(&host[p.off_items], p.items.data(), p.items.size() * 4);
+        memcpy(&host[p.off_loff], p.level_off.data(), p.level_off.size() * 4);
+        memcpy(&host[p.off_thr], p.thr.data(), p.thr.size() * 4);
+        memcpy(&host[p.off_coef], p.coef.data(), p.coef.size() * 8);
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(base, host.data(), host.size(), cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(base + p.off_spins, 0, q->block_bytes - p.off_spins, s->stream)) != cudaSuccess)
+            return sfail(s, PT_ECUDA, "admission upload: %s", cudaGetErrorString(e));
+        q->state = 1;
+        s->queued.pop_front();
+        s->active.push_back(q->id);
+        fresh.push_back(q);
+    }
+    // initial spins and (E, M) of the newly admitted requests, one block per chain
+    size_t k = 0;
+    while (k < fresh.size()) {
+        std::vector<BatchInstance> insts;
+        std::vector<int2> map;
+        while (k < fresh.size() && (int)insts.size() < s->max_active &&
+               (int)(map.size() + fresh[k]->prep.R) <= s->map_capacity) {
+            for (int rho = 0; rho < fresh[k]->prep.R; ++rho) map.push_back(make_int2((int)insts.size(), rho));
+            insts.push_back(fresh[k]->inst);
+            ++k;
+        }
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(s->d_inst, insts.data(), insts.size() * sizeof(BatchInstance),
+                                 cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(s->d_map, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                 s->stream)) != cudaSuccess ||
+            (e = launch_batch_init(s->d_inst, s->d_map, (int)map.size(), s->stream)) != cudaSuccess)
+            return sfail(s, PT_ECUDA, "admission init: %s", cudaGetErrorString(e));
+        s->launches += 1;
+    }
+    return PT_OK;
+}
+
+extern "C" int pt_server_step(pt_server* s, int64_t* done_ids, int32_t max_done, int32_t* n_done) {
+    if (!s || !n_done || (max_done > 0 && !done_ids)) return PT_EINVAL;
+    if (s->err) return s->err;
+    int rc = admit(s);
+    if (rc) return rc;
+    if (!s->active.empty()) {
+        std::vector<BatchInstance> insts;
+        std::vector<int64_t> chunk(s->active.size());
+        insts.reserve(s->active.size());
+        for (size_t a = 0; a < s->active.size(); ++a) {
+            ServeReq* q = s->reqs[s->active[a]];
+            const int sps = q->inst.sweeps_per_swap;
+            long long c = std::min<long long>(q->remaining, s->quantum);
+            if (sps > 0 && c < q->remaining) c = std::max<long long>(sps, (c / sps) * sps);
+            c = std::min<long long>(c, q->remaining);
+            chunk[a] = c;
+            BatchInstance I = q->inst;
+            I.n_sweeps = (int)c;
+            insts.push_back(I);
+        }
+        std::vector<int32_t> order(insts.size());
+        for (size_t a = 0; a < order.size(); ++a) order[a] = (int32_t)a;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            const double wx = (double)insts[x].N * insts[x].P * insts[x].R * (double)insts[x].n_sweeps;
+            const double wy = (double)insts[y].N * insts[y].P * insts[y].R * (double)insts[y].n_sweeps;
+            return wx > wy;
+        });
+        size_t smem = 0;
+        for (const BatchInstance& I : insts) smem = std::max(smem, batch_smem_bytes(I, s->cluster, s->threads));
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(s->d_inst, insts.data(), insts.size() * sizeof(BatchInstance),
+                                 cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(s->d_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                 s->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(s->d_counter, 0, sizeof(int), s->stream)) != cudaSuccess)
+            return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+        BatchParams bp;
+        bp.inst = s->d_inst;
+        bp.order = s->d_order;
+        bp.count = (int)insts.size();
+        bp.next_job = s->d_counter;
+        bp.status = s->d_status;
+        const int ncl = std::min<int>(s->n_clusters, (int)insts.size());
+        if ((e = launch_batch(bp, s->cluster, ncl, s->threads, smem, s->stream)) != cudaSuccess)
+            return sfail(s, PT_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+        s->launches += 1;
+        if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
+            return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+        s->steps += 1;
+        std::vector<int64_t> still;
+        for (size_t a = 0; a < s->active.size(); ++a) {
+            ServeReq* q = s->reqs[s->active[a]];
+            q->remaining -= chunk[a];
+            q->inst.t0 += chunk[a];
+            if (q->inst.sweeps_per_swap > 0) q->inst.q0 += chunk[a] / q->inst.sweeps_per_swap;
+            if (q->remaining == 0) {
+                q->state = 2;
+                s->finished_unreported.push_back(q->id);
+            } else {
+                still.push_back(q->id);
+            }
+        }
+        s->active.swap(still);
+    }
+    int n = 0;
+    while (n < max_done && !s->finished_unreported.empty()) {
+        done_ids[n++] = s->finished_unreported.front();
+        s->finished_unreported.pop_front();
+    }
+    *n_done = n;
+    return PT_OK;
+}
+
+extern "C" int pt_server_read_result(pt_server* s, int64_t id, int8_t* state, size_t bytes, pt_observables* o) {
+    if (!s) return PT_EINVAL;
+    if (s->err) return s->err;
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return sfail(s, PT_EINVAL, "unknown request %lld", (long long)id);
+    ServeReq* q = it->second;
+    if (q->state != 2) return sfail(s, PT_EBUSY, "request %lld has not finished", (long long)id);
+    const BatchInstance& I = q->inst;
+    const int R = I.R;
+    std::vector<int32_t> slot_of(R);
+    std::vector<long long> E(R), M(R);
+    std::vector<unsigned long long> acc((size_t)R * kAccCount), sw(2 * (size_t)R);
+    std::vector<int8_t> spins;
+    cudaError_t e;
+    cudaStream_t st = s->stream;
+    if ((e = cudaMemcpyAsync(slot_of.data(), I.slot_of_rung, R * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(E.data(), I.E, R * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(M.data(), I.M, R * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(acc.data(), I.acc, acc.size() * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(sw.data(), I.swap_stats, sw.size() * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+    if (state) {
+        const size_t need = (size_t)R * I.N * I.P;
+        if (bytes < need) return sfail(s, PT_EINVAL, "state buffer needs %zu bytes", need);
+        spins.resize((size_t)R * I.slot_stride);
+        if ((e = cudaMemcpyAsync(spins.data(), I.spins, spins.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+    if (state) {
+        // replica order on the device, rung order across the boundary
+        const size_t chain = (size_t)I.N * I.P;
+        for (int r = 0; r < R; ++r) memcpy(state + (size_t)r * chain, &spins[(size_t)slot_of[r] * I.slot_stride], chain);
+    }
+    if (o) {
+        o->t = I.t0;
+        o->q = I.q0;
+        for (int r = 0; r < R; ++r) {
+            const int slot = slot_of[r];
+            if (o->E) o->E[r] = E[slot];
+            if (o->M) o->M[r] = M[slot];
+            const unsigned long long* a = &acc[(size_t)r * kAccCount];
+            if (o->n_meas) o->n_meas[r] = (int64_t)a[kAccN];
+            if (o->sum_E) o->sum_E[r] = (int64_t)a[kAccE];
+            if (o->sum_E2) o->sum_E2[r] = (int64_t)a[kAccE2];
+            if (o->sum_M) o->sum_M[r] = (int64_t)a[kAccM];
+            if (o->sum_M2) o->sum_M2[r] = (int64_t)a[kAccM2];
+            if (o->flip_acc) o->flip_acc[r] = (int64_t)a[kAccFlip];
+            if (o->replica_at) o->replica_at[r] = slot;
+        }
+        for (int r = 0; r + 1 < R; ++r) {
+            if (o->swap_att) o->swap_att[r] = (int64_t)sw[2 * r];
+            if (o->swap_acc) o->swap_acc[r] = (int64_t)sw[2 * r + 1];
+        }
+    }
+    return PT_OK;
+}
+
+extern "C" int pt_server_release(pt_server* s, int64_t id) {
+    if (!s) return PT_EINVAL;
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return sfail(s, PT_EINVAL, "unknown request %lld", (long long)id);
+    ServeReq* q = it->second;
+    if (q->state == 1) return sfail(s, PT_EBUSY, "request %lld is still running", (long long)id);
+    if (q->state == 0) s->queued.erase(std::find(s->queued.begin(), s->queued.end(), id));
+    if (q->state == 2) s->alloc->release(q->block_off, q->block_bytes);
+    delete q;
+    s->reqs.erase(it);
+    return PT_OK;
+}
+
+extern "C" int pt_server_get_info(const pt_server* s, pt_server_info* o) {
+    if (!s || !o) return PT_EINVAL;
+    o->active = (int32_t)s->active.size();
+    o->queued = (int32_t)s->queued.size();
+    o->arena_bytes = (int64_t)s->alloc->size();
+    o->arena_used = (int64_t)s->alloc->used();
+    o->steps = s->steps;
+    o->kernel_launches = s->launches;
+    return PT_OK;
+}
+
+extern "C" int pt_server_destroy(pt_server* s) {
+    if (!s) return PT_OK;
+    cudaStreamSynchronize(s->stream);
+    free_server(s);
+    return PT_OK;
+}
+
+extern "C" const char* pt_server_last_error(const pt_server* s) { return s ? s->msg : g_srv_create_msg; }

@@ -62,6 +62,16 @@ class pt_batch_info(ctypes.Structure):
                 ("smem_bytes", _i64), ("device_bytes", _i64), ("kernel_launches", _i64), ("h2d_bytes", _i64)]
 
 
+class pt_server_options(ctypes.Structure):
+    _fields_ = [("arena_bytes", _i64), ("max_active", _i32), ("quantum_sweeps", _i32), ("cluster_size", _i32),
+                ("reserved", _i32 * 3)]
+
+
+class pt_server_info(ctypes.Structure):
+    _fields_ = [("active", _i32), ("queued", _i32), ("arena_bytes", _i64), ("arena_used", _i64), ("steps", _i64),
+                ("kernel_launches", _i64)]
+
+
 class pt_device_problem(ctypes.Structure):
     _fields_ = [("n", _i32), ("P", _i32), ("R", _i32), ("lmax", _i32), ("row_stride", _i32), ("n_levels", _i32),
                 ("nbr", _vp), ("h", _vp), ("items", _vp), ("level_off", _vp), ("thr", _vp), ("coef", _vp),
@@ -113,6 +123,15 @@ def load(path: str = LIB_PATH):
     lib.pt_batch_destroy.argtypes = [_vp]
     lib.pt_batch_last_error.argtypes = [_vp]
     lib.pt_batch_last_error.restype = ctypes.c_char_p
+    lib.pt_server_create.argtypes = [ctypes.POINTER(pt_server_options), _vp, ctypes.POINTER(_vp)]
+    lib.pt_server_submit.argtypes = [_vp, ctypes.POINTER(pt_request), _p_i64]
+    lib.pt_server_step.argtypes = [_vp, _p_i64, _i32, _p_i32]
+    lib.pt_server_read_result.argtypes = [_vp, _i64, _vp, _sz, ctypes.POINTER(pt_observables)]
+    lib.pt_server_release.argtypes = [_vp, _i64]
+    lib.pt_server_get_info.argtypes = [_vp, ctypes.POINTER(pt_server_info)]
+    lib.pt_server_destroy.argtypes = [_vp]
+    lib.pt_server_last_error.argtypes = [_vp]
+    lib.pt_server_last_error.restype = ctypes.c_char_p
     lib.pt_noalloc_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
@@ -125,7 +144,9 @@ def exported_symbols():
             "pt_last_error", "pt_make_tables", "pt_make_schedule", "pt_run_noalloc",
             "pt_noalloc_last_error", "pt_batch_create", "pt_batch_run", "pt_batch_read_state",
             "pt_batch_read_observables", "pt_batch_get_info", "pt_batch_sync", "pt_batch_destroy",
-            "pt_batch_last_error"]
+            "pt_batch_last_error", "pt_server_create", "pt_server_submit", "pt_server_step",
+            "pt_server_read_result", "pt_server_release", "pt_server_get_info", "pt_server_destroy",
+            "pt_server_last_error"]
 
 
 def _instance(n, ei, ej, J, h, keep):
@@ -334,6 +355,71 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             self.lib.pt_batch_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
+def _request(prob, keep):
+    inst = _instance(prob.n, prob.ei, prob.ej, prob.J, prob.h, keep)
+    ladder = (pt_rung * prob.R)(*[pt_rung(float(a), float(b)) for a, b in zip(prob.T, prob.gamma)])
+    keep.append(ladder)
+    return pt_request(inst, int(prob.P), ladder, int(prob.R), int(prob.seed) & 0xFFFFFFFFFFFFFFFF,
+                      int(prob.n_sweeps), int(prob.sweeps_per_swap))
+
+
+class Server:
+    """Continuous-batching server (include/pt.h, pt_server_*)."""
+
+    def __init__(self, arena_bytes=0, max_active=0, quantum_sweeps=0, cluster_size=0, stream=None):
+        self.lib = load()
+        opt = pt_server_options(int(arena_bytes), int(max_active), int(quantum_sweeps), int(cluster_size))
+        h = _vp()
+        rc = self.lib.pt_server_create(ctypes.byref(opt), None if stream is None else _vp(int(stream)),
+                                       ctypes.byref(h))
+        if rc != PT_OK:
+            raise PTError(rc, self.lib.pt_server_last_error(None).decode())
+        self.handle = h
+        self.problems = {}
+
+    def _check(self, rc):
+        if rc != PT_OK:
+            raise PTError(rc, self.lib.pt_server_last_error(self.handle).decode())
+
+    def submit(self, prob):
+        keep = []
+        req = _request(prob, keep)
+        rid = ctypes.c_int64()
+        self._check(self.lib.pt_server_submit(self.handle, ctypes.byref(req), ctypes.byref(rid)))
+        self.problems[rid.value] = prob
+        return rid.value
+
+    def step(self, max_done=4096):
+        ids = np.zeros(max_done, np.int64)
+        n = ctypes.c_int32()
+        self._check(self.lib.pt_server_step(self.handle, ids.ctypes.data_as(_p_i64), int(max_done), ctypes.byref(n)))
+        return ids[: n.value].tolist()
+
+    def result(self, rid, state=True):
+        prob = self.problems[rid]
+        out = np.empty((prob.R, prob.n, prob.P), np.int8) if state else None
+        obs = _read_obs(prob.R, lambda o: self.lib.pt_server_read_result(
+            self.handle, int(rid), None if out is None else _ptr(out), 0 if out is None else out.nbytes,
+            ctypes.byref(o)), self._check)
+        return out, obs
+
+    def release(self, rid):
+        self._check(self.lib.pt_server_release(self.handle, int(rid)))
+        self.problems.pop(rid, None)
+
+    def info(self):
+        i = pt_server_info()
+        self._check(self.lib.pt_server_get_info(self.handle, ctypes.byref(i)))
+        return i
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.pt_server_destroy(self.handle)
             self.handle = None
 
     __del__ = close

@@ -114,7 +114,8 @@ def test_ctypes_structs_match_the_c_header(tmp_path):
         pytest.skip("gcc not available")
     structs = {"pt_instance": pt.pt_instance, "pt_rung": pt.pt_rung, "pt_options": pt.pt_options,
                "pt_observables": pt.pt_observables, "pt_info": pt.pt_info, "pt_request": pt.pt_request,
-               "pt_batch_info": pt.pt_batch_info, "pt_device_problem": pt.pt_device_problem}
+               "pt_batch_info": pt.pt_batch_info, "pt_device_problem": pt.pt_device_problem,
+               "pt_server_options": pt.pt_server_options, "pt_server_info": pt.pt_server_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pt.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))

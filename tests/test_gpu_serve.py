@@ -1,0 +1,87 @@
+"""Continuous batching (pt_server_*): requests submitted at different times share launches
+with whatever else is on the device, and each result is the same as the request run alone
+(pt_create + pt_run) and as the oracle."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_1004_0023_gb300 import instances, pt, serve
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(libpt):
+    return libpt
+
+
+def _requests(count, seed, sweep_range):
+    rng = np.random.default_rng(seed)
+    probs = instances.batch_problems(count=count, index=seed, n_sweeps=1, n_range=(16, 96), r_range=(2, 12),
+                                     p_choices=(8, 16, 32))
+    for p in probs:
+        p.n_sweeps = int(rng.integers(sweep_range[0], sweep_range[1] + 1))
+        p.sweeps_per_swap = int(rng.integers(1, 4))
+    return probs
+
+
+def _same(a_state, a_obs, b_state, b_obs, where):
+    assert np.array_equal(a_state, b_state), where
+    for key in b_obs:
+        assert np.array_equal(np.asarray(a_obs[key]), np.asarray(b_obs[key])), (where, key)
+
+
+@pytest.mark.parametrize("arena_bytes,max_active", [(0, 512), (1 << 20, 3)])
+def test_results_are_the_same_alone_and_in_the_mix(arena_bytes, max_active):
+    """Requests arrive over several steps; a small arena / slot count forces queueing."""
+    probs = _requests(14, 5, (20, 90))
+    srv = pt.Server(arena_bytes=arena_bytes, max_active=max_active, quantum_sweeps=16)
+    pending = list(enumerate(probs))
+    ids, results, mix = {}, {}, 0
+    while len(results) < len(probs):
+        for _ in range(3):  # a few new arrivals before every step
+            if pending:
+                k, p = pending.pop(0)
+                ids[srv.submit(p)] = k
+        mix = max(mix, srv.info().active)
+        for rid in srv.step():
+            results[ids[rid]] = srv.result(rid)
+            srv.release(rid)
+        mix = max(mix, srv.info().active)
+    assert mix >= 2 or max_active < 2
+    for k, p in enumerate(probs):
+        alone = pt.PT.from_problem(p)
+        alone.run(p.n_sweeps, p.sweeps_per_swap)
+        _same(results[k][0], results[k][1], alone.read_state(), alone.obs(), "request %d vs alone" % k)
+        alone.close()
+    for k in (0, 7):
+        o = Oracle.from_problem(probs[k], threads=THREADS)
+        o.run(probs[k].n_sweeps, probs[k].sweeps_per_swap)
+        _same(results[k][0], results[k][1], o.read_state(), o.obs(), "request %d vs oracle" % k)
+    info = srv.info()
+    assert info.active == 0 and info.queued == 0 and info.arena_used == 0
+    srv.close()
+
+
+def test_server_rejects_a_request_larger_than_its_arena():
+    srv = pt.Server(arena_bytes=1 << 16, max_active=4, quantum_sweeps=8)
+    big = _requests(1, 9, (10, 10))[0]
+    big.n, big.R = big.n, big.R
+    rng = np.random.default_rng(3)
+    huge = instances.make_problem("regular", rng, n=512, degree=3, P=64, R=16, n_sweeps=5)
+    with pytest.raises(pt.PTError) as e:
+        srv.submit(huge)
+    assert e.value.code == pt.PT_ENOMEM
+    srv.close()
+
+
+def test_poisson_replay_batched_and_plain_complete_every_request():
+    trace = [(0.002 * i, p) for i, p in enumerate(_requests(10, 11, (30, 60)))]
+    b = serve.replay_batched(trace, quantum_sweeps=16)
+    p = serve.replay_plain(trace)
+    assert b["completed"] == 10 and p["completed"] == 10
+    assert b["p99_s"] >= b["p50_s"] > 0 and p["p99_s"] >= p["p50_s"] > 0
