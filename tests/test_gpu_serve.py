@@ -69,8 +69,6 @@ def test_results_are_the_same_alone_and_in_the_mix(arena_bytes, max_active):
 
 def test_server_rejects_a_request_larger_than_its_arena():
     srv = pt.Server(arena_bytes=1 << 16, max_active=4, quantum_sweeps=8)
-    big = _requests(1, 9, (10, 10))[0]
-    big.n, big.R = big.n, big.R
     rng = np.random.default_rng(3)
     huge = instances.make_problem("regular", rng, n=512, degree=3, P=64, R=16, n_sweeps=5)
     with pytest.raises(pt.PTError) as e:
