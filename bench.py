@@ -51,6 +51,12 @@ def parse_args(argv=None):
     ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per step (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-sweeps", type=int, default=1000)
+    ap.add_argument("--serving-seconds", type=float, default=10.0)
+    ap.add_argument("--serving-rate", type=float, default=200.0)
     return ap.parse_args(argv)
 
 
@@ -217,6 +223,12 @@ def run_ours(args, rank, world, local_rank):
         cpu = cpu_baseline(prob, budget_s=12.0)
 
     ctx.close()
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, pt, instances, torch, n_sm, sm_max)
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = run_serving(args, torch, batched)
     if rank != 0:
         return None
     return {
@@ -240,7 +252,89 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "wall_s_timed_region": wall,
+        "batched": batched,
+        "serving": serving,
     }
+
+
+def run_batched(args, pt, instances, torch, n_sm, sm_max):
+    """Many independent requests in one persistent launch vs one pt_run per request.
+
+    Workload: `batch_count` requests, N ~ U{32..1024} (3-regular or K4,4 cells), P ~ U{32,64,128},
+    R ~ U{16..128}, `batch_sweeps` sweeps each, a swap pass after every sweep."""
+    probs = instances.batch_problems(count=args.batch_count, index=1, n_sweeps=args.batch_sweeps)
+    attempts = sum(p.attempts_per_sweep * p.n_sweeps for p in probs)
+    stream = torch.cuda.Stream()
+    b = pt.Batch(probs, cluster_size=2, stream=stream.cuda_stream)
+    info = b.info()
+    b.run()
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run()
+    e1.record(stream)
+    b.sync()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    b.close()
+    # plain path: every request through its own pt_create + pt_run, one after another
+    ctxs = []
+    for p in probs:
+        ctxs.append(pt.PT.from_problem(p, stream=stream.cuda_stream))
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for c, p in zip(ctxs, probs):
+        c.run(p.n_sweeps, p.sweeps_per_swap)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+    plain_launches = sum(int(c.get_info().kernel_launches) for c in ctxs)
+    for c in ctxs:
+        c.close()
+    value = attempts / (ms / 1e3)
+    deg = [max(np.bincount(np.concatenate([p.ei, p.ej]), minlength=p.n)) for p in probs]
+    ialg = float(np.average([alg_instr_per_attempt(int(d)) for d in deg],
+                            weights=[p.attempts_per_sweep * p.n_sweeps for p in probs]))
+    peak = n_sm * 128 * sm_max * 1e6 / 1e12
+    return {"workload": "%d requests, N~U{32..1024} 3-regular or K4,4 cells, P~U{32,64,128}, R~U{16..128}, "
+                        "%d sweeps, swap pass after every sweep" % (args.batch_count, args.batch_sweeps),
+            "value": value, "unit": "attempts/s", "ms": ms, "attempts": attempts,
+            "plain_value": attempts / (plain_ms / 1e3), "plain_ms": plain_ms,
+            "speedup_vs_plain": plain_ms / ms, "gpu_launches": 1, "plain_gpu_launches": plain_launches,
+            "cluster": info.cluster, "n_clusters": info.n_clusters, "smem_bytes": int(info.smem_bytes),
+            "roofline": {"bound": "alu", "achieved": ialg * value / 1e12, "peak": peak, "unit": "Tinstr/s",
+                         "frac": ialg * value / 1e12 / peak, "kernel": "batch_kernel"}}
+
+
+def run_serving(args, torch, batched):
+    """Poisson arrivals of requests from the batched size distribution, 500..5000 sweeps each."""
+    from paper_1004_0023_gb300 import serve
+
+    out = {"workload": "Poisson arrivals, sizes as the batched workload, sweeps~U{500..5000}, swap every sweep",
+           "arrival_seconds": args.serving_seconds}
+    stream = torch.cuda.Stream()
+    trace = serve.poisson_trace(args.serving_rate, args.serving_seconds, seed=2)
+    offered = sum(p.attempts_per_sweep * p.n_sweeps for _, p in trace) / max(args.serving_seconds, 1e-9)
+    res = serve.replay_batched(trace, quantum_sweeps=100, stream=stream.cuda_stream,
+                               deadline=args.serving_seconds + 30.0)
+    res["rate_per_s"] = args.serving_rate
+    res["offered_attempts_per_s"] = offered
+    res["arrived"] = len(trace)
+    out["at_configured_rate"] = res
+    # a rate the batched server sustains (half its measured batched capacity), both modes
+    if batched:
+        mean_work = np.mean([p.attempts_per_sweep * p.n_sweeps for _, p in trace]) if trace else 1.0
+        rate = max(1.0, 0.5 * batched["value"] / mean_work)
+        trace2 = serve.poisson_trace(rate, args.serving_seconds, seed=3)
+        b = serve.replay_batched(trace2, quantum_sweeps=100, stream=stream.cuda_stream,
+                                 deadline=args.serving_seconds + 30.0)
+        p = serve.replay_plain(trace2, stream=stream.cuda_stream, deadline=args.serving_seconds + 30.0)
+        for r in (b, p):
+            r["rate_per_s"] = rate
+            r["arrived"] = len(trace2)
+        out["at_half_capacity"] = {"batched": b, "plain": p}
+    return out
 
 
 def run_e2e(args, prob, pt, torch):
