@@ -224,9 +224,11 @@ const char* pt_batch_last_error(const pt_batch* b);
 /* ---- Serving: continuous batching ----------------------------------------------------
  * A request (pt_request) is copied and queued by pt_server_submit. pt_server_step admits
  * queued requests in arrival order while a slot (max_active) and room in the device arena
- * are free, then runs one batched launch in which every admitted request advances by up
- * to quantum_sweeps sweeps (whole swap intervals) with its state and counters resident in
- * the arena; it reports the ids of requests that have finished. Results are read with
+ * are free, then runs one launch in which every admitted request advances by up to
+ * quantum_sweeps sweeps (whole swap intervals) with its state and counters resident in the
+ * arena; it reports the ids of requests that have finished. When all admitted chains fit on
+ * the device at once the launch gives every chain its own CTA (latency at light load),
+ * otherwise it packs chains onto clusters (throughput at heavy load). Results are read with
  * pt_server_read_result and the arena room is returned by pt_server_release. Each result
  * equals pt_create + pt_run of that request alone. Same request limits as pt_batch. */
 typedef struct pt_server pt_server;
@@ -236,7 +238,7 @@ typedef struct {
     int32_t max_active;     /* requests on the device at once (0 = 512) */
     int32_t quantum_sweeps; /* sweeps per request per step (0 = 100) */
     int32_t cluster_size;   /* CTAs per cluster (0 = 2) */
-    int32_t reserved[3];
+    int32_t reserved[3];    /* reserved[0] = 1: never use the wide launch shape (tests) */
 } pt_server_options;
 
 typedef struct {
@@ -246,6 +248,7 @@ typedef struct {
     int64_t arena_used;
     int64_t steps;
     int64_t kernel_launches;
+    int64_t wide_steps;     /* steps that ran one CTA per chain (the rest packed chains) */
 } pt_server_info;
 
 int pt_server_create(const pt_server_options* opt, void* cuda_stream, pt_server** out);

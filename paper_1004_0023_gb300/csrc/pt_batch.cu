@@ -505,7 +505,7 @@ int ptq::prepare_request(const pt_request& r, Prepared& pr, char* why, size_t wh
 }
 
 // Offsets of one request's data inside a block of its own (constants, then state).
-size_t ptq::request_block_layout(Prepared& p) {
+size_t ptq::request_block_layout(Prepared& p, size_t mailbox_entries) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -524,6 +524,7 @@ size_t ptq::request_block_layout(Prepared& p) {
     p.off_slot = take((size_t)p.R * 4);
     p.off_acc = take((size_t)p.R * kAccCount * 8);
     p.off_sw = take((size_t)p.R * 16);
+    p.off_mbox = take(mailbox_entries * sizeof(Mailbox));
     return off;
 }
 

@@ -120,6 +120,18 @@ cudaError_t launch_scatter_state(const DevProblem& p, const int8_t* in, cudaStre
 cudaError_t sweep_kernel_occupancy(const DevProblem& p, const LaunchPlan& plan, int* blocks_per_sm);
 cudaError_t prepare_sweep_kernel(const LaunchPlan& plan);
 
+// One problem of a multi-problem cooperative launch (one CTA per chain of every problem).
+struct MultiProblem {
+    DevProblem p;
+    int dc;                    // packed neighbour slots: 4 or 8
+    int n_sweeps, sweeps_per_swap;
+    long long t0, q0, timeout_ns;
+};
+size_t multi_smem_bytes(const DevProblem& p, int dc);
+cudaError_t multi_prepare(int threads, size_t smem, int* blocks_per_sm);
+cudaError_t launch_multi(const MultiProblem* probs, const int2* map, int n_blocks, int threads, size_t smem,
+                         cudaStream_t s);
+
 // Host-side preparation shared by single and batched problems (pt_host.cu).
 void build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vector<uint32_t>& thr,
                   std::vector<double>& coef);
@@ -135,11 +147,11 @@ struct Prepared {
     std::vector<int32_t> level_off;
     std::vector<double> coef;
     size_t off_sdesc, off_items, off_loff, off_thr, off_coef, off_spins, off_E, off_M, off_rung, off_slot, off_acc,
-        off_sw;
+        off_sw, off_mbox = 0;
     long long sweep_limit;
 };
 int prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len);
-size_t request_block_layout(Prepared& p);
+size_t request_block_layout(Prepared& p, size_t mailbox_entries = 0);
 void fill_instance(BatchInstance& I, const Prepared& p, unsigned char* base, const pt_request& r);
 void choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_cap);
 

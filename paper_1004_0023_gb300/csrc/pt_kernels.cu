@@ -347,14 +347,12 @@ __device__ __forceinline__ void produce_words(uint4* buf, uint32_t t, const uint
 // random words of sweep s+1 into one shared buffer while the consumer warps run the levels
 // of sweep s out of the other; consumers synchronise levels on named barrier 1 and both
 // groups meet once per sweep.
-template <int DC, bool PRE, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1)
-sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
-                    long long timeout_ns, int n_consumer) {
-    extern __shared__ __align__(16) unsigned char smem[];
+template <int DC, bool PRE>
+__device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot, long long t0, long long q0,
+                                                  int n_sweeps, int sweeps_per_swap, long long timeout_ns,
+                                                  int n_consumer, unsigned char* smem) {
     const int N = p.N, P = p.P;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int slot = blockIdx.x;
     const FastLayout L(p, DC, PRE);
     int8_t* sp = reinterpret_cast<int8_t*>(smem + L.spins);
     uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem + L.desc);
@@ -471,6 +469,48 @@ sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int 
         p.rung_of_slot[slot] = rung;
         p.slot_of_rung[rung] = slot;
     }
+}
+
+template <int DC, bool PRE, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
+                    long long timeout_ns, int n_consumer) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    sweep_packed_body<DC, PRE>(p, blockIdx.x, t0, q0, n_sweeps, sweeps_per_swap, timeout_ns, n_consumer, smem);
+}
+
+// Several problems in one cooperative launch (all chains resident at once): block b sweeps
+// chain map[b].y of problem map[b].x with the random words computed inline. Swap passes use
+// each problem's own mailboxes, so problems never wait for one another.
+__global__ void __launch_bounds__(512, 1) sweep_packed_multi_kernel(const MultiProblem* probs, const int2* map) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int2 m = map[blockIdx.x];
+    const MultiProblem mp = probs[m.x];
+    if (mp.dc == 4)
+        sweep_packed_body<4, false>(mp.p, m.y, mp.t0, mp.q0, mp.n_sweeps, mp.sweeps_per_swap, mp.timeout_ns,
+                                    blockDim.x, smem);
+    else
+        sweep_packed_body<8, false>(mp.p, m.y, mp.t0, mp.q0, mp.n_sweeps, mp.sweeps_per_swap, mp.timeout_ns,
+                                    blockDim.x, smem);
+}
+
+size_t multi_smem_bytes(const DevProblem& p, int dc) { return FastLayout(p, dc, false).total; }
+
+cudaError_t multi_prepare(int threads, size_t smem, int* blocks_per_sm) {
+    int dev = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep_packed_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sweep_packed_multi_kernel, threads, smem);
+}
+
+cudaError_t launch_multi(const MultiProblem* probs, const int2* map, int n_blocks, int threads, size_t smem,
+                         cudaStream_t s) {
+    void* args[] = {(void*)&probs, (void*)&map};
+    return cudaLaunchCooperativeKernel((const void*)sweep_packed_multi_kernel, dim3(n_blocks), dim3(threads), args,
+                                       smem, s);
 }
 
 // ------------------------------------------------------------------------- init / energy

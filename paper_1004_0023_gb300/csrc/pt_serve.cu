@@ -3,11 +3,17 @@
 // Requests arrive at any time (pt_server_submit) and wait in a FIFO until a slot and room
 // in a preallocated device arena are free; then their data and initial state are placed
 // in the arena, where their spins, (E, M), rung permutation, statistics and sweep / pass
-// counters stay until they finish. Every pt_server_step is one batched launch in which
-// each admitted request advances by up to `quantum` sweeps (whole swap intervals), so the
-// work of requests that arrived at different times overlaps on the device; requests that
-// complete are reported and admission runs again. A request's arithmetic never depends
-// on what else is in the launch: its result equals pt_create + pt_run on it alone.
+// counters stay until they finish. Every pt_server_step is one launch in which each
+// admitted request advances by up to `quantum` sweeps (whole swap intervals), so the work
+// of requests that arrived at different times overlaps on the device; requests that
+// complete are reported and admission runs again. Two launch shapes:
+//   wide   -- when every chain of every admitted request fits on the device at once, one
+//             cooperative launch with a CTA per chain (each request's swaps go through its
+//             own mailboxes), so a lightly loaded server gives a request as many SMs as it
+//             has chains;
+//   packed -- otherwise the batched cluster kernel, which packs many chains per CTA.
+// A request's arithmetic never depends on what else is in the launch or on the shape: its
+// result equals pt_create + pt_run on it alone.
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdint.h>
@@ -89,6 +95,12 @@ struct pt_server {
     unsigned char* arena;
     ArenaAllocator* alloc;
     int max_active, quantum, cluster, threads, n_clusters;
+    int wide_threads, n_sm;
+    bool wide;
+    MultiProblem* d_multi;
+    int2* d_wmap;
+    int wmap_capacity;
+    int64_t wide_steps;
     size_t smem_cap;
     std::map<int64_t, ServeReq*> reqs;
     std::deque<int64_t> queued;
@@ -142,6 +154,9 @@ extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream,
     s->quantum = (opt && opt->quantum_sweeps > 0) ? opt->quantum_sweeps : 100;
     s->cluster = (opt && opt->cluster_size > 0) ? opt->cluster_size : 2;
     s->threads = 512;
+    s->wide_threads = 256;
+    s->wide = !(opt && opt->reserved[0] == 1);  // reserved[0] == 1: packed launches only
+    s->wide_steps = 0;
     if (s->cluster > 16 || s->max_active > 65536) {
         delete s;
         return sfail(nullptr, PT_EINVAL, "cluster_size <= 16 and max_active <= 65536");
@@ -160,8 +175,10 @@ extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream,
     int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, dev);
     s->smem_cap = (size_t)max_smem - 1024;
     s->map_capacity = 1 << 16;
+    s->wmap_capacity = s->n_sm * 8;
     void* p = nullptr;
     cudaError_t e;
     auto grab = [&](size_t bytes) -> void* {
@@ -176,7 +193,10 @@ extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream,
     s->d_counter = (int*)grab(16);
     s->d_status = (int*)grab(16);
     s->d_map = (int2*)grab(sizeof(int2) * s->map_capacity);
-    if (!s->arena || !s->d_inst || !s->d_order || !s->d_counter || !s->d_status || !s->d_map) {
+    s->d_multi = (MultiProblem*)grab(sizeof(MultiProblem) * s->max_active);
+    s->d_wmap = (int2*)grab(sizeof(int2) * s->wmap_capacity);
+    if (!s->arena || !s->d_inst || !s->d_order || !s->d_counter || !s->d_status || !s->d_map || !s->d_multi ||
+        !s->d_wmap) {
         free_server(s);
         return sfail(nullptr, PT_ENOMEM, "could not allocate the serving arena (%zu bytes)", arena_bytes);
     }
@@ -206,7 +226,8 @@ extern "C" int pt_server_submit(pt_server* s, const pt_request* r, int64_t* id) 
         delete q;
         return sfail(s, rc, "%s", why);
     }
-    q->block_bytes = request_block_layout(q->prep);
+    // mailboxes for the wide launch shape: one entry per rung per swap pass of a step
+    q->block_bytes = request_block_layout(q->prep, (size_t)s->quantum * q->prep.R);
     if (q->block_bytes > s->alloc->size()) {
         delete q;
         return sfail(s, PT_ENOMEM, "request needs %zu bytes, the arena holds %zu", q->block_bytes, s->alloc->size());
@@ -309,6 +330,73 @@ extern "C" int pt_server_step(pt_server* s, int64_t* done_ids, int32_t max_done,
             I.n_sweeps = (int)c;
             insts.push_back(I);
         }
+        // ---- wide shape: every chain of every admitted request on its own CTA
+        bool ran = false;
+        if (s->wide) {
+            std::vector<MultiProblem> mps(insts.size());
+            std::vector<int2> wmap;
+            size_t wsmem = 0;
+            for (size_t a = 0; a < insts.size(); ++a) {
+                const BatchInstance& I = insts[a];
+                ServeReq* q = s->reqs[s->active[a]];
+                MultiProblem& mp = mps[a];
+                memset(&mp, 0, sizeof(mp));
+                DevProblem& p = mp.p;
+                p.desc = I.sdesc;
+                p.items = I.items;
+                p.level_off = I.level_off;
+                p.thr = I.thr;
+                p.coef = I.coef;
+                p.spins = I.spins;
+                p.E = I.E;
+                p.M = I.M;
+                p.rung_of_slot = I.rung_of_slot;
+                p.slot_of_rung = I.slot_of_rung;
+                p.acc = I.acc;
+                p.swap_stats = I.swap_stats;
+                p.mbox = (Mailbox*)(s->arena + q->block_off + q->prep.off_mbox);
+                p.status = s->d_status;
+                p.N = I.N;
+                p.P = I.P;
+                p.R = I.R;
+                p.Lmax = I.Lmax;
+                p.nL3 = I.nL3;
+                p.n_levels = I.n_levels;
+                p.dmax = I.dc;
+                p.slot_stride = I.slot_stride;
+                p.withhold_rung = -1;
+                p.key0 = I.key0;
+                p.key1 = I.key1;
+                p.acc_in_smem = (size_t)I.R * kAccCount * 8 <= 16384 ? 1 : 0;
+                p.tables_in_smem = (size_t)I.R * I.nL3 * 4 <= 49152 ? 1 : 0;
+                if (p.tables_in_smem && multi_smem_bytes(p, I.dc) > s->smem_cap) p.tables_in_smem = 0;
+                mp.dc = I.dc;
+                mp.n_sweeps = I.n_sweeps;
+                mp.sweeps_per_swap = I.sweeps_per_swap;
+                mp.t0 = I.t0;
+                mp.q0 = I.q0;
+                mp.timeout_ns = 5000000000ll;
+                wsmem = std::max(wsmem, multi_smem_bytes(p, I.dc));
+                for (int rho = 0; rho < I.R; ++rho) wmap.push_back(make_int2((int)a, rho));
+            }
+            int per_sm = 0;
+            const bool fits = wsmem <= s->smem_cap && (int)wmap.size() <= s->wmap_capacity &&
+                              multi_prepare(s->wide_threads, wsmem, &per_sm) == cudaSuccess &&
+                              (long long)per_sm * s->n_sm >= (long long)wmap.size();
+            if (fits) {
+                cudaError_t e;
+                if ((e = cudaMemcpyAsync(s->d_multi, mps.data(), mps.size() * sizeof(MultiProblem),
+                                         cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
+                    (e = cudaMemcpyAsync(s->d_wmap, wmap.data(), wmap.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                         s->stream)) != cudaSuccess ||
+                    (e = launch_multi(s->d_multi, s->d_wmap, (int)wmap.size(), s->wide_threads, wsmem, s->stream)) !=
+                        cudaSuccess)
+                    return sfail(s, PT_ECUDA, "wide launch: %s", cudaGetErrorString(e));
+                s->launches += 1;
+                s->wide_steps += 1;
+                ran = true;
+            }
+        }
         std::vector<int32_t> order(insts.size());
         for (size_t a = 0; a < order.size(); ++a) order[a] = (int32_t)a;
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -332,11 +420,20 @@ extern "C" int pt_server_step(pt_server* s, int64_t* done_ids, int32_t max_done,
         bp.next_job = s->d_counter;
         bp.status = s->d_status;
         const int ncl = std::min<int>(s->n_clusters, (int)insts.size());
-        if ((e = launch_batch(bp, s->cluster, ncl, s->threads, smem, s->stream)) != cudaSuccess)
-            return sfail(s, PT_ECUDA, "batch launch: %s", cudaGetErrorString(e));
-        s->launches += 1;
+        if (!ran) {
+            if ((e = launch_batch(bp, s->cluster, ncl, s->threads, smem, s->stream)) != cudaSuccess)
+                return sfail(s, PT_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+            s->launches += 1;
+        }
         if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
             return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+        {
+            int st = 0;
+            if ((e = cudaMemcpy(&st, s->d_status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+                return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+            if (st == PT_ETIMEDOUT) return sfail(s, PT_ETIMEDOUT, "a swap wait timed out");
+            if (st) return sfail(s, PT_ECUDA, "device status %d", st);
+        }
         s->steps += 1;
         std::vector<int64_t> still;
         for (size_t a = 0; a < s->active.size(); ++a) {
@@ -441,6 +538,7 @@ extern "C" int pt_server_get_info(const pt_server* s, pt_server_info* o) {
     o->arena_used = (int64_t)s->alloc->used();
     o->steps = s->steps;
     o->kernel_launches = s->launches;
+    o->wide_steps = s->wide_steps;
     return PT_OK;
 }
 

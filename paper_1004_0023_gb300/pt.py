@@ -69,7 +69,7 @@ class pt_server_options(ctypes.Structure):
 
 class pt_server_info(ctypes.Structure):
     _fields_ = [("active", _i32), ("queued", _i32), ("arena_bytes", _i64), ("arena_used", _i64), ("steps", _i64),
-                ("kernel_launches", _i64)]
+                ("kernel_launches", _i64), ("wide_steps", _i64)]
 
 
 class pt_device_problem(ctypes.Structure):
@@ -371,9 +371,11 @@ def _request(prob, keep):
 class Server:
     """Continuous-batching server (include/pt.h, pt_server_*)."""
 
-    def __init__(self, arena_bytes=0, max_active=0, quantum_sweeps=0, cluster_size=0, stream=None):
+    def __init__(self, arena_bytes=0, max_active=0, quantum_sweeps=0, cluster_size=0, stream=None,
+                 packed_only=False):
         self.lib = load()
         opt = pt_server_options(int(arena_bytes), int(max_active), int(quantum_sweeps), int(cluster_size))
+        opt.reserved[0] = 1 if packed_only else 0
         h = _vp()
         rc = self.lib.pt_server_create(ctypes.byref(opt), None if stream is None else _vp(int(stream)),
                                        ctypes.byref(h))

@@ -45,10 +45,10 @@ def _summary(lat, attempts, wall, extra):
 
 
 def replay_batched(trace, quantum_sweeps=100, max_active=512, arena_bytes=0, cluster_size=0, stream=None,
-                   deadline=None):
+                   deadline=None, packed_only=False):
     """Drive the continuous-batching server in real time; stop admitting new work after `deadline` s."""
     srv = pt.Server(arena_bytes=arena_bytes, max_active=max_active, quantum_sweeps=quantum_sweeps,
-                    cluster_size=cluster_size, stream=stream)
+                    cluster_size=cluster_size, stream=stream, packed_only=packed_only)
     arrival = {}
     done_t = {}
     attempts = {}
@@ -78,7 +78,8 @@ def replay_batched(trace, quantum_sweeps=100, max_active=512, arena_bytes=0, clu
     info = srv.info()
     out = _summary(lat, sum(attempts[r] for r in done_t), wall,
                    {"mode": "batched", "submitted": k, "max_active_seen": max_mix, "steps": int(info.steps),
-                    "kernel_launches": int(info.kernel_launches), "quantum_sweeps": quantum_sweeps})
+                    "wide_steps": int(info.wide_steps), "kernel_launches": int(info.kernel_launches),
+                    "quantum_sweeps": quantum_sweeps})
     srv.close()
     return out
 

@@ -35,11 +35,12 @@ def _same(a_state, a_obs, b_state, b_obs, where):
         assert np.array_equal(np.asarray(a_obs[key]), np.asarray(b_obs[key])), (where, key)
 
 
-@pytest.mark.parametrize("arena_bytes,max_active", [(0, 512), (1 << 20, 3)])
-def test_results_are_the_same_alone_and_in_the_mix(arena_bytes, max_active):
-    """Requests arrive over several steps; a small arena / slot count forces queueing."""
+@pytest.mark.parametrize("arena_bytes,max_active,packed_only", [(0, 512, False), (0, 512, True), (1 << 20, 3, False)])
+def test_results_are_the_same_alone_and_in_the_mix(arena_bytes, max_active, packed_only):
+    """Requests arrive over several steps; a small arena / slot count forces queueing; both
+    launch shapes (a CTA per chain, or chains packed on clusters) give the same bits."""
     probs = _requests(14, 5, (20, 90))
-    srv = pt.Server(arena_bytes=arena_bytes, max_active=max_active, quantum_sweeps=16)
+    srv = pt.Server(arena_bytes=arena_bytes, max_active=max_active, quantum_sweeps=16, packed_only=packed_only)
     pending = list(enumerate(probs))
     ids, results, mix = {}, {}, 0
     while len(results) < len(probs):
@@ -64,6 +65,10 @@ def test_results_are_the_same_alone_and_in_the_mix(arena_bytes, max_active):
         _same(results[k][0], results[k][1], o.read_state(), o.obs(), "request %d vs oracle" % k)
     info = srv.info()
     assert info.active == 0 and info.queued == 0 and info.arena_used == 0
+    if packed_only:
+        assert info.wide_steps == 0
+    else:
+        assert info.wide_steps > 0
     srv.close()
 
 
