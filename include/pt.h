@@ -222,13 +222,13 @@ int pt_batch_destroy(pt_batch* b);
 const char* pt_batch_last_error(const pt_batch* b);
 
 /* ---- Serving: continuous batching ----------------------------------------------------
- * A request (pt_request) is copied and queued by pt_server_submit. pt_server_step admits
- * queued requests in arrival order while a slot (max_active) and room in the device arena
- * are free, then runs one launch in which every admitted request advances by up to
- * quantum_sweeps sweeps (whole swap intervals) with its state and counters resident in the
- * arena; it reports the ids of requests that have finished. When all admitted chains fit on
- * the device at once the launch gives every chain its own CTA (latency at light load),
- * otherwise it packs chains onto clusters (throughput at heavy load). Results are read with
+ * A request (pt_request) is copied and queued by pt_server_submit. pt_server_step never
+ * blocks: it reports the requests that have finished, then admits queued requests in
+ * arrival order while a slot (max_active) and room in the device arena are free. An
+ * admitted request's state and counters live in the arena; all of its sweeps are launched
+ * at once on one stream of a pool (one CTA per chain), so requests that arrive while others
+ * run overlap with them on the device. In stepped mode each step instead advances every
+ * admitted request by quantum_sweeps sweeps in one launch and waits for it. Results are read with
  * pt_server_read_result and the arena room is returned by pt_server_release. Each result
  * equals pt_create + pt_run of that request alone. Same request limits as pt_batch. */
 typedef struct pt_server pt_server;
@@ -238,7 +238,8 @@ typedef struct {
     int32_t max_active;     /* requests on the device at once (0 = 512) */
     int32_t quantum_sweeps; /* sweeps per request per step (0 = 100) */
     int32_t cluster_size;   /* CTAs per cluster (0 = 2) */
-    int32_t reserved[3];    /* reserved[0] = 1: never use the wide launch shape (tests) */
+    int32_t reserved[3];    /* reserved[1] = 1: stepped mode (a quantum of sweeps per launch);
+                               reserved[0] = 1: stepped mode with chains packed on clusters only */
 } pt_server_options;
 
 typedef struct {

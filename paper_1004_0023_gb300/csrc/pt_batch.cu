@@ -525,6 +525,9 @@ size_t ptq::request_block_layout(Prepared& p, size_t mailbox_entries) {
     p.off_acc = take((size_t)p.R * kAccCount * 8);
     p.off_sw = take((size_t)p.R * 16);
     p.off_mbox = take(mailbox_entries * sizeof(Mailbox));
+    p.off_inst = take(sizeof(BatchInstance));
+    p.off_map = take((size_t)p.R * sizeof(int2));
+    p.off_status = take(16);
     return off;
 }
 

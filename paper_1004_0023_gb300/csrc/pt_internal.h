@@ -147,7 +147,7 @@ struct Prepared {
     std::vector<int32_t> level_off;
     std::vector<double> coef;
     size_t off_sdesc, off_items, off_loff, off_thr, off_coef, off_spins, off_E, off_M, off_rung, off_slot, off_acc,
-        off_sw, off_mbox = 0;
+        off_sw, off_mbox = 0, off_inst = 0, off_map = 0, off_status = 0;
     long long sweep_limit;
 };
 int prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len);

@@ -6,13 +6,17 @@
 // counters stay until they finish. Every pt_server_step is one launch in which each
 // admitted request advances by up to `quantum` sweeps (whole swap intervals), so the work
 // of requests that arrived at different times overlaps on the device; requests that
-// complete are reported and admission runs again. Two launch shapes:
-//   wide   -- when every chain of every admitted request fits on the device at once, one
-//             cooperative launch with a CTA per chain (each request's swaps go through its
-//             own mailboxes), so a lightly loaded server gives a request as many SMs as it
-//             has chains;
-//   packed -- otherwise the batched cluster kernel, which packs many chains per CTA.
-// A request's arithmetic never depends on what else is in the launch or on the shape: its
+// complete are reported and admission runs again.
+//
+// Default (streamed) mode: every admitted request is launched at once, with all of its
+// sweeps, on one stream of a pool -- one CTA per chain, the launch plan pt_create would
+// choose -- and its completion is tracked with an event. Requests that arrive while others
+// run start as soon as a slot and arena room free up, and the GPU runs their kernels side
+// by side as SMs become free, so the device does the continuous batching at CTA
+// granularity. Stepped mode (pt_server_options.reserved[1] = 1) instead advances all
+// admitted requests by a quantum of sweeps per launch, one CTA per chain when they all fit
+// (wide), chains packed onto clusters otherwise (packed).
+// A request's arithmetic never depends on what else runs or on the launch shape: its
 // result equals pt_create + pt_run on it alone.
 #include <cuda_runtime.h>
 #include <stdarg.h>
@@ -85,7 +89,13 @@ struct ServeReq {
     BatchInstance inst;
     int64_t remaining = 0;
     int state = 0;  // 0 queued, 1 on the device, 2 finished
+    // streamed mode
+    cudaEvent_t done = nullptr;
+    int stream_idx = 0;
 };
+
+// Streamed mode launches a request's sweeps in pieces of at most this many swap passes.
+constexpr int kStreamedPasses = 256;
 
 }  // namespace
 
@@ -101,6 +111,9 @@ struct pt_server {
     int2* d_wmap;
     int wmap_capacity;
     int64_t wide_steps;
+    bool streamed;
+    std::vector<cudaStream_t> pool;
+    int next_stream;
     size_t smem_cap;
     std::map<int64_t, ServeReq*> reqs;
     std::deque<int64_t> queued;
@@ -130,7 +143,14 @@ static int sfail(pt_server* s, int code, const char* fmt, ...) {
 }
 
 static void free_server(pt_server* s) {
-    for (auto& kv : s->reqs) delete kv.second;
+    for (cudaStream_t st : s->pool) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    for (auto& kv : s->reqs) {
+        if (kv.second->done) cudaEventDestroy(kv.second->done);
+        delete kv.second;
+    }
     for (void* p : s->allocs) cudaFree(p);
     delete s->alloc;
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -155,7 +175,9 @@ extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream,
     s->cluster = (opt && opt->cluster_size > 0) ? opt->cluster_size : 2;
     s->threads = 512;
     s->wide_threads = 256;
-    s->wide = !(opt && opt->reserved[0] == 1);  // reserved[0] == 1: packed launches only
+    s->wide = !(opt && opt->reserved[0] == 1);    // reserved[0] == 1: stepped, packed launches only
+    s->streamed = !(opt && (opt->reserved[1] == 1 || opt->reserved[0] == 1));  // reserved[1] == 1: stepped
+    s->next_stream = 0;
     s->wide_steps = 0;
     if (s->cluster > 16 || s->max_active > 65536) {
         delete s;
@@ -212,6 +234,16 @@ extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream,
         return sfail(nullptr, PT_EINVAL, "no cluster of %d CTAs fits (%s)", s->cluster, cudaGetErrorString(e));
     }
     s->n_clusters = ncl;
+    if (s->streamed) {
+        for (int k = 0; k < 16; ++k) {
+            cudaStream_t st;
+            if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+                free_server(s);
+                return sfail(nullptr, PT_ECUDA, "cudaStreamCreate failed");
+            }
+            s->pool.push_back(st);
+        }
+    }
     *out = s;
     return PT_OK;
 }
@@ -227,7 +259,7 @@ extern "C" int pt_server_submit(pt_server* s, const pt_request* r, int64_t* id) 
         return sfail(s, rc, "%s", why);
     }
     // mailboxes for the wide launch shape: one entry per rung per swap pass of a step
-    q->block_bytes = request_block_layout(q->prep, (size_t)s->quantum * q->prep.R);
+    q->block_bytes = request_block_layout(q->prep, (size_t)std::max(s->quantum, kStreamedPasses) * q->prep.R);
     if (q->block_bytes > s->alloc->size()) {
         delete q;
         return sfail(s, PT_ENOMEM, "request needs %zu bytes, the arena holds %zu", q->block_bytes, s->alloc->size());
@@ -310,9 +342,190 @@ static int admit(pt_server* s) {
     return PT_OK;
 }
 
+// Streamed mode: place a request in the arena and launch all of its sweeps on a pool stream.
+static int launch_streamed(pt_server* s, ServeReq* q) {
+    cudaStream_t st = s->pool[s->next_stream];
+    q->stream_idx = s->next_stream;
+    s->next_stream = (s->next_stream + 1) % (int)s->pool.size();
+    unsigned char* base = s->arena + q->block_off;
+    const Prepared& pr = q->prep;
+    const int gthreads = q->inst.group_threads, resident = q->inst.resident;
+    fill_instance(q->inst, pr, base, q->req);
+    q->inst.group_threads = gthreads;
+    q->inst.resident = resident;
+    std::vector<unsigned char> host(pr.off_spins, 0);
+    memcpy(&host[pr.off_sdesc], pr.sdesc.data(), pr.sdesc.size() * 4);
+    memcpy(&host[pr.off_items], pr.items.data(), pr.items.size() * 4);
+    memcpy(&host[pr.off_loff], pr.level_off.data(), pr.level_off.size() * 4);
+    memcpy(&host[pr.off_thr], pr.thr.data(), pr.thr.size() * 4);
+    memcpy(&host[pr.off_coef], pr.coef.data(), pr.coef.size() * 8);
+    std::vector<int2> map(pr.R);
+    for (int rho = 0; rho < pr.R; ++rho) map[rho] = make_int2(0, rho);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(base, host.data(), host.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(base + pr.off_spins, 0, q->block_bytes - pr.off_spins, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(base + pr.off_inst, &q->inst, sizeof(BatchInstance), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(base + pr.off_map, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = launch_batch_init((const BatchInstance*)(base + pr.off_inst), (const int2*)(base + pr.off_map), pr.R,
+                               st)) != cudaSuccess)
+        return sfail(s, PT_ECUDA, "streamed admission: %s", cudaGetErrorString(e));
+    s->launches += 1;
+
+    // the single-problem packed kernel, as pt_create would plan it
+    DevProblem p;
+    memset(&p, 0, sizeof(p));
+    p.desc = q->inst.sdesc;
+    p.items = q->inst.items;
+    p.level_off = q->inst.level_off;
+    p.thr = q->inst.thr;
+    p.coef = q->inst.coef;
+    p.spins = q->inst.spins;
+    p.E = q->inst.E;
+    p.M = q->inst.M;
+    p.rung_of_slot = q->inst.rung_of_slot;
+    p.slot_of_rung = q->inst.slot_of_rung;
+    p.acc = q->inst.acc;
+    p.swap_stats = q->inst.swap_stats;
+    p.mbox = (Mailbox*)(base + pr.off_mbox);
+    p.status = (int*)(base + pr.off_status);
+    p.N = pr.N;
+    p.P = pr.P;
+    p.R = pr.R;
+    p.Lmax = pr.Lmax;
+    p.nL3 = (2 * pr.Lmax + 1) * 3;
+    p.n_levels = pr.n_levels;
+    p.dmax = pr.dc;
+    p.slot_stride = pr.slot_stride;
+    p.withhold_rung = -1;
+    p.key0 = q->inst.key0;
+    p.key1 = q->inst.key1;
+    p.acc_in_smem = (size_t)pr.R * kAccCount * 8 <= 16384 ? 1 : 0;
+    p.tables_in_smem = (size_t)pr.R * p.nL3 * 4 <= 49152 ? 1 : 0;
+    LaunchPlan plan;
+    plan.dclass = pr.dc;
+    plan.path = kPathPacked;
+    if (sweep_smem_bytes(p, kPathPacked, pr.dc) > s->smem_cap) plan.path = kPathPackedInline;
+    if (p.tables_in_smem && sweep_smem_bytes(p, plan.path, pr.dc) > s->smem_cap) p.tables_in_smem = 0;
+    if (p.acc_in_smem && sweep_smem_bytes(p, plan.path, pr.dc) > s->smem_cap) p.acc_in_smem = 0;
+    plan.smem_bytes = sweep_smem_bytes(p, plan.path, pr.dc);
+    if (plan.path == kPathPacked) {
+        plan.threads = 512;
+        plan.n_consumer = 384;
+    } else {
+        const long long units = 2ll * pr.N * (pr.P / 8);
+        long long avg = (units + pr.n_levels - 1) / pr.n_levels;
+        avg = ((avg + 31) / 32) * 32;
+        plan.threads = (int)std::min<long long>(512, std::max<long long>(128, avg));
+        plan.n_consumer = plan.threads;
+    }
+    if (prepare_sweep_kernel(plan) != cudaSuccess) return sfail(s, PT_ECUDA, "cudaFuncSetAttribute failed");
+    const int sps = q->inst.sweeps_per_swap;
+    const bool swaps = sps > 0 && pr.R > 1;
+    int per_sm = 0;
+    const bool coop = swaps && sweep_kernel_occupancy(p, plan, &per_sm) == cudaSuccess &&
+                      (long long)per_sm * s->n_sm >= pr.R;
+    long long t = q->inst.t0, qq = q->inst.q0;
+    long long left = q->remaining;
+    const long long timeout = 5000000000ll;
+    if (!swaps || coop) {
+        const long long full = swaps ? (left / sps) * sps : 0;
+        long long done = 0;
+        while (done < left) {
+            long long chunk;
+            int use_sps = 0;
+            if (done < full) {
+                chunk = std::min<long long>(full - done, (long long)kStreamedPasses * sps);
+                use_sps = sps;
+            } else {
+                chunk = left - done;
+            }
+            if ((e = launch_sweeps(p, plan, t, qq, (int)chunk, use_sps, timeout, use_sps > 0, st)) != cudaSuccess)
+                return sfail(s, PT_ECUDA, "streamed launch: %s", cudaGetErrorString(e));
+            s->launches += 1;
+            t += chunk;
+            if (use_sps > 0) qq += chunk / sps;
+            done += chunk;
+        }
+        if (!swaps && sps > 0) qq += left / sps;
+    } else {
+        // chains cannot all be resident: one launch per swap interval and a swap launch
+        for (long long done = 0; done + sps <= left; done += sps) {
+            if ((e = launch_sweeps(p, plan, t, qq, sps, 0, timeout, false, st)) != cudaSuccess ||
+                (e = launch_swap(p, qq, st)) != cudaSuccess)
+                return sfail(s, PT_ECUDA, "streamed launch: %s", cudaGetErrorString(e));
+            s->launches += 2;
+            t += sps;
+            qq += 1;
+        }
+        const long long rest = left % sps;
+        if (rest > 0) {
+            if ((e = launch_sweeps(p, plan, t, qq, (int)rest, 0, timeout, false, st)) != cudaSuccess)
+                return sfail(s, PT_ECUDA, "streamed launch: %s", cudaGetErrorString(e));
+            s->launches += 1;
+            t += rest;
+        }
+    }
+    if (!q->done && (e = cudaEventCreateWithFlags(&q->done, cudaEventDisableTiming)) != cudaSuccess)
+        return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+    if ((e = cudaEventRecord(q->done, st)) != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+    q->inst.t0 = t;
+    q->inst.q0 = qq;
+    q->remaining = 0;
+    q->state = 1;
+    return PT_OK;
+}
+
+static int step_streamed(pt_server* s) {
+    // completions first, so their arena room can go to queued requests
+    std::vector<int64_t> still;
+    for (int64_t id : s->active) {
+        ServeReq* q = s->reqs[id];
+        const cudaError_t e = cudaEventQuery(q->done);
+        if (e == cudaErrorNotReady) {
+            still.push_back(id);
+            continue;
+        }
+        if (e != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+        int st = 0;
+        const cudaError_t e2 =
+            cudaMemcpy(&st, s->arena + q->block_off + q->prep.off_status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e2 != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e2));
+        if (st == PT_ETIMEDOUT) return sfail(s, PT_ETIMEDOUT, "a swap wait timed out");
+        if (st) return sfail(s, PT_ECUDA, "device status %d", st);
+        q->state = 2;
+        s->finished_unreported.push_back(id);
+    }
+    s->active.swap(still);
+    while (!s->queued.empty() && (int)s->active.size() < s->max_active) {
+        ServeReq* q = s->reqs[s->queued.front()];
+        size_t off = 0;
+        if (!s->alloc->alloc(q->block_bytes, &off)) break;
+        q->block_off = off;
+        s->queued.pop_front();
+        const int rc = launch_streamed(s, q);
+        if (rc) return rc;
+        s->active.push_back(q->id);
+    }
+    s->steps += 1;
+    return PT_OK;
+}
+
 extern "C" int pt_server_step(pt_server* s, int64_t* done_ids, int32_t max_done, int32_t* n_done) {
     if (!s || !n_done || (max_done > 0 && !done_ids)) return PT_EINVAL;
     if (s->err) return s->err;
+    if (s->streamed) {
+        const int rc = step_streamed(s);
+        if (rc) return rc;
+        int n = 0;
+        while (n < max_done && !s->finished_unreported.empty()) {
+            done_ids[n++] = s->finished_unreported.front();
+            s->finished_unreported.pop_front();
+        }
+        *n_done = n;
+        return PT_OK;
+    }
     int rc = admit(s);
     if (rc) return rc;
     if (!s->active.empty()) {
@@ -525,6 +738,7 @@ extern "C" int pt_server_release(pt_server* s, int64_t id) {
     if (q->state == 1) return sfail(s, PT_EBUSY, "request %lld is still running", (long long)id);
     if (q->state == 0) s->queued.erase(std::find(s->queued.begin(), s->queued.end(), id));
     if (q->state == 2) s->alloc->release(q->block_off, q->block_bytes);
+    if (q->done) cudaEventDestroy(q->done);
     delete q;
     s->reqs.erase(it);
     return PT_OK;

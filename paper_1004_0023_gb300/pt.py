@@ -372,10 +372,11 @@ class Server:
     """Continuous-batching server (include/pt.h, pt_server_*)."""
 
     def __init__(self, arena_bytes=0, max_active=0, quantum_sweeps=0, cluster_size=0, stream=None,
-                 packed_only=False):
+                 stepped=False, packed_only=False):
         self.lib = load()
         opt = pt_server_options(int(arena_bytes), int(max_active), int(quantum_sweeps), int(cluster_size))
         opt.reserved[0] = 1 if packed_only else 0
+        opt.reserved[1] = 1 if stepped else 0
         h = _vp()
         rc = self.lib.pt_server_create(ctypes.byref(opt), None if stream is None else _vp(int(stream)),
                                        ctypes.byref(h))

@@ -45,10 +45,10 @@ def _summary(lat, attempts, wall, extra):
 
 
 def replay_batched(trace, quantum_sweeps=100, max_active=512, arena_bytes=0, cluster_size=0, stream=None,
-                   deadline=None, packed_only=False):
+                   deadline=None, stepped=False, packed_only=False, poll_s=0.0005):
     """Drive the continuous-batching server in real time; stop admitting new work after `deadline` s."""
     srv = pt.Server(arena_bytes=arena_bytes, max_active=max_active, quantum_sweeps=quantum_sweeps,
-                    cluster_size=cluster_size, stream=stream, packed_only=packed_only)
+                    cluster_size=cluster_size, stream=stream, stepped=stepped, packed_only=packed_only)
     arrival = {}
     done_t = {}
     attempts = {}
@@ -70,14 +70,17 @@ def replay_batched(trace, quantum_sweeps=100, max_active=512, arena_bytes=0, clu
                 time.sleep(max(0.0, min(trace[k][0] - now, 0.01)))
             continue
         max_mix = max(max_mix, info.active)
-        for rid in srv.step():
+        finished = srv.step()
+        for rid in finished:
             done_t[rid] = time.perf_counter() - t0
             srv.release(rid)
+        if not finished and not stepped:
+            time.sleep(poll_s)
     wall = (max(done_t.values()) if done_t else 0.0) - (trace[0][0] if trace else 0.0)
     lat = [done_t[r] - arrival[r] for r in done_t]
     info = srv.info()
     out = _summary(lat, sum(attempts[r] for r in done_t), wall,
-                   {"mode": "batched", "submitted": k, "max_active_seen": max_mix, "steps": int(info.steps),
+                   {"mode": "stepped" if stepped else "streamed", "submitted": k, "max_active_seen": max_mix, "steps": int(info.steps),
                     "wide_steps": int(info.wide_steps), "kernel_launches": int(info.kernel_launches),
                     "quantum_sweeps": quantum_sweeps})
     srv.close()

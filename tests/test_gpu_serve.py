@@ -35,12 +35,16 @@ def _same(a_state, a_obs, b_state, b_obs, where):
         assert np.array_equal(np.asarray(a_obs[key]), np.asarray(b_obs[key])), (where, key)
 
 
-@pytest.mark.parametrize("arena_bytes,max_active,packed_only", [(0, 512, False), (0, 512, True), (1 << 20, 3, False)])
-def test_results_are_the_same_alone_and_in_the_mix(arena_bytes, max_active, packed_only):
-    """Requests arrive over several steps; a small arena / slot count forces queueing; both
-    launch shapes (a CTA per chain, or chains packed on clusters) give the same bits."""
+@pytest.mark.parametrize("arena_bytes,max_active,stepped,packed_only",
+                         [(0, 512, False, False), (1 << 20, 3, False, False), (0, 512, True, False),
+                          (0, 512, True, True), (1 << 20, 3, True, False)])
+def test_results_are_the_same_alone_and_in_the_mix(arena_bytes, max_active, stepped, packed_only):
+    """Requests arrive over several steps; a small arena / slot count forces queueing; every
+    mode (streamed launches, stepped with a CTA per chain, stepped with chains packed on
+    clusters) gives each request the bits it gets alone."""
     probs = _requests(14, 5, (20, 90))
-    srv = pt.Server(arena_bytes=arena_bytes, max_active=max_active, quantum_sweeps=16, packed_only=packed_only)
+    srv = pt.Server(arena_bytes=arena_bytes, max_active=max_active, quantum_sweeps=16, stepped=stepped,
+                    packed_only=packed_only)
     pending = list(enumerate(probs))
     ids, results, mix = {}, {}, 0
     while len(results) < len(probs):
@@ -65,7 +69,7 @@ def test_results_are_the_same_alone_and_in_the_mix(arena_bytes, max_active, pack
         _same(results[k][0], results[k][1], o.read_state(), o.obs(), "request %d vs oracle" % k)
     info = srv.info()
     assert info.active == 0 and info.queued == 0 and info.arena_used == 0
-    if packed_only:
+    if packed_only or not stepped:
         assert info.wide_steps == 0
     else:
         assert info.wide_steps > 0
@@ -85,6 +89,8 @@ def test_server_rejects_a_request_larger_than_its_arena():
 def test_poisson_replay_batched_and_plain_complete_every_request():
     trace = [(0.002 * i, p) for i, p in enumerate(_requests(10, 11, (30, 60)))]
     b = serve.replay_batched(trace, quantum_sweeps=16)
+    st = serve.replay_batched(trace, quantum_sweeps=16, stepped=True)
     p = serve.replay_plain(trace)
-    assert b["completed"] == 10 and p["completed"] == 10
-    assert b["p99_s"] >= b["p50_s"] > 0 and p["p99_s"] >= p["p50_s"] > 0
+    for r in (b, st, p):
+        assert r["completed"] == 10
+        assert r["p99_s"] >= r["p50_s"] > 0
