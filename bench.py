@@ -312,12 +312,13 @@ def run_serving(args, torch, batched):
     from paper_1004_0023_gb300 import serve
 
     out = {"workload": "Poisson arrivals, sizes as the batched workload, sweeps~U{500..5000}, swap every sweep",
-           "arrival_seconds": args.serving_seconds}
+           "arrival_seconds": args.serving_seconds,
+           "server": "continuous batching: requests admitted as slots and arena room free up, each launched on a "
+                     "stream of a pool with one CTA per chain; plain = one request at a time, pt_create + pt_run"}
     stream = torch.cuda.Stream()
     trace = serve.poisson_trace(args.serving_rate, args.serving_seconds, seed=2)
     offered = sum(p.attempts_per_sweep * p.n_sweeps for _, p in trace) / max(args.serving_seconds, 1e-9)
-    res = serve.replay_batched(trace, quantum_sweeps=100, stream=stream.cuda_stream,
-                               deadline=args.serving_seconds + 30.0)
+    res = serve.replay_batched(trace, stream=stream.cuda_stream, deadline=args.serving_seconds + 30.0)
     res["rate_per_s"] = args.serving_rate
     res["offered_attempts_per_s"] = offered
     res["arrived"] = len(trace)
@@ -327,13 +328,12 @@ def run_serving(args, torch, batched):
         mean_work = np.mean([p.attempts_per_sweep * p.n_sweeps for _, p in trace]) if trace else 1.0
         rate = max(1.0, 0.5 * batched["value"] / mean_work)
         trace2 = serve.poisson_trace(rate, args.serving_seconds, seed=3)
-        b = serve.replay_batched(trace2, quantum_sweeps=100, stream=stream.cuda_stream,
-                                 deadline=args.serving_seconds + 30.0)
+        b = serve.replay_batched(trace2, stream=stream.cuda_stream, deadline=args.serving_seconds + 30.0)
         p = serve.replay_plain(trace2, stream=stream.cuda_stream, deadline=args.serving_seconds + 30.0)
         for r in (b, p):
             r["rate_per_s"] = rate
             r["arrived"] = len(trace2)
-        out["at_half_capacity"] = {"batched": b, "plain": p}
+        out["at_half_capacity"] = {"server": b, "plain": p}
     return out
 
 
