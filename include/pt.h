@@ -76,7 +76,9 @@ typedef struct {
                                    and the call fails with PT_ETIMEDOUT (no fault, no hang) */
     int32_t kernel_path;        /* 0 = auto, 1 = byte-wise, 2 = packed with inline random
                                    words, 3 = packed with random words produced one sweep
-                                   ahead by dedicated warps (needs P % 8 == 0, degree <= 7) */
+                                   ahead by dedicated warps, 4 = packed with one bit per
+                                   copy in shared memory (paths 2-4 need P % 8 == 0 and
+                                   degree <= 7) */
     int32_t producer_threads;   /* path 3: threads producing random words (0 = auto) */
     int32_t test_exact_swaps;   /* test hook: 1 = skip the FP32 pre-decision of swaps and always
                                    evaluate the FP64 rule (results are identical either way) */

@@ -258,3 +258,93 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc,
 }
 
 }  // namespace ptq
+
+namespace ptq {
+
+// Bit-packed chains (shared memory only): row i is P/8 bytes, bit k of byte g is copy 8g+k,
+// set = spin -1. lut[p*256 + b] spreads the four parity-p bits (p, p+2, p+4, p+6) of byte b
+// into four +1/-1 bytes, so each neighbour contributes one byte load and one table load and
+// the field / Trotter logic of packed_unit is reused unchanged.
+template <int DC, bool PRE>
+__device__ __forceinline__ void packed_unit_bits(uint8_t* bp, const uint32_t* s_sdesc, uint32_t item,
+                                                 const uint4* rb, int q, int g, int G, const uint32_t* lut,
+                                                 uint32_t t, uint32_t slot, const PhiloxKey& key,
+                                                 const uint32_t* thr_c, int& sumL, int& sumC, int& nflip) {
+    const uint32_t par = item & 1u;
+    const uint32_t* desc = s_sdesc + (item >> 1) * SiteDesc<DC>::DW;
+    const uint4 d0 = *reinterpret_cast<const uint4*>(desc);
+    const uint32_t row = d0.x;
+    uint32_t nrow[DC];
+    uint32_t jpack[DC / 4];
+    {
+        const uint4 d1 = *reinterpret_cast<const uint4*>(desc + 4);
+        nrow[0] = d1.x;
+        nrow[1] = d1.y;
+        nrow[2] = d1.z;
+        nrow[3] = d1.w;
+        jpack[0] = d0.z;
+        if (DC == 8) {
+            const uint4 d2 = *reinterpret_cast<const uint4*>(desc + 8);
+            nrow[DC > 4 ? 4 : 0] = d2.x;
+            nrow[DC > 5 ? 5 : 0] = d2.y;
+            nrow[DC > 6 ? 6 : 0] = d2.z;
+            nrow[DC > 7 ? 7 : 0] = d2.w;
+            jpack[DC > 4 ? 1 : 0] = d0.w;
+        }
+    }
+    const uint32_t ug = (uint32_t)g, last = (uint32_t)G - 1u;
+    const uint32_t own = bp[row + ug];
+    // the one Trotter neighbour outside the byte: copy 8g-1 (bit 7 of byte g-1) for even
+    // copies, copy 8g+8 (bit 0 of byte g+1) for odd ones, periodic in the row
+    const uint32_t eb = par ? (bp[row + (ug == last ? 0u : ug + 1u)] & 1u)
+                            : ((uint32_t)bp[row + (ug == 0 ? last : ug - 1u)] >> 7);
+    const uint32_t* lut_p = lut + (par << 8);
+    uint32_t nbyte[DC];
+#pragma unroll
+    for (int d = 0; d < DC; ++d) nbyte[d] = bp[nrow[d] + ug];
+    uint4 r4;
+    if (PRE) {
+        r4 = rb[q * G + g];
+    } else {
+        r4 = philox(make_uint4(t, d0.y, slot, (par << 24) | (uint32_t)g), key);
+    }
+    const uint32_t u[4] = {r4.x, r4.y, r4.z, r4.w};
+    const uint32_t S = lut_p[own];
+    const uint32_t Rn = par ? lut[256 + (((own >> 1) | (eb << 7)) & 0xFFu)] : lut[256 + own];
+    const uint32_t Ln = par ? lut[own] : lut[((own << 1) | eb) & 0xFFu];
+    const uint32_t X = (S ^ Ln) & 0x02020202u;
+    const uint32_t Y = (S ^ Rn) & 0x02020202u;
+    const uint32_t Z = 0x02020202u - ((X + Y) >> 1);
+
+    int f[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int b = 0; b < DC / 4; ++b) {
+        const uint32_t a0 = lut_p[nbyte[4 * b + 0]];
+        const uint32_t a1 = lut_p[nbyte[4 * b + 1]];
+        const uint32_t a2 = lut_p[nbyte[4 * b + 2]];
+        const uint32_t a3 = lut_p[nbyte[4 * b + 3]];
+        const uint32_t t0 = __byte_perm(a0, a1, 0x5140u), t1 = __byte_perm(a0, a1, 0x7362u);
+        const uint32_t t2 = __byte_perm(a2, a3, 0x5140u), t3 = __byte_perm(a2, a3, 0x7362u);
+        f[0] = __dp4a((int)__byte_perm(t0, t2, 0x5410u), (int)jpack[b], f[0]);
+        f[1] = __dp4a((int)__byte_perm(t0, t2, 0x7632u), (int)jpack[b], f[1]);
+        f[2] = __dp4a((int)__byte_perm(t1, t3, 0x5410u), (int)jpack[b], f[2]);
+        f[3] = __dp4a((int)__byte_perm(t1, t3, 0x7632u), (int)jpack[b], f[3]);
+    }
+    uint32_t F = 0, flipbits = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int sw = (int)prmt(S, 0u, 0x8880u | (0x1110u * (uint32_t)w) | (uint32_t)w);
+        const int Lw = sw * f[w];
+        const int col = (int)__byte_perm(Z, 0u, 0x4440u | (uint32_t)w);
+        const uint32_t th = thr_c[3 * Lw + col];
+        const bool acc = (u[w] < th) | (th == 0xFFFFFFFFu);
+        F |= acc ? (0xFEu << (8 * w)) : 0u;
+        flipbits |= acc ? (1u << (2 * w)) : 0u;
+        sumL += acc ? Lw : 0;
+    }
+    nflip += __popc(F & 0x02020202u);
+    sumC = __dp4a((int)(Z & (F >> 1)), 0x01010101, sumC);
+    if (flipbits) bp[row + ug] = (uint8_t)(own ^ (flipbits << par));
+}
+
+}  // namespace ptq

@@ -139,6 +139,7 @@ void ptq::level_schedule(int N, const std::vector<std::vector<int>>& adj, std::v
 
 // ---------------------------------------------------------------------------------
 // Packed-path site descriptors (see SiteDesc in pt_kernels.cu).
+// P = bytes per chain row: the copy count for int8 chains, copies / 8 for bit-packed ones.
 void ptq::build_site_desc(int N, int P, int dclass, const std::vector<std::vector<int>>& adj,
                             const std::vector<std::vector<int>>& adjJ, const int32_t* h, std::vector<uint32_t>& desc) {
     const int DW = dclass == 4 ? 8 : 12;
@@ -319,11 +320,11 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     const int packed_dc = (dmax + 1 <= 4) ? 4 : ((dmax + 1 <= 8) ? 8 : 0);
     const bool packed_ok = (P % 8 == 0) && packed_dc > 0;
     const int want_path = opt ? opt->kernel_path : 0;
-    if (want_path < 0 || want_path > 3) {
+    if (want_path < 0 || want_path > 4) {
         free_ctx(c);
-        return create_fail(PT_EINVAL, "kernel_path must be 0..3");
+        return create_fail(PT_EINVAL, "kernel_path must be 0..4");
     }
-    if ((want_path == kPathPacked || want_path == kPathPackedInline) && !packed_ok) {
+    if ((want_path == kPathPacked || want_path == kPathPackedInline || want_path == kPathBits) && !packed_ok) {
         free_ctx(c);
         return create_fail(PT_EINVAL, "the packed kernel needs P %% 8 == 0 and degree <= 7");
     }
@@ -333,14 +334,25 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     p.tables_in_smem = (size_t)R * p.nL3 * 4 <= 49152 ? 1 : 0;
     int path = want_path;
     const int want_threads = opt ? opt->threads_per_block : 0;
+    // a layout fits if it does with the threshold rows and / or the statistics moved out
+    auto fits = [&](int pth) {
+        DevProblem q = p;
+        if (sweep_smem_bytes(q, pth, packed_dc) <= (size_t)max_smem) return true;
+        q.tables_in_smem = 0;
+        if (sweep_smem_bytes(q, pth, packed_dc) <= (size_t)max_smem) return true;
+        q.acc_in_smem = 0;
+        return sweep_smem_bytes(q, pth, packed_dc) <= (size_t)max_smem;
+    };
     if (path == 0) {
         path = kPathGeneric;
         if (packed_ok) {
-            // producer warps need a block of at least two warps
-            if ((want_threads == 0 || want_threads >= 64) &&
-                sweep_smem_bytes(p, kPathPacked, packed_dc) <= (size_t)max_smem)
+            // producer warps need a block of at least two warps; int8 chains before bit-packed ones
+            if ((want_threads == 0 || want_threads >= 64) && fits(kPathPacked))
                 path = kPathPacked;
-            else if (sweep_smem_bytes(p, kPathPackedInline, packed_dc) <= (size_t)max_smem) path = kPathPackedInline;
+            else if (fits(kPathPackedInline))
+                path = kPathPackedInline;
+            else if (fits(kPathBits))
+                path = kPathBits;
         }
     }
     c->plan.path = path;
@@ -387,7 +399,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     // against a constant row of +1 copies, the remaining slots have J = 0.
     std::vector<uint32_t> desc;
     if (path != kPathGeneric)
-        build_site_desc(N, P, c->plan.dclass, adj, adjJ, inst->h, desc);
+        build_site_desc(N, path == kPathBits ? P / 8 : P, c->plan.dclass, adj, adjJ, inst->h, desc);
 
     // overflow guard: |E| <= P * (sum|J| + sum|h|), |M| <= N*P; sum of squares stays in int64
     {

@@ -63,7 +63,7 @@ struct DevProblem {
 
 // Sweep kernel variants: byte-wise (any shape), packed with Philox inline, packed with the
 // random words produced one sweep ahead by dedicated warps.
-enum { kPathGeneric = 1, kPathPackedInline = 2, kPathPacked = 3 };
+enum { kPathGeneric = 1, kPathPackedInline = 2, kPathPacked = 3, kPathBits = 4 };
 
 struct LaunchPlan {
     int path;            // kPath*
@@ -137,7 +137,7 @@ void build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vector<uin
                   std::vector<double>& coef);
 void level_schedule(int N, const std::vector<std::vector<int>>& adj, std::vector<uint32_t>& items,
                     std::vector<int32_t>& level_off);
-void build_site_desc(int N, int P, int dclass, const std::vector<std::vector<int>>& adj,
+void build_site_desc(int N, int row_bytes, int dclass, const std::vector<std::vector<int>>& adj,
                      const std::vector<std::vector<int>>& adjJ, const int32_t* h, std::vector<uint32_t>& desc);
 
 // Host-side preparation of one batched request (pt_batch.cu).

@@ -56,13 +56,17 @@ struct GenericLayout {
 // slot points at it), per-site descriptors, the schedule, level offsets, the threshold
 // row(s), statistics, reduction scratch, control words and, when
 // the random words are produced ahead, two buffers of one sweep's words each.
+// With bits, the chain is P/8 bytes per site, the constant row holds +1 copies as zero bits,
+// and two 256-entry tables spread parity bits into +1/-1 bytes.
 struct FastLayout {
-    size_t spins, ones, desc, items, loff, thr, acc, red, ctl, rbuf, total;
-    __host__ __device__ FastLayout(const DevProblem& p, int dc, bool pre) {
+    size_t spins, ones, lut, desc, items, loff, thr, acc, red, ctl, rbuf, total;
+    __host__ __device__ FastLayout(const DevProblem& p, int dc, bool pre, bool bits = false) {
         const int N = p.N, P = p.P;
+        const size_t row = bits ? (size_t)P / 8 : (size_t)P;
         size_t o = 0;
-        spins = o; o += up16((size_t)N * P);
-        ones = o;  o += up16((size_t)P);
+        spins = o; o += up16((size_t)N * row);
+        ones = o;  o += up16(row);
+        lut = o;   o += bits ? 2048 : 0;
         desc = o;  o += (size_t)N * (dc == 4 ? 32 : 48);
         items = o; o += up16((size_t)2 * N * 4);
         loff = o;  o += up16((size_t)(p.n_levels + 1) * 4);
@@ -78,7 +82,7 @@ struct FastLayout {
 
 size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass) {
     if (path == kPathGeneric) return GenericLayout(p).total;
-    return FastLayout(p, dclass, path == kPathPacked).total;
+    return FastLayout(p, dclass, path == kPathPacked, path == kPathBits).total;
 }
 
 
@@ -347,14 +351,16 @@ __device__ __forceinline__ void produce_words(uint4* buf, uint32_t t, const uint
 // random words of sweep s+1 into one shared buffer while the consumer warps run the levels
 // of sweep s out of the other; consumers synchronise levels on named barrier 1 and both
 // groups meet once per sweep.
-template <int DC, bool PRE>
+template <int DC, bool PRE, bool BITS = false>
 __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot, long long t0, long long q0,
                                                   int n_sweeps, int sweeps_per_swap, long long timeout_ns,
                                                   int n_consumer, unsigned char* smem) {
     const int N = p.N, P = p.P;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const FastLayout L(p, DC, PRE);
+    const FastLayout L(p, DC, PRE, BITS);
     int8_t* sp = reinterpret_cast<int8_t*>(smem + L.spins);
+    uint8_t* bp = reinterpret_cast<uint8_t*>(smem + L.spins);
+    uint32_t* s_lut = reinterpret_cast<uint32_t*>(smem + L.lut);
     uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem + L.desc);
     uint32_t* s_items = reinterpret_cast<uint32_t*>(smem + L.items);
     int32_t* s_loff = reinterpret_cast<int32_t*>(smem + L.loff);
@@ -367,13 +373,37 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     const bool consumer = tid < NC;
     const int DW = SiteDesc<DC>::DW;
 
-    {
+    if (BITS) {
+        // int8 chain in global memory -> one bit per copy in shared memory
+        const uint2* src = reinterpret_cast<const uint2*>(p.spins + (size_t)slot * p.slot_stride);
+        for (int x = tid; x < N * (P / 8); x += nt) {
+            const uint2 v = src[x];
+            uint32_t b = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                b |= ((v.x >> (8 * k + 7)) & 1u) << k;
+                b |= ((v.y >> (8 * k + 7)) & 1u) << (k + 4);
+            }
+            bp[x] = (uint8_t)b;
+        }
+        uint8_t* zeros = reinterpret_cast<uint8_t*>(smem + L.ones);
+        for (int x = tid; x < P / 8; x += nt) zeros[x] = 0;
+        for (int x = tid; x < 512; x += nt) {
+            const uint32_t par = (uint32_t)x >> 8, byte = (uint32_t)x & 0xFFu;
+            uint32_t v = 0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) v |= (((byte >> (par + 2 * w)) & 1u) ? 0xFFu : 0x01u) << (8 * w);
+            s_lut[x] = v;
+        }
+    } else {
         const int4* src = reinterpret_cast<const int4*>(p.spins + (size_t)slot * p.slot_stride);
         int4* dst = reinterpret_cast<int4*>(sp);
         const int n16 = (int)(up16((size_t)N * P) / 16);
         for (int x = tid; x < n16; x += nt) dst[x] = src[x];
         int8_t* ones = reinterpret_cast<int8_t*>(smem + L.ones);
         for (int x = tid; x < P; x += nt) ones[x] = 1;
+    }
+    {
         const int4* dsrc = reinterpret_cast<const int4*>(p.desc);
         int4* ddst = reinterpret_cast<int4*>(s_desc);
         for (int x = tid; x < N * DW / 4; x += nt) ddst[x] = dsrc[x];
@@ -411,8 +441,12 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
                     const int g = u & gmask;
                     if (g >= G) continue;
                     const int q = base + (u >> lg);
-                    packed_unit<DC, PRE>(sp, s_desc, s_items[q], rb, q, g, G, P, t, (uint32_t)slot, key, thr_c, sumL,
-                                         sumC, nf);
+                    if (BITS)
+                        packed_unit_bits<DC, PRE>(bp, s_desc, s_items[q], rb, q, g, G, s_lut, t, (uint32_t)slot, key,
+                                                  thr_c, sumL, sumC, nf);
+                    else
+                        packed_unit<DC, PRE>(sp, s_desc, s_items[q], rb, q, g, G, P, t, (uint32_t)slot, key, thr_c,
+                                             sumL, sumC, nf);
                 }
                 if (PRE) named_barrier(1, NC); else __syncthreads();
             }
@@ -457,7 +491,19 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     }
     flush_acc(p, s_acc, tid, nt);
 
-    {
+    if (BITS) {
+        uint2* dst = reinterpret_cast<uint2*>(p.spins + (size_t)slot * p.slot_stride);
+        for (int x = tid; x < N * (P / 8); x += nt) {
+            const uint32_t b = bp[x];
+            uint2 v = make_uint2(0u, 0u);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v.x |= (((b >> k) & 1u) ? 0xFFu : 0x01u) << (8 * k);
+                v.y |= (((b >> (k + 4)) & 1u) ? 0xFFu : 0x01u) << (8 * k);
+            }
+            dst[x] = v;
+        }
+    } else {
         int4* dst = reinterpret_cast<int4*>(p.spins + (size_t)slot * p.slot_stride);
         const int4* src = reinterpret_cast<const int4*>(sp);
         const int n16 = (int)(up16((size_t)N * P) / 16);
@@ -471,12 +517,13 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     }
 }
 
-template <int DC, bool PRE, int MAXT>
+template <int DC, bool PRE, int MAXT, bool BITS = false>
 __global__ void __launch_bounds__(MAXT, 1)
 sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
                     long long timeout_ns, int n_consumer) {
     extern __shared__ __align__(16) unsigned char smem[];
-    sweep_packed_body<DC, PRE>(p, blockIdx.x, t0, q0, n_sweeps, sweeps_per_swap, timeout_ns, n_consumer, smem);
+    sweep_packed_body<DC, PRE, BITS>(p, blockIdx.x, t0, q0, n_sweeps, sweeps_per_swap, timeout_ns, n_consumer,
+                                     smem);
 }
 
 // Several problems in one cooperative launch (all chains resident at once): block b sweeps
@@ -617,6 +664,13 @@ static const void* sweep_fn(const LaunchPlan& plan) {
             case 8: return (const void*)sweep_kernel<8>;
             default: return (const void*)sweep_kernel<32>;
         }
+    }
+    if (plan.path == kPathBits) {
+        if (plan.threads > 512)
+            return plan.dclass == 4 ? (const void*)sweep_packed_kernel<4, false, 1024, true>
+                                    : (const void*)sweep_packed_kernel<8, false, 1024, true>;
+        return plan.dclass == 4 ? (const void*)sweep_packed_kernel<4, false, 512, true>
+                                : (const void*)sweep_packed_kernel<8, false, 512, true>;
     }
     const bool pre = plan.path == kPathPacked;
     if (plan.threads > 512) {

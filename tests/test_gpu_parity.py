@@ -118,6 +118,7 @@ def test_layouts_and_swap_modes_give_identical_bits():
                dict(kernel_path=1), dict(kernel_path=1, threads_per_block=96), dict(kernel_path=2),
                dict(kernel_path=2, threads_per_block=64), dict(kernel_path=3), dict(kernel_path=3, producer_threads=32),
                dict(kernel_path=3, threads_per_block=256, producer_threads=160), dict(kernel_path=3, swap_mode=2),
+               dict(kernel_path=4), dict(kernel_path=4, threads_per_block=32), dict(kernel_path=4, swap_mode=2),
                dict(test_exact_swaps=1), dict(test_exact_swaps=1, swap_mode=2)):
         g = pt.PT.from_problem(prob, **kw)
         g.run(300, 1)
@@ -131,7 +132,7 @@ def test_layouts_and_swap_modes_give_identical_bits():
                 assert np.array_equal(np.asarray(cur[1][k]), np.asarray(ref[1][k])), (kw, k)
 
 
-@pytest.mark.parametrize("path", [1, 2, 3])
+@pytest.mark.parametrize("path", [1, 2, 3, 4])
 def test_medium_workload_each_kernel_path(path):
     prob = instances.workload("regular3_n256_p64_r64", 4)
     g, o = both(prob, kernel_path=path)
@@ -141,7 +142,7 @@ def test_medium_workload_each_kernel_path(path):
     assert_same(g, o, "path %d" % path)
 
 
-@pytest.mark.parametrize("path", [1, 2, 3])
+@pytest.mark.parametrize("path", [1, 2, 3, 4])
 @pytest.mark.parametrize("name", ["prism_p8_r3", "complete8_p16_r4"])
 def test_tiny_packed_problems_each_path(name, path):
     prob = TINY[name]
@@ -153,6 +154,40 @@ def test_tiny_packed_problems_each_path(name, path):
     g.run(300, 2)
     o.run(300, 2)
     assert_same(g, o, "after 300 more")
+
+
+def test_lattice_workload_bit_packed():
+    """K4,4 cells on a 16x16 grid (N=2048), P=128, R=96: one int8 chain (256 KiB) does not
+    fit in shared memory, so the automatic plan holds it at one bit per copy; checked every
+    50 sweeps over the first 200 and at the end of the 500-sweep run."""
+    prob = instances.workload("chimera16_n2048_p128_r96", 1)
+    g, o = both(prob)
+    assert g.info.kernel_path == 4
+    for chunk in range(4):
+        g.run(50, 1)
+        o.run(50, 1)
+        assert_same(g, o, "sweep %d" % (50 * (chunk + 1)))
+    g.run(prob.n_sweeps - 200, 1)
+    o.run(prob.n_sweeps - 200, 1)
+    assert_same(g, o, "sweep %d" % prob.n_sweeps)
+
+
+@pytest.mark.parametrize("P", [8, 24, 136])
+def test_bit_packed_row_lengths(P):
+    """Rows of 1, 3 and 17 bytes (periodic Trotter neighbour across the row's ends, ragged
+    16-byte padding of the chain), degree-6 lattice with fields and degree-3 graph."""
+    rng = np.random.default_rng(P)
+    for graph, kw in (("chimera", dict(rows=2, cols=3)), ("regular", dict(n=38, degree=3))):
+        prob = instances.make_problem(graph, rng, P=P, R=5, n_sweeps=0, seed=instances.philox_seed(500 + P),
+                                      ladder="geometric", g0=0.1, g1=3.0, T=0.2, J=(-3, -1, 2, 4), h=(-2, 0, 1), **kw)
+        g, o = both(prob, kernel_path=4)
+        for s in range(6):
+            g.run(1, 1)
+            o.run(1, 1)
+            assert_same(g, o, "%s P=%d sweep %d" % (graph, P, s + 1))
+        g.run(200, 3)
+        o.run(200, 3)
+        assert_same(g, o, "%s P=%d after 200 more" % (graph, P))
 
 
 def test_exact_swap_rule_and_fast_pre_decision_agree_on_the_medium_workload():
