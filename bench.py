@@ -265,7 +265,9 @@ def run_batched(args, pt, instances, torch, n_sm, sm_max):
     probs = instances.batch_problems(count=args.batch_count, index=1, n_sweeps=args.batch_sweeps)
     attempts = sum(p.attempts_per_sweep * p.n_sweeps for p in probs)
     stream = torch.cuda.Stream()
-    b = pt.Batch(probs, cluster_size=2, stream=stream.cuda_stream)
+    t_create = time.perf_counter()
+    b = pt.Batch(probs, cluster_size=0, stream=stream.cuda_stream)  # layout autotuned at create
+    create_s = time.perf_counter() - t_create
     info = b.info()
     b.run()
     b.sync()
@@ -276,6 +278,7 @@ def run_batched(args, pt, instances, torch, n_sm, sm_max):
     b.sync()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    b_graph = b.info().graph
     b.close()
     # plain path: every request through its own pt_create + pt_run, one after another
     ctxs = []
@@ -303,6 +306,8 @@ def run_batched(args, pt, instances, torch, n_sm, sm_max):
             "plain_value": attempts / (plain_ms / 1e3), "plain_ms": plain_ms,
             "speedup_vs_plain": plain_ms / ms, "gpu_launches": 1, "plain_gpu_launches": plain_launches,
             "cluster": info.cluster, "n_clusters": info.n_clusters, "smem_bytes": int(info.smem_bytes),
+            "group_widen": info.group_widen, "autotuned_layouts": info.tuned_layouts,
+            "create_and_autotune_s": create_s, "graph_replay": bool(b_graph),
             "roofline": {"bound": "alu", "achieved": ialg * value / 1e12, "peak": peak, "unit": "Tinstr/s",
                          "frac": ialg * value / 1e12 / peak, "kernel": "batch_kernel"}}
 

@@ -82,7 +82,9 @@ typedef struct {
     int32_t producer_threads;   /* path 3: threads producing random words (0 = auto) */
     int32_t test_exact_swaps;   /* test hook: 1 = skip the FP32 pre-decision of swaps and always
                                    evaluate the FP64 rule (results are identical either way) */
-    int32_t cluster_size;       /* batched launches: CTAs per thread-block cluster (0 = 4) */
+    int32_t cluster_size;       /* batched launches: CTAs per thread-block cluster (1..16), or
+                                   0 = autotune (pt_batch_create times a short run of each
+                                   layout and keeps the fastest; results never depend on it) */
     int32_t reserved[4];
 } pt_options;
 
@@ -209,12 +211,21 @@ typedef struct {
     int64_t device_bytes;
     int64_t kernel_launches;
     int64_t h2d_bytes;
+    int32_t tuned_layouts;      /* layouts the autotuner timed (0 = layout given) */
+    int32_t group_widen;        /* chosen threads-per-chain doubling (0 = default width) */
+    int32_t graph;              /* 1 = runs replay a captured CUDA graph */
+    int32_t reserved;
 } pt_batch_info;
 
 /* Copy and prepare every request (tables, schedules, initial spins as in pt_create). */
 int pt_batch_create(const pt_request* reqs, int32_t count, const pt_options* opt, void* cuda_stream,
                     pt_batch** out);
-/* One persistent launch running every request's n_sweeps (with its swap passes). Async. */
+/* One persistent launch running every request's n_sweeps (with its swap passes). Async.
+ * The first call captures the launch into a CUDA graph and later calls replay it. On a
+ * stream that is itself being captured the launch is recorded into the caller's graph;
+ * every replay of that graph is one more run (the sweep and pass counters live on the
+ * device and advance with it), but only runs made through pt_batch_run are checked
+ * against the counter limits (PT_EOVERFLOW). */
 int pt_batch_run(pt_batch* b);
 int pt_batch_read_state(pt_batch* b, int32_t index, int8_t* out, size_t bytes);   /* syncs */
 int pt_batch_read_observables(pt_batch* b, int32_t index, pt_observables* out);  /* syncs */

@@ -256,6 +256,13 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchParams bp) {
         else
             run_problem<8>(I, smem, cluster, rank, K);
         cluster.sync();  // peers are done reading this CTA's published (E, M)
+        if (rank == 0 && threadIdx.x == 0) {
+            // a finished problem's counters advance on the device, so the same launch can be
+            // replayed (a CUDA graph) without uploading the problem records again
+            BatchInstance* W = bp.inst + bp.order[job];
+            W->t0 = I.t0 + I.n_sweeps;
+            if (I.sweeps_per_swap > 0) W->q0 = I.q0 + I.n_sweeps / I.sweeps_per_swap;
+        }
     }
 }
 
@@ -390,6 +397,14 @@ struct pt_batch {
     int8_t* d_staging;
     std::vector<BatchInstance> h_inst;
     std::vector<long long> sweep_limit;
+    unsigned char* arena;    // constants [0, const_bytes), then every request's state
+    size_t const_bytes, arena_bytes, smem_cap;
+    int2* d_map;             // (request, chain) of every chain, for the initial-state kernel
+    int n_map;
+    int widen;               // group widening of the chosen layout (choose_groups)
+    int tuned;               // layouts timed by the autotuner (0 = layout given)
+    cudaGraphExec_t exec;    // the captured run (memset of the work counter + persistent launch)
+    int graph_failed;        // capture was not possible; runs launch directly
     int err;
     char msg[256];
 };
@@ -406,6 +421,7 @@ static int bfail(pt_batch* b, int code, const char* fmt, ...) {
 }
 
 static void free_batch(pt_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
     for (void* p : b->allocs) cudaFree(p);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -559,18 +575,134 @@ void ptq::fill_instance(BatchInstance& I, const Prepared& p, unsigned char* base
     I.swap_stats = (unsigned long long*)(base + p.off_sw);
 }
 
-void ptq::choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_cap) {
+void ptq::choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_cap, int widen) {
     // threads per chain: about one 4-copy unit per thread in an average level, at least two
-    // warps, and no more groups than a CTA has chains; chains stay resident when they fit
+    // warps, and no more groups than a CTA has chains; chains stay resident when they fit.
+    // widen doubles the group that many times (fewer chains at once, shorter levels).
     const long long units = 2ll * I.N * (I.P / 8);
     const long long avg = (units + I.n_levels - 1) / I.n_levels;
     const int C = (I.R + cluster - 1) / cluster;
     int g = 64;
     while (g < 512 && g < avg) g <<= 1;
     while (g < 512 && threads / g > C) g <<= 1;
+    for (int w = 0; w < widen && g < 512 && g < threads; ++w) g <<= 1;
     I.group_threads = g;
     I.resident = 1;
     if (batch_smem_bytes(I, cluster, threads) > smem_cap) I.resident = 0;
+}
+
+// Groups per request, the CTA's shared memory and the persistent grid for one layout.
+static int plan_layout(pt_batch* b, int cluster, int widen, char* why, size_t why_len) {
+    size_t smem = 0;
+    for (int k = 0; k < b->count; ++k) {
+        BatchInstance& I = b->h_inst[k];
+        choose_groups(I, cluster, b->threads, b->smem_cap, widen);
+        const size_t need = batch_smem_bytes(I, cluster, b->threads);
+        if (need > b->smem_cap) {
+            snprintf(why, why_len, "request %d needs %zu bytes of shared memory per CTA (device: %zu)", k, need,
+                     b->smem_cap);
+            return PT_EINVAL;
+        }
+        smem = std::max(smem, need);
+    }
+    int ncl = 0;
+    const cudaError_t e = batch_max_clusters(cluster, b->threads, smem, &ncl);
+    if (e != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        snprintf(why, why_len, "no cluster of %d CTAs with %zu bytes of shared memory fits (%s)", cluster, smem,
+                 cudaGetErrorString(e));
+        return PT_EINVAL;
+    }
+    b->cluster = cluster;
+    b->widen = widen;
+    b->smem = smem;
+    b->n_clusters = std::min(ncl, b->count);
+    return PT_OK;
+}
+
+// Every request back to its initial state: zero statistics, counters at 0, initial spins
+// and (E, M) from the Philox init stream. Synchronous.
+static cudaError_t reset_state(pt_batch* b) {
+    for (BatchInstance& I : b->h_inst) I.t0 = I.q0 = 0;
+    cudaStream_t s = b->stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b->arena + b->const_bytes, 0, b->arena_bytes - b->const_bytes, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(BatchInstance) * b->count, cudaMemcpyHostToDevice,
+                             s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->d_status, 0, 16, s)) != cudaSuccess ||
+        (e = launch_batch_init(b->d_inst, b->d_map, b->n_map, s)) != cudaSuccess)
+        return e;
+    b->launches += 1;
+    b->h2d_bytes += (int64_t)(sizeof(BatchInstance) * b->count);
+    return cudaStreamSynchronize(s);
+}
+
+// One run of every request: reset the work counter, then the persistent launch.
+static cudaError_t enqueue_run(pt_batch* b) {
+    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream);
+    if (e != cudaSuccess) return e;
+    BatchParams bp;
+    bp.inst = b->d_inst;
+    bp.order = b->d_order;
+    bp.count = b->count;
+    bp.next_job = b->d_counter;
+    bp.status = b->d_status;
+    return launch_batch(bp, b->cluster, b->n_clusters, b->threads, b->smem, b->stream);
+}
+
+// Layout autotuner: times a short run (1 % of every request's sweeps, at least one) for
+// each cluster size and group width that fits and keeps the fastest. The layout changes
+// which CTA sweeps which chain and when, never the arithmetic or the random counters, so
+// the choice cannot change any result; the state is reset afterwards.
+static int autotune(pt_batch* b) {
+    static const int kClusters[] = {1, 2, 4, 8};
+    std::vector<int> full(b->count);
+    for (int k = 0; k < b->count; ++k) {
+        full[k] = b->h_inst[k].n_sweeps;
+        b->h_inst[k].n_sweeps = std::max(1, full[k] / 100);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best_ms = 0.f;
+    int best_c = 0, best_w = 0, timed = 0;
+    char why[200];
+    for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
+            if (plan_layout(b, kClusters[ci], w, why, sizeof(why)) != PT_OK) continue;
+            for (int rep = 0; rep < (timed == 0 ? 2 : 1) && e == cudaSuccess; ++rep) {  // first: one warm-up
+                for (BatchInstance& I : b->h_inst) I.t0 = I.q0 = 0;
+                if ((e = cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(BatchInstance) * b->count,
+                                         cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+                    (e = cudaEventRecord(e0, b->stream)) != cudaSuccess || (e = enqueue_run(b)) != cudaSuccess ||
+                    (e = cudaEventRecord(e1, b->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess)
+                    break;
+                b->launches += 1;
+            }
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            if (timed == 0 || ms < best_ms) {
+                best_ms = ms;
+                best_c = kClusters[ci];
+                best_w = w;
+            }
+            ++timed;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (int k = 0; k < b->count; ++k) b->h_inst[k].n_sweeps = full[k];
+    if (e != cudaSuccess) return bfail(b, PT_ECUDA, "autotuner: %s", cudaGetErrorString(e));
+    int st = 0;
+    if ((e = cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess || st)
+        return bfail(b, PT_ECUDA, "autotuner: device status %d (%s)", st, cudaGetErrorString(e));
+    if (timed == 0) return bfail(b, PT_EINVAL, "no batched layout fits: %s", why);
+    b->tuned = timed;
+    const int rc = plan_layout(b, best_c, best_w, why, sizeof(why));
+    if (rc) return bfail(b, rc, "%s", why);
+    if ((e = reset_state(b)) != cudaSuccess) return bfail(b, PT_ECUDA, "autotuner reset: %s", cudaGetErrorString(e));
+    return PT_OK;
 }
 
 extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_options* opt, void* cuda_stream,
@@ -584,11 +716,19 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
         const int rc = prepare_request(reqs[k], pr[k], why, sizeof(why));
         if (rc) return bfail(nullptr, rc, "request %d: %s", k, why);
     }
+    if (opt && (opt->cluster_size < 0 || opt->cluster_size > 16))
+        return bfail(nullptr, PT_EINVAL, "cluster_size must be 0 (autotune) or 1..16");
     pt_batch* b = new pt_batch();
     b->count = count;
     b->stream = (cudaStream_t)cuda_stream;
     b->own_stream = false;
     b->device_bytes = b->launches = b->h2d_bytes = 0;
+    b->arena = nullptr;
+    b->d_map = nullptr;
+    b->exec = nullptr;
+    b->graph_failed = 0;
+    b->tuned = 0;
+    b->widen = 0;
     b->err = 0;
     b->msg[0] = 0;
     if (!b->stream) {
@@ -601,13 +741,8 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
     int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t smem_cap = (size_t)max_smem - 1024;  // room for the kernel's static shared memory
+    b->smem_cap = (size_t)max_smem - 1024;  // room for the kernel's static shared memory
     b->threads = 512;
-    b->cluster = (opt && opt->cluster_size > 0) ? opt->cluster_size : 4;
-    if (b->cluster > 16) {
-        free_batch(b);
-        return bfail(nullptr, PT_EINVAL, "cluster_size must be <= 16");
-    }
 
     // device layout of every request in one arena: constants first, then state
     b->h_inst.resize(count);
@@ -618,7 +753,7 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
         off += (bytes + 255) & ~(size_t)255;
         return o;
     };
-    size_t max_state = 0, smem = 0;
+    size_t max_state = 0;
     for (int k = 0; k < count; ++k) {
         Prepared& p = pr[k];
         p.off_sdesc = take(p.sdesc.size() * 4);
@@ -653,16 +788,19 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
         I.n_sweeps = (int)reqs[k].n_sweeps;
         I.sweeps_per_swap = reqs[k].sweeps_per_swap;
         b->sweep_limit[k] = p.sweep_limit;
-        choose_groups(I, b->cluster, b->threads, smem_cap);
-        const size_t need = batch_smem_bytes(I, b->cluster, b->threads);
-        if (need > smem_cap) {
-            free_batch(b);
-            return bfail(nullptr, PT_EINVAL, "request %d needs %zu bytes of shared memory per CTA (device: %zu)", k,
-                         need, smem_cap);
-        }
-        smem = std::max(smem, need);
     }
-    b->smem = smem;
+    b->const_bytes = const_bytes;
+    b->arena_bytes = off;
+    const int fixed_cluster = (opt && opt->cluster_size > 0) ? opt->cluster_size : 0;
+    {
+        // the given layout, or (autotuning) the smallest cluster, which needs the most
+        // shared memory per CTA: a request that fits nowhere is rejected before allocating
+        const int rc = plan_layout(b, fixed_cluster ? fixed_cluster : 1, 0, why, sizeof(why));
+        if (rc != PT_OK && (fixed_cluster || plan_layout(b, 8, 0, why, sizeof(why)) != PT_OK)) {
+            free_batch(b);
+            return bfail(nullptr, PT_EINVAL, "%s", why);
+        }
+    }
 
     unsigned char* arena = nullptr;
     cudaError_t e;
@@ -673,6 +811,7 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
         return bfail(nullptr, e == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA, "cudaMalloc: %s",
                      cudaGetErrorString(e));
     }
+    b->arena = arena;
     std::vector<unsigned char> host_const(const_bytes, 0);
     std::vector<int2> map;
     for (int k = 0; k < count; ++k) {
@@ -705,34 +844,28 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
         const double wc = (double)pr[c].N * pr[c].P * pr[c].R * (double)reqs[c].n_sweeps;
         return wa > wc;
     });
-    int2* d_map = nullptr;
     cudaStream_t s = b->stream;
-    if ((e = balloc(b, &d_map, map.size() * sizeof(int2))) != cudaSuccess ||
+    b->n_map = (int)map.size();
+    if ((e = balloc(b, &b->d_map, map.size() * sizeof(int2))) != cudaSuccess ||
         (e = cudaMemcpyAsync(arena, host_const.data(), const_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(arena + const_bytes, 0, off - const_bytes, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(BatchInstance) * count, cudaMemcpyHostToDevice,
-                             s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(b->d_order, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s)) !=
             cudaSuccess ||
-        (e = cudaMemcpyAsync(d_map, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) !=
+        (e = cudaMemcpyAsync(b->d_map, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) !=
             cudaSuccess ||
-        (e = cudaMemsetAsync(b->d_status, 0, 16, s)) != cudaSuccess ||
-        (e = launch_batch_init(b->d_inst, d_map, (int)map.size(), s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        (e = reset_state(b)) != cudaSuccess) {
         cudaStreamSynchronize(s);
         free_batch(b);
         return bfail(nullptr, PT_ECUDA, "batch setup: %s", cudaGetErrorString(e));
     }
-    b->launches += 1;
-    b->h2d_bytes += (int64_t)(const_bytes + sizeof(BatchInstance) * count + sizeof(int32_t) * count +
-                              map.size() * sizeof(int2));
-    int ncl = 0;
-    if ((e = batch_max_clusters(b->cluster, b->threads, b->smem, &ncl)) != cudaSuccess || ncl < 1) {
-        free_batch(b);
-        return bfail(nullptr, PT_EINVAL, "no cluster of %d CTAs with %zu bytes of shared memory fits (%s)", b->cluster,
-                     b->smem, cudaGetErrorString(e));
+    b->h2d_bytes += (int64_t)(const_bytes + sizeof(int32_t) * count + map.size() * sizeof(int2));
+    if (!fixed_cluster) {
+        const int rc = autotune(b);
+        if (rc != PT_OK) {
+            snprintf(g_batch_create_msg, sizeof(g_batch_create_msg), "%s", b->msg);
+            free_batch(b);
+            return rc;
+        }
     }
-    b->n_clusters = std::min(ncl, count);
     *out = b;
     return PT_OK;
 }
@@ -760,28 +893,42 @@ extern "C" int pt_batch_run(pt_batch* b) {
         if (I.t0 + I.n_sweeps > b->sweep_limit[k] || I.q0 + passes > 0xFFFFFFFFll)
             return bfail(b, PT_EOVERFLOW, "request %d: sweep or pass counter would overflow", k);
     }
-    cudaError_t e;
-    if ((e = cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(BatchInstance) * b->count, cudaMemcpyHostToDevice,
-                             b->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream)) != cudaSuccess)
-        return bfail(b, PT_ECUDA, "%s", cudaGetErrorString(e));
-    BatchParams bp;
-    bp.inst = b->d_inst;
-    bp.order = b->d_order;
-    bp.count = b->count;
-    bp.next_job = b->d_counter;
-    bp.status = b->d_status;
-    if ((e = launch_batch(bp, b->cluster, b->n_clusters, b->threads, b->smem, b->stream)) != cudaSuccess)
-        return bfail(b, PT_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+    cudaError_t e = cudaSuccess;
+    if (!b->exec && !b->graph_failed) {
+        // the first run is captured into a CUDA graph and every run replays it (the problem
+        // records on the device carry the counters forward). A stream that is already
+        // capturing gets the plain launch, recorded into the caller's own graph.
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(b->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+        } else if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            cudaGraph_t graph = nullptr;
+            const cudaError_t le = enqueue_run(b);
+            const cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+            if (le == cudaSuccess && ce == cudaSuccess && graph &&
+                cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess)
+                b->exec = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+            if (!b->exec) {
+                b->graph_failed = 1;
+                cudaGetLastError();
+            }
+        } else {
+            b->graph_failed = 1;
+            cudaGetLastError();
+        }
+    }
+    if (b->exec)
+        e = cudaGraphLaunch(b->exec, b->stream);
+    else
+        e = enqueue_run(b);
+    if (e != cudaSuccess) return bfail(b, PT_ECUDA, "batch launch: %s", cudaGetErrorString(e));
     b->launches += 1;
-    b->h2d_bytes += (int64_t)(sizeof(BatchInstance) * b->count);
     for (int k = 0; k < b->count; ++k) {
         BatchInstance& I = b->h_inst[k];
         I.t0 += I.n_sweeps;
         if (I.sweeps_per_swap > 0) I.q0 += I.n_sweeps / I.sweeps_per_swap;
     }
-    // the host copy changes only after the asynchronous upload above has been consumed
-    // by cudaMemcpyAsync (pageable source: copied before the call returns)
     return PT_OK;
 }
 
@@ -823,9 +970,12 @@ extern "C" int pt_batch_read_observables(pt_batch* b, int32_t index, pt_observab
     std::vector<long long> E(R), M(R);
     std::vector<int32_t> slot_of(R);
     std::vector<unsigned long long> acc((size_t)R * kAccCount), sw(2 * (size_t)R);
+    BatchInstance dev_rec;  // the device record: its counters also count replays of a caller's graph
     cudaStream_t s = b->stream;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(E.data(), I.E, R * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+    if ((e = cudaMemcpyAsync(&dev_rec, b->d_inst + index, sizeof(BatchInstance), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(E.data(), I.E, R * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(M.data(), I.M, R * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(slot_of.data(), I.slot_of_rung, R * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(acc.data(), I.acc, acc.size() * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -833,8 +983,8 @@ extern "C" int pt_batch_read_observables(pt_batch* b, int32_t index, pt_observab
         return bfail(b, PT_ECUDA, "%s", cudaGetErrorString(e));
     int rc = bcheck(b);
     if (rc) return rc;
-    o->t = I.t0;
-    o->q = I.q0;
+    o->t = dev_rec.t0;
+    o->q = dev_rec.q0;
     for (int r = 0; r < R; ++r) {
         const int slot = slot_of[r];
         if (o->E) o->E[r] = E[slot];
@@ -865,6 +1015,10 @@ extern "C" int pt_batch_get_info(const pt_batch* b, pt_batch_info* o) {
     o->device_bytes = b->device_bytes;
     o->kernel_launches = b->launches;
     o->h2d_bytes = b->h2d_bytes;
+    o->tuned_layouts = b->tuned;
+    o->group_widen = b->widen;
+    o->graph = b->exec ? 1 : 0;
+    o->reserved = 0;
     return PT_OK;
 }
 

@@ -101,7 +101,7 @@ struct BatchInstance {
 };
 
 struct BatchParams {
-    const BatchInstance* inst;  // [count]
+    BatchInstance* inst;        // [count]; t0 / q0 of a finished problem advance in place
     const int32_t* order;       // [count] request indices, most work first
     int count;
     int* next_job;              // work counter, zero at launch
@@ -153,7 +153,7 @@ struct Prepared {
 int prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len);
 size_t request_block_layout(Prepared& p, size_t mailbox_entries = 0);
 void fill_instance(BatchInstance& I, const Prepared& p, unsigned char* base, const pt_request& r);
-void choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_cap);
+void choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_cap, int widen = 0);
 
 // Batched launchers (pt_batch.cu).
 size_t batch_smem_bytes(const BatchInstance& I, int cluster, int threads);

@@ -59,7 +59,8 @@ class pt_request(ctypes.Structure):
 
 class pt_batch_info(ctypes.Structure):
     _fields_ = [("count", _i32), ("cluster", _i32), ("n_clusters", _i32), ("threads_per_block", _i32),
-                ("smem_bytes", _i64), ("device_bytes", _i64), ("kernel_launches", _i64), ("h2d_bytes", _i64)]
+                ("smem_bytes", _i64), ("device_bytes", _i64), ("kernel_launches", _i64), ("h2d_bytes", _i64),
+                ("tuned_layouts", _i32), ("group_widen", _i32), ("graph", _i32), ("reserved", _i32)]
 
 
 class pt_server_options(ctypes.Structure):

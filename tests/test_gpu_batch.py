@@ -64,6 +64,47 @@ def test_cluster_size_does_not_change_bits(cluster):
         _same(alt.read_state(k), alt.obs(k), ref.read_state(k), ref.obs(k), "cluster %d request %d" % (cluster, k))
 
 
+def test_autotuned_layout_and_graph_replays_keep_the_bits():
+    """cluster_size 0: pt_batch_create times each layout on a short run, resets the state and
+    keeps the fastest; later runs replay one captured CUDA graph. Three runs, every request
+    against the oracle and against a fixed layout."""
+    probs = _mixed_problems(30)
+    tuned = pt.Batch(probs)
+    info = tuned.info()
+    assert info.tuned_layouts >= 2 and info.cluster in (1, 2, 4, 8)
+    fixed = pt.Batch(probs, cluster_size=2)
+    assert fixed.info().tuned_layouts == 0
+    orcs = [Oracle.from_problem(p, threads=THREADS) for p in probs]
+    for run in range(3):
+        tuned.run()
+        fixed.run()
+        for k, (p, o) in enumerate(zip(probs, orcs)):
+            o.run(p.n_sweeps, p.sweeps_per_swap)
+            _same(tuned.read_state(k), tuned.obs(k), o.read_state(), o.obs(), "tuned run %d request %d" % (run, k))
+            _same(fixed.read_state(k), fixed.obs(k), o.read_state(), o.obs(), "fixed run %d request %d" % (run, k))
+    assert tuned.info().graph == 1 and fixed.info().graph == 1
+
+
+def test_run_recorded_into_a_callers_graph():
+    """pt_batch_run on a stream under capture records the launch into the caller's graph;
+    each replay is one more run, counters included."""
+    torch = pytest.importorskip("torch")
+    probs = _mixed_problems(20)
+    stream = torch.cuda.Stream()
+    b = pt.Batch(probs, cluster_size=2, stream=stream.cuda_stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        b.run()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    for k, p in enumerate(probs):
+        o = Oracle.from_problem(p, threads=THREADS)
+        o.run(p.n_sweeps, p.sweeps_per_swap)
+        o.run(p.n_sweeps, p.sweeps_per_swap)
+        _same(b.read_state(k), b.obs(k), o.read_state(), o.obs(), "request %d" % k)
+
+
 def test_batch_requests_equal_single_problem_runs():
     """A slice of the 512-request workload (uneven N, P, R): batched == one pt_run per request."""
     probs = instances.batch_problems(count=24, index=3, n_sweeps=30)
