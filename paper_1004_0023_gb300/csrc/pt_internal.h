@@ -38,7 +38,7 @@ struct DevProblem {
     const int8_t* h;           // [N]
     const uint32_t* items;     // [2N] (i << 1) | parity, grouped by dependency level
     const int32_t* level_off;  // [n_levels + 1]
-    const uint32_t* desc;      // [2N][8 or 16] packed-path unit descriptors (schedule order)
+    const uint32_t* desc;      // [N][8 or 12] packed-path site descriptors
     const uint32_t* thr;       // [R][nL*3] Metropolis thresholds
     const double* coef;        // [2(R-1)] a_r then c_r
     // state

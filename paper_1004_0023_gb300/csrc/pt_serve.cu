@@ -201,7 +201,6 @@ extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream,
     s->smem_cap = (size_t)max_smem - 1024;
     s->map_capacity = 1 << 16;
     s->wmap_capacity = s->n_sm * 8;
-    void* p = nullptr;
     cudaError_t e;
     auto grab = [&](size_t bytes) -> void* {
         void* q = nullptr;
@@ -222,7 +221,6 @@ extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream,
         free_server(s);
         return sfail(nullptr, PT_ENOMEM, "could not allocate the serving arena (%zu bytes)", arena_bytes);
     }
-    (void)p;
     s->alloc = new ArenaAllocator(arena_bytes);
     if ((e = cudaMemsetAsync(s->d_status, 0, 16, s->stream)) != cudaSuccess) {
         free_server(s);

@@ -119,6 +119,7 @@ def test_layouts_and_swap_modes_give_identical_bits():
                dict(kernel_path=2, threads_per_block=64), dict(kernel_path=3), dict(kernel_path=3, producer_threads=32),
                dict(kernel_path=3, threads_per_block=256, producer_threads=160), dict(kernel_path=3, swap_mode=2),
                dict(kernel_path=4), dict(kernel_path=4, threads_per_block=32), dict(kernel_path=4, swap_mode=2),
+               dict(kernel_path=3, threads_per_block=64, producer_threads=32),
                dict(test_exact_swaps=1), dict(test_exact_swaps=1, swap_mode=2)):
         g = pt.PT.from_problem(prob, **kw)
         g.run(300, 1)
@@ -172,15 +173,17 @@ def test_lattice_workload_bit_packed():
     assert_same(g, o, "sweep %d" % prob.n_sweeps)
 
 
+@pytest.mark.parametrize("path", [2, 3, 4])
 @pytest.mark.parametrize("P", [8, 24, 136])
-def test_bit_packed_row_lengths(P):
-    """Rows of 1, 3 and 17 bytes (periodic Trotter neighbour across the row's ends, ragged
-    16-byte padding of the chain), degree-6 lattice with fields and degree-3 graph."""
+def test_packed_row_lengths(P, path):
+    """Rows of 8, 24 and 136 copies (1, 3 and 17 bytes bit-packed): the periodic Trotter
+    neighbour across the row's ends, ragged 16-byte padding of the chain, and row sizes that
+    are not powers of two; degree-6 lattice with fields and degree-3 graph."""
     rng = np.random.default_rng(P)
     for graph, kw in (("chimera", dict(rows=2, cols=3)), ("regular", dict(n=38, degree=3))):
         prob = instances.make_problem(graph, rng, P=P, R=5, n_sweeps=0, seed=instances.philox_seed(500 + P),
                                       ladder="geometric", g0=0.1, g1=3.0, T=0.2, J=(-3, -1, 2, 4), h=(-2, 0, 1), **kw)
-        g, o = both(prob, kernel_path=4)
+        g, o = both(prob, kernel_path=path)
         for s in range(6):
             g.run(1, 1)
             o.run(1, 1)
