@@ -41,6 +41,15 @@ def alg_instr_per_attempt(degree: int) -> int:
     return 10 + degree + 1 + 2 + 2 + 2 + 1 + 3
 
 
+KERNEL_NAMES = {1: "sweep_kernel (byte-wise)", 2: "sweep_packed_kernel (int8, inline Philox)",
+                3: "sweep_packed_kernel (int8, producer warps)", 4: "sweep_packed_kernel (bit-packed)"}
+
+# DRAM bytes (read + write) per launch of the sweep kernel, from one ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum: (workload, kernel path, sweeps per launch)
+# -> bytes. Must be retaken (or removed) whenever that kernel changes.
+MEASURED_TRAFFIC = {("regular3_n256_p64_r64", 3, 1000): 2151552}
+
+
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -55,8 +64,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-sweeps", type=int, default=1000)
+    ap.add_argument("--batch-cluster", type=int, default=0, help="CTAs per cluster (0 = autotuned at create)")
     ap.add_argument("--serving-seconds", type=float, default=10.0)
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--reference-budget-s", type=float, default=0.0,
+                    help="--impl reference: seconds of oracle work per step (0 = fit the run in ~2.5 min)")
     return ap.parse_args(argv)
 
 
@@ -243,10 +255,14 @@ def run_ours(args, rank, world, local_rank):
                    "threads_per_block": info.threads_per_block, "levels_per_sweep": info.n_levels,
                    "cooperative_swaps": bool(info.cooperative)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": MEASURED_TRAFFIC.get((args.workload, int(info.kernel_path),
+                                                      int(round(prob.n_sweeps / max(launches_per_step, 1))))),
+                     "traffic_unit": "DRAM bytes per launch (ncu)",
                      "basis": "%d algorithmic integer lane-instructions per attempt; peak = %d SMs x 128 lanes x %.0f MHz"
                               % (ialg, n_sm, sm_max),
-                     "kernel": "sweep_kernel", "launch_ms": per_launch_s * 1e3},
+                     "kernel": KERNEL_NAMES.get(int(info.kernel_path), "sweep kernel"),
+                     "launch_ms": per_launch_s * 1e3},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -266,7 +282,7 @@ def run_batched(args, pt, instances, torch, n_sm, sm_max):
     attempts = sum(p.attempts_per_sweep * p.n_sweeps for p in probs)
     stream = torch.cuda.Stream()
     t_create = time.perf_counter()
-    b = pt.Batch(probs, cluster_size=0, stream=stream.cuda_stream)  # layout autotuned at create
+    b = pt.Batch(probs, cluster_size=args.batch_cluster, stream=stream.cuda_stream)  # 0: autotuned at create
     create_s = time.perf_counter() - t_create
     info = b.info()
     b.run()
@@ -401,7 +417,7 @@ def run_reference(args, rank, world):
         return None
     prob = instances.workload(args.workload, 1)
     threads = os.cpu_count() or 1
-    per_step_budget = max(1.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+    per_step_budget = args.reference_budget_s or max(1.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
     for _ in range(args.warmup):
         cpu_baseline(prob, budget_s=per_step_budget / 4, threads=threads)
     vals, t_total = [], 0.0
