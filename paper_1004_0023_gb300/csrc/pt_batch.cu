@@ -104,18 +104,17 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
             for (int x = tid; x < P; x += nt) ones[x] = 1;
         }
         if (I.resident) {
-            const int n16 = I.slot_stride / 16;
-            for (int lc = 0; lc < c_count; ++lc) {
-                const int4* cs = reinterpret_cast<const int4*>(I.spins + (size_t)(c_begin + lc) * I.slot_stride);
-                int4* cd = reinterpret_cast<int4*>(s_chains + (size_t)lc * L.chain_stride);
-                for (int x = tid; x < n16; x += nt) cd[x] = cs[x];
-            }
+            for (int lc = 0; lc < c_count; ++lc)
+                load_split(reinterpret_cast<int8_t*>(s_chains + (size_t)lc * L.chain_stride),
+                           I.spins + (size_t)(c_begin + lc) * I.slot_stride, N, P, P >> 3, chunk_ginv(P >> 3), tid,
+                           nt);
         }
     }
     __syncthreads();
 
     const PhiloxKey key = philox_schedule(I.key0, I.key1);
     const int G = P >> 3;
+    const uint32_t ginv = chunk_ginv(G);
     int lg = 0;
     while ((1 << lg) < G) ++lg;
     const int gmask = (1 << lg) - 1;
@@ -129,11 +128,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
         for (int lc = grp; lc < c_count; lc += ngroups) {
             const int rho = c_begin + lc;
             int8_t* buf = reinterpret_cast<int8_t*>(s_chains + (size_t)(I.resident ? lc : grp) * L.chain_stride);
-            if (!I.resident) {
-                const int4* cs = reinterpret_cast<const int4*>(I.spins + (size_t)rho * I.slot_stride);
-                int4* cd = reinterpret_cast<int4*>(buf);
-                for (int x = gtid; x < I.slot_stride / 16; x += gsize) cd[x] = cs[x];
-            }
+            if (!I.resident) load_split(buf, I.spins + (size_t)rho * I.slot_stride, N, P, G, ginv, gtid, gsize);
             const int rung = s_rung[rho];
             for (int x = gtid; x < I.nL3; x += gsize) thr_g[x] = I.thr[(size_t)rung * I.nL3 + x];
             named_barrier(bar, gsize);
@@ -163,11 +158,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
                 red_g[gwarp * 3 + 1] = dM;
                 red_g[gwarp * 3 + 2] = nf;
             }
-            if (!I.resident) {
-                int4* cd = reinterpret_cast<int4*>(I.spins + (size_t)rho * I.slot_stride);
-                const int4* cs = reinterpret_cast<const int4*>(buf);
-                for (int x = gtid; x < I.slot_stride / 16; x += gsize) cd[x] = cs[x];
-            }
+            if (!I.resident) store_split(I.spins + (size_t)rho * I.slot_stride, buf, N, P, G, ginv, gtid, gsize);
             named_barrier(bar, gsize);
             if (gtid == 0) {
                 long long sE = 0, sM = 0, sF = 0;
@@ -223,12 +214,10 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
         I.M[c_begin + x] = s_M[x];
     }
     if (I.resident) {
-        const int n16 = I.slot_stride / 16;
-        for (int lc = 0; lc < c_count; ++lc) {
-            int4* cd = reinterpret_cast<int4*>(I.spins + (size_t)(c_begin + lc) * I.slot_stride);
-            const int4* cs = reinterpret_cast<const int4*>(s_chains + (size_t)lc * L.chain_stride);
-            for (int x = tid; x < n16; x += nt) cd[x] = cs[x];
-        }
+        for (int lc = 0; lc < c_count; ++lc)
+            store_split(I.spins + (size_t)(c_begin + lc) * I.slot_stride,
+                        reinterpret_cast<const int8_t*>(s_chains + (size_t)lc * L.chain_stride), N, P, G, ginv, tid,
+                        nt);
     }
     if (rank == 0) {
         for (int x = tid; x < R; x += nt) {

@@ -156,14 +156,64 @@ __device__ __forceinline__ void named_barrier(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// One 4-copy unit of the packed path: copies k = 8g + par + 2w (w = 0..3) of site i.
-// Each neighbour row contributes one 8-byte load; the field of the four copies comes from
-// a 4x4 byte transpose and dp4a (the site's h rides in a spare neighbour slot whose spins
-// are the constant +1 row); the Trotter column m/2+1 = 2 - [left differs] - [right differs]
-// is formed for all four copies at once from byte XORs.
+// Shared-memory rows of the int8 packed path are split by parity: row i holds the P/2 even
+// copies of site i, then its P/2 odd copies, so the 4 copies of one parity in an update
+// unit are one aligned word. Global rows interleave the copies (k fastest); these convert
+// one 8-copy chunk (copies 8g..8g+7) between the two layouts.
+__device__ __forceinline__ void split_chunk(uint2 v, uint32_t& even, uint32_t& odd) {
+    even = __byte_perm(v.x, v.y, 0x6420u);
+    odd = __byte_perm(v.x, v.y, 0x7531u);
+}
+__device__ __forceinline__ uint2 join_chunk(uint32_t even, uint32_t odd) {
+    return make_uint2(__byte_perm(even, odd, 0x5140u), __byte_perm(even, odd, 0x7362u));
+}
+
+// ceil(2^32 / G) for G > 1: with it, __umulhi(x, ginv) = x / G exactly while x * G < 2^32,
+// which holds for every chunk index of a chain that fits in shared memory. 0 for G = 1.
+__host__ __device__ inline uint32_t chunk_ginv(int G) {
+    return G > 1 ? (uint32_t)((0x100000000ull + (unsigned long long)G - 1ull) / (unsigned long long)G) : 0u;
+}
+__device__ __forceinline__ int chunk_of_row(int x, int G, uint32_t ginv) {
+    return ginv ? x - G * (int)__umulhi((uint32_t)x, ginv) : 0;
+}
+
+// Copy an interleaved chain (N sites x P copies, global) into the split layout (shared),
+// threads [tid0, tid0 + nthr) taking 8-copy chunks; and back. G = P / 8, ginv = chunk_ginv(G).
+__device__ __forceinline__ void load_split(int8_t* dst, const int8_t* src, int N, int P, int G, uint32_t ginv,
+                                           int tid0, int nthr) {
+    const uint2* s2 = reinterpret_cast<const uint2*>(src);
+    const int half = P >> 1;
+    for (int x = tid0; x < N * G; x += nthr) {
+        const int g = chunk_of_row(x, G, ginv);
+        const int row = 8 * x - 8 * g;  // i * P
+        uint32_t ev, od;
+        split_chunk(s2[x], ev, od);
+        *reinterpret_cast<uint32_t*>(dst + row + 4 * g) = ev;
+        *reinterpret_cast<uint32_t*>(dst + row + half + 4 * g) = od;
+    }
+}
+__device__ __forceinline__ void store_split(int8_t* dst, const int8_t* src, int N, int P, int G, uint32_t ginv,
+                                            int tid0, int nthr) {
+    uint2* d2 = reinterpret_cast<uint2*>(dst);
+    const int half = P >> 1;
+    for (int x = tid0; x < N * G; x += nthr) {
+        const int g = chunk_of_row(x, G, ginv);
+        const int row = 8 * x - 8 * g;
+        d2[x] = join_chunk(*reinterpret_cast<const uint32_t*>(src + row + 4 * g),
+                           *reinterpret_cast<const uint32_t*>(src + row + half + 4 * g));
+    }
+}
+
+// One 4-copy unit of the packed path: copies k = 8g + par + 2w (w = 0..3) of site i, which
+// are bytes 4g..4g+3 of the row's parity-par half.
 // Site descriptor (DW words): row offset i*P, i, packed J bytes (two words), then the row
 // offsets of the DC neighbour slots (the slot after the last neighbour holds h against the
 // constant +1 row; the remaining slots have J = 0).
+// Each neighbour slot contributes one word (its 4 copies); multiplied bytewise by the own
+// spins ((a ^ s) | 1 is the product of two +-1 bytes), a 4x4 byte transpose and dp4a give
+// L = s (h + sum_j J_ij s_j) of the four copies directly. The Trotter column
+// m/2+1 = 2 - [left differs] - [right differs] comes from the opposite-parity word and one
+// edge byte with byte XORs.
 template <int DC>
 struct SiteDesc {
     static constexpr int DW = (DC == 4) ? 8 : 12;
@@ -177,8 +227,9 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc,
     const uint32_t par = item & 1u;
     const uint32_t* desc = s_sdesc + (item >> 1) * SiteDesc<DC>::DW;
     const uint4 d0 = *reinterpret_cast<const uint4*>(desc);
-    const uint32_t row = d0.x;
-    const uint32_t c = 8u * (uint32_t)g;
+    const uint32_t half = (uint32_t)P >> 1;
+    const uint32_t w4 = 4u * (uint32_t)g;
+    const uint32_t own_off = par * half + w4;  // this parity's word in every row
     uint32_t nrow[DC];
     uint32_t jpack[DC / 4];
     {
@@ -197,13 +248,17 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc,
             jpack[DC > 4 ? 1 : 0] = d0.w;
         }
     }
-    const uint2 own = *reinterpret_cast<const uint2*>(sp + row + c);
-    // the one Trotter neighbour outside the chunk: copy c-1 for even copies, c+8 for odd
-    const uint32_t eoff = par ? (c + 8 == (uint32_t)P ? 0u : c + 8) : (c == 0 ? (uint32_t)P - 1 : c - 1);
+    const uint32_t row = d0.x;
+    uint32_t* own_p = reinterpret_cast<uint32_t*>(sp + row + own_off);
+    const uint32_t S = *own_p;
+    const uint32_t O = *reinterpret_cast<const uint32_t*>(sp + row + (half - par * half) + w4);
+    // the one Trotter neighbour outside the word: odd copy 8g-1 for even copies, even copy
+    // 8g+8 for odd ones (periodic)
+    const uint32_t eoff = par ? ((w4 + 4u == half) ? 0u : w4 + 4u) : (half + (g == 0 ? half - 1u : w4 - 1u));
     const uint32_t edge = (uint8_t)sp[row + eoff];
-    uint2 nb[DC];
+    uint32_t a[DC];
 #pragma unroll
-    for (int d = 0; d < DC; ++d) nb[d] = *reinterpret_cast<const uint2*>(sp + nrow[d] + c);
+    for (int d = 0; d < DC; ++d) a[d] = *reinterpret_cast<const uint32_t*>(sp + nrow[d] + own_off);
     uint4 r4;
     if (PRE) {
         r4 = rb[q * G + g];
@@ -212,49 +267,39 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc,
     }
     const uint32_t u[4] = {r4.x, r4.y, r4.z, r4.w};
 
-    const uint32_t selS = par ? 0x7531u : 0x6420u;
-    const uint32_t S = __byte_perm(own.x, own.y, selS);
-    uint32_t Rn = __byte_perm(own.x, own.y, par ? 0x0642u : 0x7531u);
-    Rn = par ? __byte_perm(Rn, edge, 0x4210u) : Rn;
-    uint32_t Ln = __byte_perm(own.x, own.y, par ? 0x6420u : 0x5310u);
-    Ln = par ? Ln : __byte_perm(Ln, edge, 0x3214u);
+    const uint32_t Ln = par ? O : __byte_perm(O, edge, 0x2104u);
+    const uint32_t Rn = par ? __byte_perm(O, edge, 0x4321u) : O;
     const uint32_t X = (S ^ Ln) & 0x02020202u;
     const uint32_t Y = (S ^ Rn) & 0x02020202u;
     const uint32_t Z = 0x02020202u - ((X + Y) >> 1);
 
-    int f[4] = {0, 0, 0, 0};
+    int L[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int b = 0; b < DC / 4; ++b) {
-        const uint32_t a0 = __byte_perm(nb[4 * b + 0].x, nb[4 * b + 0].y, selS);
-        const uint32_t a1 = __byte_perm(nb[4 * b + 1].x, nb[4 * b + 1].y, selS);
-        const uint32_t a2 = __byte_perm(nb[4 * b + 2].x, nb[4 * b + 2].y, selS);
-        const uint32_t a3 = __byte_perm(nb[4 * b + 3].x, nb[4 * b + 3].y, selS);
+        const uint32_t a0 = (a[4 * b + 0] ^ S) | 0x01010101u;
+        const uint32_t a1 = (a[4 * b + 1] ^ S) | 0x01010101u;
+        const uint32_t a2 = (a[4 * b + 2] ^ S) | 0x01010101u;
+        const uint32_t a3 = (a[4 * b + 3] ^ S) | 0x01010101u;
         const uint32_t t0 = __byte_perm(a0, a1, 0x5140u), t1 = __byte_perm(a0, a1, 0x7362u);
         const uint32_t t2 = __byte_perm(a2, a3, 0x5140u), t3 = __byte_perm(a2, a3, 0x7362u);
-        f[0] = __dp4a((int)__byte_perm(t0, t2, 0x5410u), (int)jpack[b], f[0]);
-        f[1] = __dp4a((int)__byte_perm(t0, t2, 0x7632u), (int)jpack[b], f[1]);
-        f[2] = __dp4a((int)__byte_perm(t1, t3, 0x5410u), (int)jpack[b], f[2]);
-        f[3] = __dp4a((int)__byte_perm(t1, t3, 0x7632u), (int)jpack[b], f[3]);
+        L[0] = __dp4a((int)__byte_perm(t0, t2, 0x5410u), (int)jpack[b], L[0]);
+        L[1] = __dp4a((int)__byte_perm(t0, t2, 0x7632u), (int)jpack[b], L[1]);
+        L[2] = __dp4a((int)__byte_perm(t1, t3, 0x5410u), (int)jpack[b], L[2]);
+        L[3] = __dp4a((int)__byte_perm(t1, t3, 0x7632u), (int)jpack[b], L[3]);
     }
     uint32_t F = 0;  // 0xFE in byte w when copy w flips (XOR turns +1 <-> -1)
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const int sw = (int)prmt(S, 0u, 0x8880u | (0x1110u * (uint32_t)w) | (uint32_t)w);
-        const int Lw = sw * f[w];
         const int col = (int)__byte_perm(Z, 0u, 0x4440u | (uint32_t)w);
-        const uint32_t th = thr_c[3 * Lw + col];
+        const uint32_t th = thr_c[3 * L[w] + col];
         const bool acc = (u[w] < th) | (th == 0xFFFFFFFFu);
         F |= acc ? (0xFEu << (8 * w)) : 0u;
-        sumL += acc ? Lw : 0;
+        sumL += acc ? L[w] : 0;
     }
     // flips and their Trotter columns from the packed flip mask
     nflip += __popc(F & 0x02020202u);
     sumC = __dp4a((int)(Z & (F >> 1)), 0x01010101, sumC);
-    if (F) {
-        const uint32_t lo = __byte_perm(F, 0u, par ? 0x1404u : 0x4140u);
-        const uint32_t hi = __byte_perm(F, 0u, par ? 0x3424u : 0x4342u);
-        *reinterpret_cast<uint2*>(sp + row + c) = make_uint2(own.x ^ lo, own.y ^ hi);
-    }
+    if (F) *own_p = S ^ F;
 }
 
 }  // namespace ptq

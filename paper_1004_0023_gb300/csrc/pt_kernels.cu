@@ -396,10 +396,8 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
             s_lut[x] = v;
         }
     } else {
-        const int4* src = reinterpret_cast<const int4*>(p.spins + (size_t)slot * p.slot_stride);
-        int4* dst = reinterpret_cast<int4*>(sp);
-        const int n16 = (int)(up16((size_t)N * P) / 16);
-        for (int x = tid; x < n16; x += nt) dst[x] = src[x];
+        // interleaved int8 chain in global memory -> parity-split rows in shared memory
+        load_split(sp, p.spins + (size_t)slot * p.slot_stride, N, P, P >> 3, chunk_ginv(P >> 3), tid, nt);
         int8_t* ones = reinterpret_cast<int8_t*>(smem + L.ones);
         for (int x = tid; x < P; x += nt) ones[x] = 1;
     }
@@ -504,10 +502,7 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
             dst[x] = v;
         }
     } else {
-        int4* dst = reinterpret_cast<int4*>(p.spins + (size_t)slot * p.slot_stride);
-        const int4* src = reinterpret_cast<const int4*>(sp);
-        const int n16 = (int)(up16((size_t)N * P) / 16);
-        for (int x = tid; x < n16; x += nt) dst[x] = src[x];
+        store_split(p.spins + (size_t)slot * p.slot_stride, sp, N, P, P >> 3, chunk_ginv(P >> 3), tid, nt);
     }
     if (tid == 0) {
         p.E[slot] = E;
