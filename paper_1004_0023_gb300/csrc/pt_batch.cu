@@ -146,13 +146,9 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
                 }
                 named_barrier(bar, gsize);
             }
-            int dE = -2 * sumL, dM = -4 * (sumC - nf);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                dE += __shfl_xor_sync(0xFFFFFFFFu, dE, o);
-                dM += __shfl_xor_sync(0xFFFFFFFFu, dM, o);
-                nf += __shfl_xor_sync(0xFFFFFFFFu, nf, o);
-            }
+            const int dE = __reduce_add_sync(0xFFFFFFFFu, -2 * sumL);
+            const int dM = __reduce_add_sync(0xFFFFFFFFu, -4 * (sumC - nf));
+            nf = __reduce_add_sync(0xFFFFFFFFu, nf);
             if (lane == 0) {
                 red_g[gwarp * 3 + 0] = dE;
                 red_g[gwarp * 3 + 1] = dM;

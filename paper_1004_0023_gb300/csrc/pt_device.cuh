@@ -138,13 +138,6 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 __device__ __forceinline__ void st_relaxed_s64(long long* p, long long v) {
     asm volatile("st.relaxed.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-// prmt.b32 in its generic mode: a selector nibble with its top bit set replicates the
-// sign of the selected byte (used to sign-extend packed int8 spins).
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -209,9 +202,8 @@ __device__ __forceinline__ void store_split(int8_t* dst, const int8_t* src, int 
 // Site descriptor (DW words): row offset i*P, i, packed J bytes (two words), then the row
 // offsets of the DC neighbour slots (the slot after the last neighbour holds h against the
 // constant +1 row; the remaining slots have J = 0).
-// Each neighbour slot contributes one word (its 4 copies); multiplied bytewise by the own
-// spins ((a ^ s) | 1 is the product of two +-1 bytes), a 4x4 byte transpose and dp4a give
-// L = s (h + sum_j J_ij s_j) of the four copies directly. The Trotter column
+// Each neighbour slot contributes one word (its 4 copies) to field_times_spin, which forms
+// L = s (h + sum_j J_ij s_j) of the four copies. The Trotter column
 // m/2+1 = 2 - [left differs] - [right differs] comes from the opposite-parity word and one
 // edge byte with byte XORs.
 template <int DC>
@@ -219,11 +211,58 @@ struct SiteDesc {
     static constexpr int DW = (DC == 4) ? 8 : 12;
 };
 
+// L_w = s_w (h + sum_j J_j s_j,w) for the four copies w of a unit, from the DC neighbour
+// words a[d] (4 copies of slot d as +-1 bytes), the own word S and the J bytes. A 4x4 byte
+// transpose per four slots feeds dp4a. With four slots the neighbour bytes are first
+// multiplied by the own spins ((a ^ s) | 1 is the product of two +-1 bytes), so dp4a gives
+// L directly; with eight the field is formed first and multiplied by the spin after, which
+// takes fewer ALU operations.
+template <int DC>
+__device__ __forceinline__ void field_times_spin(const uint32_t* a, uint32_t S, const uint32_t* jpack, int* L) {
+    int f[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int b = 0; b < DC / 4; ++b) {
+        uint32_t a0 = a[4 * b + 0], a1 = a[4 * b + 1], a2 = a[4 * b + 2], a3 = a[4 * b + 3];
+        if (DC == 4) {
+            a0 = (a0 ^ S) | 0x01010101u;
+            a1 = (a1 ^ S) | 0x01010101u;
+            a2 = (a2 ^ S) | 0x01010101u;
+            a3 = (a3 ^ S) | 0x01010101u;
+        }
+        const uint32_t t0 = __byte_perm(a0, a1, 0x5140u), t1 = __byte_perm(a0, a1, 0x7362u);
+        const uint32_t t2 = __byte_perm(a2, a3, 0x5140u), t3 = __byte_perm(a2, a3, 0x7362u);
+        f[0] = __dp4a((int)__byte_perm(t0, t2, 0x5410u), (int)jpack[b], f[0]);
+        f[1] = __dp4a((int)__byte_perm(t0, t2, 0x7632u), (int)jpack[b], f[1]);
+        f[2] = __dp4a((int)__byte_perm(t1, t3, 0x5410u), (int)jpack[b], f[2]);
+        f[3] = __dp4a((int)__byte_perm(t1, t3, 0x7632u), (int)jpack[b], f[3]);
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        if (DC == 4) {
+            L[w] = f[w];
+        } else {
+            const int sw = (int)(int8_t)((S >> (8 * w)) & 0xFFu);  // +1 or -1
+            L[w] = sw * f[w];
+        }
+    }
+}
+
+// The packed unit in three steps, so that a unit can be evaluated before the threshold row
+// it needs is known: evaluate (loads, fields, Trotter columns, random words), decide the
+// flips against one threshold row, commit (flip store and the sweep's sums).
+struct UnitEval {
+    uint32_t* own;  // the unit's word in shared memory
+    uint32_t S;     // its 4 copies as +-1 bytes
+    uint32_t Z;     // Trotter column m/2+1 per copy
+    int L[4];       // L = s (h + sum_j J s_j) per copy
+    uint32_t u[4];  // random words
+};
+
 template <int DC, bool PRE>
-__device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc, uint32_t item, const uint4* rb,
-                                            int q, int g, int G, int P, uint32_t t, uint32_t slot,
-                                            const PhiloxKey& key, const uint32_t* thr_c, int& sumL, int& sumC,
-                                            int& nflip) {
+__device__ __forceinline__ UnitEval packed_unit_eval(int8_t* sp, const uint32_t* s_sdesc, uint32_t item,
+                                                     const uint4* rb, int q, int g, int G, int P, uint32_t t,
+                                                     uint32_t slot, const PhiloxKey& key) {
+    UnitEval e;
     const uint32_t par = item & 1u;
     const uint32_t* desc = s_sdesc + (item >> 1) * SiteDesc<DC>::DW;
     const uint4 d0 = *reinterpret_cast<const uint4*>(desc);
@@ -249,8 +288,8 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc,
         }
     }
     const uint32_t row = d0.x;
-    uint32_t* own_p = reinterpret_cast<uint32_t*>(sp + row + own_off);
-    const uint32_t S = *own_p;
+    e.own = reinterpret_cast<uint32_t*>(sp + row + own_off);
+    const uint32_t S = *e.own;
     const uint32_t O = *reinterpret_cast<const uint32_t*>(sp + row + (half - par * half) + w4);
     // the one Trotter neighbour outside the word: odd copy 8g-1 for even copies, even copy
     // 8g+8 for odd ones (periodic)
@@ -265,41 +304,64 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc,
     } else {
         r4 = philox(make_uint4(t, d0.y, slot, (par << 24) | (uint32_t)g), key);
     }
-    const uint32_t u[4] = {r4.x, r4.y, r4.z, r4.w};
+    e.u[0] = r4.x;
+    e.u[1] = r4.y;
+    e.u[2] = r4.z;
+    e.u[3] = r4.w;
 
     const uint32_t Ln = par ? O : __byte_perm(O, edge, 0x2104u);
     const uint32_t Rn = par ? __byte_perm(O, edge, 0x4321u) : O;
     const uint32_t X = (S ^ Ln) & 0x02020202u;
     const uint32_t Y = (S ^ Rn) & 0x02020202u;
-    const uint32_t Z = 0x02020202u - ((X + Y) >> 1);
+    e.Z = 0x02020202u - ((X + Y) >> 1);
+    e.S = S;
+    field_times_spin<DC>(a, S, jpack, e.L);
+    return e;
+}
 
-    int L[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int b = 0; b < DC / 4; ++b) {
-        const uint32_t a0 = (a[4 * b + 0] ^ S) | 0x01010101u;
-        const uint32_t a1 = (a[4 * b + 1] ^ S) | 0x01010101u;
-        const uint32_t a2 = (a[4 * b + 2] ^ S) | 0x01010101u;
-        const uint32_t a3 = (a[4 * b + 3] ^ S) | 0x01010101u;
-        const uint32_t t0 = __byte_perm(a0, a1, 0x5140u), t1 = __byte_perm(a0, a1, 0x7362u);
-        const uint32_t t2 = __byte_perm(a2, a3, 0x5140u), t3 = __byte_perm(a2, a3, 0x7362u);
-        L[0] = __dp4a((int)__byte_perm(t0, t2, 0x5410u), (int)jpack[b], L[0]);
-        L[1] = __dp4a((int)__byte_perm(t0, t2, 0x7632u), (int)jpack[b], L[1]);
-        L[2] = __dp4a((int)__byte_perm(t1, t3, 0x5410u), (int)jpack[b], L[2]);
-        L[3] = __dp4a((int)__byte_perm(t1, t3, 0x7632u), (int)jpack[b], L[3]);
-    }
-    uint32_t F = 0;  // 0xFE in byte w when copy w flips (XOR turns +1 <-> -1)
+// 0xFE in byte w when copy w flips under the threshold row thr_c (offset to L = 0, m = -2).
+// Produced words (PRE) are already min(u, 2^32 - 2), which folds in the "always" entry.
+template <bool PRE>
+__device__ __forceinline__ uint32_t unit_flips(const UnitEval& e, const uint32_t* thr_c) {
+    uint32_t F = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const int col = (int)__byte_perm(Z, 0u, 0x4440u | (uint32_t)w);
-        const uint32_t th = thr_c[3 * L[w] + col];
-        const bool acc = (u[w] < th) | (th == 0xFFFFFFFFu);
+        const int col = (int)__byte_perm(e.Z, 0u, 0x4440u | (uint32_t)w);
+        const uint32_t th = thr_c[3 * e.L[w] + col];
+        const bool acc = PRE ? (e.u[w] < th) : ((e.u[w] < th) | (th == 0xFFFFFFFFu));
         F |= acc ? (0xFEu << (8 * w)) : 0u;
-        sumL += acc ? L[w] : 0;
     }
+    return F;
+}
+
+__device__ __forceinline__ void unit_commit(const UnitEval& e, uint32_t F, int& sumL, int& sumC, int& nflip) {
+#pragma unroll
+    for (int w = 0; w < 4; ++w) sumL += ((F >> (8 * w)) & 0x2u) ? e.L[w] : 0;
     // flips and their Trotter columns from the packed flip mask
     nflip += __popc(F & 0x02020202u);
-    sumC = __dp4a((int)(Z & (F >> 1)), 0x01010101, sumC);
-    if (F) *own_p = S ^ F;
+    sumC = __dp4a((int)(e.Z & (F >> 1)), 0x01010101, sumC);
+    if (F) *e.own = e.S ^ F;
+}
+
+template <int DC, bool PRE>
+__device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc, uint32_t item, const uint4* rb,
+                                            int q, int g, int G, int P, uint32_t t, uint32_t slot,
+                                            const PhiloxKey& key, const uint32_t* thr_c, int& sumL, int& sumC,
+                                            int& nflip) {
+    const UnitEval e = packed_unit_eval<DC, PRE>(sp, s_sdesc, item, rb, q, g, G, P, t, slot, key);
+    // flips and sums in one pass (the acceptance predicate feeds both)
+    uint32_t F = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int col = (int)__byte_perm(e.Z, 0u, 0x4440u | (uint32_t)w);
+        const uint32_t th = thr_c[3 * e.L[w] + col];
+        const bool acc = PRE ? (e.u[w] < th) : ((e.u[w] < th) | (th == 0xFFFFFFFFu));
+        F |= acc ? (0xFEu << (8 * w)) : 0u;
+        sumL += acc ? e.L[w] : 0;
+    }
+    nflip += __popc(F & 0x02020202u);
+    sumC = __dp4a((int)(e.Z & (F >> 1)), 0x01010101, sumC);
+    if (F) *e.own = e.S ^ F;
 }
 
 }  // namespace ptq
@@ -361,31 +423,20 @@ __device__ __forceinline__ void packed_unit_bits(uint8_t* bp, const uint32_t* s_
     const uint32_t Y = (S ^ Rn) & 0x02020202u;
     const uint32_t Z = 0x02020202u - ((X + Y) >> 1);
 
-    int f[4] = {0, 0, 0, 0};
+    uint32_t a[DC];
 #pragma unroll
-    for (int b = 0; b < DC / 4; ++b) {
-        const uint32_t a0 = lut_p[nbyte[4 * b + 0]];
-        const uint32_t a1 = lut_p[nbyte[4 * b + 1]];
-        const uint32_t a2 = lut_p[nbyte[4 * b + 2]];
-        const uint32_t a3 = lut_p[nbyte[4 * b + 3]];
-        const uint32_t t0 = __byte_perm(a0, a1, 0x5140u), t1 = __byte_perm(a0, a1, 0x7362u);
-        const uint32_t t2 = __byte_perm(a2, a3, 0x5140u), t3 = __byte_perm(a2, a3, 0x7362u);
-        f[0] = __dp4a((int)__byte_perm(t0, t2, 0x5410u), (int)jpack[b], f[0]);
-        f[1] = __dp4a((int)__byte_perm(t0, t2, 0x7632u), (int)jpack[b], f[1]);
-        f[2] = __dp4a((int)__byte_perm(t1, t3, 0x5410u), (int)jpack[b], f[2]);
-        f[3] = __dp4a((int)__byte_perm(t1, t3, 0x7632u), (int)jpack[b], f[3]);
-    }
+    for (int d = 0; d < DC; ++d) a[d] = lut_p[nbyte[d]];
+    int L[4];
+    field_times_spin<DC>(a, S, jpack, L);
     uint32_t F = 0, flipbits = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const int sw = (int)prmt(S, 0u, 0x8880u | (0x1110u * (uint32_t)w) | (uint32_t)w);
-        const int Lw = sw * f[w];
         const int col = (int)__byte_perm(Z, 0u, 0x4440u | (uint32_t)w);
-        const uint32_t th = thr_c[3 * Lw + col];
-        const bool acc = (u[w] < th) | (th == 0xFFFFFFFFu);
+        const uint32_t th = thr_c[3 * L[w] + col];
+        const bool acc = PRE ? (u[w] < th) : ((u[w] < th) | (th == 0xFFFFFFFFu));
         F |= acc ? (0xFEu << (8 * w)) : 0u;
         flipbits |= acc ? (1u << (2 * w)) : 0u;
-        sumL += acc ? Lw : 0;
+        sumL += acc ? L[w] : 0;
     }
     nflip += __popc(F & 0x02020202u);
     sumC = __dp4a((int)(Z & (F >> 1)), 0x01010101, sumC);

@@ -73,7 +73,7 @@ struct FastLayout {
         thr = o;   o += thr_bytes(p);
         acc = o;   o += acc_bytes(p);
         red = o;   o += 32 * 3 * 8;
-        ctl = o;   o += 16;
+        ctl = o;   o += 32;
         rbuf = o;
         if (pre) o += (size_t)2 * (2 * N) * (P / 8) * 16;
         total = o;
@@ -91,13 +91,20 @@ __device__ __forceinline__ unsigned long long mbox_tag(long long q) {
     return (unsigned long long)(q % kTagPeriod) + 1ull;
 }
 
+// A chain's side of the swap pass that follows a sweep: rl is the lower rung of its pair,
+// partner the other rung; active = 0 when no pass follows or the chain has no partner.
+struct SwapSide {
+    int active, rl, partner, pass;
+    long long q;
+    unsigned long long tag;
+};
+
 // Thread 0 of a chain's CTA, after the sweep's changes are reduced: update E and M, add the
-// statistics of the rung the chain sits on (to `acc`, shared or global), and run the chain's
-// side of swap pass q when one follows this sweep. Returns the chain's rung for the next
-// sweep; sets *abort when the partner's mailbox never arrived within the time limit.
-__device__ int end_of_sweep(const DevProblem& p, unsigned long long* acc, int rung, long long& E, long long& M,
-                            long long dE, long long dM, long long nflip, int s, long long q0, int sweeps_per_swap,
-                            long long timeout_ns, const PhiloxKey& key, int* abort) {
+// statistics of the rung the chain sits on (to `acc`, shared or global) and, when a swap
+// pass follows this sweep, publish (E, M) in the pass's mailbox. Does not wait.
+__device__ SwapSide eos_publish(const DevProblem& p, unsigned long long* acc, int rung, long long& E, long long& M,
+                                long long dE, long long dM, long long nflip, int s, long long q0,
+                                int sweeps_per_swap) {
     E += dE;
     M += dM;
     unsigned long long* a = acc + (size_t)rung * kAccCount;
@@ -116,32 +123,44 @@ __device__ int end_of_sweep(const DevProblem& p, unsigned long long* acc, int ru
         atomicAdd(a + kAccM2, (unsigned long long)(M * M));
         atomicAdd(a + kAccFlip, (unsigned long long)nflip);
     }
-    *abort = 0;
-    if (sweeps_per_swap <= 0 || (s + 1) % sweeps_per_swap != 0) return rung;
+    SwapSide w;
+    w.active = 0;
+    if (sweeps_per_swap <= 0 || (s + 1) % sweeps_per_swap != 0) return w;
     const int R = p.R;
-    const int pass = (s + 1) / sweeps_per_swap - 1;
-    const long long q = q0 + pass;
-    const unsigned long long tag = mbox_tag(q);
-    Mailbox* mb = p.mbox + (size_t)pass * R;
+    w.pass = (s + 1) / sweeps_per_swap - 1;
+    w.q = q0 + w.pass;
+    w.tag = mbox_tag(w.q);
+    Mailbox* mb = p.mbox + (size_t)w.pass * R;
     if (rung != p.withhold_rung) {
-        st_relaxed_u64(&mb[rung].a, ((unsigned long long)E << 24) | tag);
-        st_relaxed_u64(&mb[rung].b, ((unsigned long long)(uint32_t)(int32_t)M << 32) | tag);
+        st_relaxed_u64(&mb[rung].a, ((unsigned long long)E << 24) | w.tag);
+        st_relaxed_u64(&mb[rung].b, ((unsigned long long)(uint32_t)(int32_t)M << 32) | w.tag);
     }
-    int rl, partner;
-    if ((rung & 1) == (int)(q & 1)) {
-        rl = rung;
-        partner = rung + 1;
+    if ((rung & 1) == (int)(w.q & 1)) {
+        w.rl = rung;
+        w.partner = rung + 1;
     } else {
-        rl = rung - 1;
-        partner = rung - 1;
+        w.rl = rung - 1;
+        w.partner = rung - 1;
     }
-    if (rl < 0 || rl + 1 >= R) return rung;
+    w.active = (w.rl >= 0 && w.rl + 1 < R) ? 1 : 0;
+    return w;
+}
+
+// Thread 0 again: wait for the partner's mailbox (bounded by timeout_ns) and take the
+// decision both chains of the pair take. Returns the chain's rung for the next sweep; sets
+// *abort when the partner's mailbox never arrived within the time limit.
+__device__ int eos_decide(const DevProblem& p, const SwapSide& w, int rung, long long E, long long M,
+                          long long timeout_ns, const PhiloxKey& key, int* abort) {
+    *abort = 0;
+    if (!w.active) return rung;
+    const int R = p.R;
+    const Mailbox* mb = p.mbox + (size_t)w.pass * R;
     long long pE, pM;
     const unsigned long long start = globaltimer_ns();
     for (;;) {
-        const unsigned long long wa = ld_relaxed_u64(&mb[partner].a);
-        const unsigned long long wb = ld_relaxed_u64(&mb[partner].b);
-        if ((wa & 0xFFFFFFull) == tag && (wb & 0xFFFFFFull) == tag) {
+        const unsigned long long wa = ld_relaxed_u64(&mb[w.partner].a);
+        const unsigned long long wb = ld_relaxed_u64(&mb[w.partner].b);
+        if ((wa & 0xFFFFFFull) == w.tag && (wb & 0xFFFFFFull) == w.tag) {
             pE = (long long)wa >> 24;
             pM = (long long)(int32_t)(uint32_t)(wb >> 32);
             break;
@@ -152,15 +171,24 @@ __device__ int end_of_sweep(const DevProblem& p, unsigned long long* acc, int ru
             return rung;
         }
     }
+    const int rl = w.rl;
     const bool lower = (rung == rl);
     const bool acc_swap = swap_accept_fast(lower ? E : pE, lower ? pE : E, lower ? M : pM, lower ? pM : M,
-                                           p.coef[rl], p.coef[(R - 1) + rl], (uint32_t)q, (uint32_t)rl, key,
+                                           p.coef[rl], p.coef[(R - 1) + rl], (uint32_t)w.q, (uint32_t)rl, key,
                                            p.exact_swaps != 0);
     if (lower) {
         atomicAdd(p.swap_stats + 2 * rl, 1ull);
         if (acc_swap) atomicAdd(p.swap_stats + 2 * rl + 1, 1ull);
     }
-    return acc_swap ? partner : rung;
+    return acc_swap ? w.partner : rung;
+}
+
+// Both steps at once (the byte-wise kernel).
+__device__ int end_of_sweep(const DevProblem& p, unsigned long long* acc, int rung, long long& E, long long& M,
+                            long long dE, long long dM, long long nflip, int s, long long q0, int sweeps_per_swap,
+                            long long timeout_ns, const PhiloxKey& key, int* abort) {
+    const SwapSide w = eos_publish(p, acc, rung, E, M, dE, dM, nflip, s, q0, sweeps_per_swap);
+    return eos_decide(p, w, rung, E, M, timeout_ns, key, abort);
 }
 
 // Shared-memory threshold rows: every rung's row when they fit, else the current one.
@@ -342,7 +370,11 @@ __device__ __forceinline__ void produce_words(uint4* buf, uint32_t t, const uint
         if (g >= G) continue;
         const int q = x >> lg;
         const uint32_t it = s_items[q];
-        buf[q * G + g] = philox(make_uint4(t, it >> 1, slot, ((it & 1u) << 24) | (uint32_t)g), key);
+        // stored as min(u, 2^32 - 2): then u < thr alone is the acceptance rule, the
+        // "accept always" entry 0xFFFFFFFF included
+        const uint4 r = philox(make_uint4(t, it >> 1, slot, ((it & 1u) << 24) | (uint32_t)g), key);
+        buf[q * G + g] = make_uint4(min(r.x, 0xFFFFFFFEu), min(r.y, 0xFFFFFFFEu), min(r.z, 0xFFFFFFFEu),
+                                    min(r.w, 0xFFFFFFFEu));
     }
 }
 
@@ -422,17 +454,33 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     const uint32_t* thr_c = thr_row(p, s_thr, rung) + 3 * p.Lmax;
     const int n_items = 2 * N;
     const int lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_ctl[4] = -1;  // partner rung of the pending swap pass
+        s_ctl[5] = 0;   // a swap wait gave up
+    }
     __syncthreads();
     if (PRE && !consumer)
         produce_words(rbuf, (uint32_t)t0, s_items, n_items, G, lg, gmask, tid - NC, nt - NC, (uint32_t)slot, key);
     if (PRE) __syncthreads();
 
+    // Level 0 of the next sweep can be evaluated while the swap decision is still pending:
+    // its inputs are the spins after this sweep and the next sweep's random words; only its
+    // threshold row depends on the decision, and both candidate rows are in shared memory.
+    // Up to two level-0 units per consumer thread are held in registers.
+    // Warp 0 takes no level-0 unit, so that thread 0 can poll the partner's mailbox at once.
+    const int units0 = (s_loff[1] - s_loff[0]) << lg;
+    const bool spec_ok = !BITS && p.tables_in_smem && NC > 32 && units0 <= 2 * (NC - 32);
+    bool spec_done = false;  // level 0 of sweep s was applied at the end of sweep s - 1
+    int sumL = 0, sumC = 0, nf = 0;
+    SwapSide side;  // thread 0
+    side.active = 0;
+
     for (int s = 0; s < n_sweeps; ++s) {
         const uint32_t t = (uint32_t)(t0 + s);
-        if (consumer) {
+        if (consumer && !s_ctl[5]) {
             const uint4* rb = rbuf + (size_t)(s & 1) * n_items * G;
-            int sumL = 0, sumC = 0, nf = 0;
-            for (int lev = 0; lev < p.n_levels; ++lev) {
+            if (!spec_done) sumL = sumC = nf = 0;
+            for (int lev = spec_done ? 1 : 0; lev < p.n_levels; ++lev) {
                 const int base = s_loff[lev];
                 const int units = (s_loff[lev + 1] - base) << lg;
                 for (int u = tid; u < units; u += NC) {
@@ -448,45 +496,86 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
                 }
                 if (PRE) named_barrier(1, NC); else __syncthreads();
             }
-            int dE = -2 * sumL, dM = -4 * (sumC - nf);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                dE += __shfl_xor_sync(0xFFFFFFFFu, dE, o);
-                dM += __shfl_xor_sync(0xFFFFFFFFu, dM, o);
-                nf += __shfl_xor_sync(0xFFFFFFFFu, nf, o);
-            }
+            const int dE = __reduce_add_sync(0xFFFFFFFFu, -2 * sumL);
+            const int dM = __reduce_add_sync(0xFFFFFFFFu, -4 * (sumC - nf));
+            const int dF = __reduce_add_sync(0xFFFFFFFFu, nf);
             if (lane == 0) {
                 s_red[warp * 3 + 0] = dE;
                 s_red[warp * 3 + 1] = dM;
-                s_red[warp * 3 + 2] = nf;
+                s_red[warp * 3 + 2] = dF;
             }
             if (PRE) named_barrier(1, NC); else __syncthreads();
-            if (tid == 0) {
-                long long sE = 0, sM = 0, sF = 0;
-                for (int w = 0; w < NC / 32; ++w) {
-                    sE += s_red[w * 3 + 0];
-                    sM += s_red[w * 3 + 1];
-                    sF += s_red[w * 3 + 2];
+            if (warp == 0) {
+                // one partial per consumer warp; a chain's per-sweep changes fit in 32 bits
+                const bool has = lane < (NC >> 5);
+                const int sE = __reduce_add_sync(0xFFFFFFFFu, has ? (int)s_red[lane * 3 + 0] : 0);
+                const int sM = __reduce_add_sync(0xFFFFFFFFu, has ? (int)s_red[lane * 3 + 1] : 0);
+                const int sF = __reduce_add_sync(0xFFFFFFFFu, has ? (int)s_red[lane * 3 + 2] : 0);
+                if (lane == 0) {
+                    side = eos_publish(p, p.acc_in_smem ? s_acc : p.acc, rung, E, M, sE, sM, sF, s, q0,
+                                       sweeps_per_swap);
+                    s_ctl[4] = side.active ? side.partner : -1;
                 }
-                int abort_flag = 0;
-                s_ctl[2 * (s & 1)] = end_of_sweep(p, p.acc_in_smem ? s_acc : p.acc, rung, E, M, sE, sM, sF, s,
-                                                  q0, sweeps_per_swap, timeout_ns, key, &abort_flag);
-                s_ctl[2 * (s & 1) + 1] = abort_flag;
-            }
-            if (PRE) named_barrier(1, NC); else __syncthreads();
-            const int nr = s_ctl[2 * (s & 1)];
-            if (!s_ctl[2 * (s & 1) + 1] && nr != rung) {
-                rung = nr;
-                if (!p.tables_in_smem) load_thr(p, s_thr, rung, tid, NC);
-                thr_c = thr_row(p, s_thr, rung) + 3 * p.Lmax;
             }
         } else if (s + 1 < n_sweeps) {
             produce_words(rbuf + (size_t)((s + 1) & 1) * n_items * G, t + 1u, s_items, n_items, G, lg, gmask,
                           tid - NC, nt - NC, (uint32_t)slot, key);
         }
+        // the next sweep's random words are complete and every consumer has finished sweep s;
+        // a wait that gave up in the previous sweep ends the launch here, for every thread
         __syncthreads();
-        if (s_ctl[2 * (s & 1) + 1]) return;  // a partner never arrived; status holds PT_ETIMEDOUT
+        if (s_ctl[5]) return;  // status holds PT_ETIMEDOUT
+        if (!consumer) continue;
+
+        // level 0 of sweep s + 1 under both candidate rungs
+        const bool spec = spec_ok && s + 1 < n_sweeps;
+        const int prung = s_ctl[4];
+        UnitEval ev[2];
+        uint32_t Fa[2] = {0u, 0u}, Fb[2] = {0u, 0u};
+        bool valid[2] = {false, false};
+        if (spec) {
+            const uint4* rb1 = rbuf + (size_t)((s + 1) & 1) * n_items * G;
+            const uint32_t* thr_b = prung >= 0 ? thr_row(p, s_thr, prung) + 3 * p.Lmax : thr_c;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int u = (tid - 32) + k * (NC - 32);
+                const int g = u & gmask;
+                valid[k] = tid >= 32 && u < units0 && g < G;
+                if (valid[k]) {
+                    const int q = s_loff[0] + (u >> lg);
+                    ev[k] = packed_unit_eval<DC, PRE>(sp, s_desc, s_items[q], rb1, q, g, G, P, t + 1u, (uint32_t)slot,
+                                                      key);
+                    Fa[k] = unit_flips<PRE>(ev[k], thr_c);
+                    Fb[k] = prung >= 0 ? unit_flips<PRE>(ev[k], thr_b) : Fa[k];
+                }
+            }
+        }
+        if (tid == 0) {
+            int abort_flag = 0;
+            s_ctl[2 * (s & 1)] = eos_decide(p, side, rung, E, M, timeout_ns, key, &abort_flag);
+            if (abort_flag) s_ctl[5] = 1;  // a partner never arrived
+        }
+        if (PRE) named_barrier(1, NC); else __syncthreads();
+        if (s_ctl[5]) continue;  // skip to the next barrier with the producers, then leave
+        const int nr = s_ctl[2 * (s & 1)];
+        const bool moved = nr != rung;
+        if (moved) {
+            rung = nr;
+            if (!p.tables_in_smem) load_thr(p, s_thr, rung, tid, NC);
+            thr_c = thr_row(p, s_thr, rung) + 3 * p.Lmax;
+        }
+        spec_done = spec;
+        if (spec) {
+            sumL = sumC = nf = 0;
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                if (valid[k]) unit_commit(ev[k], moved ? Fb[k] : Fa[k], sumL, sumC, nf);
+        }
+        // the next sweep's reads of shared memory (level 1, or a reloaded threshold row) follow
+        if (PRE) named_barrier(1, NC); else __syncthreads();
     }
+    __syncthreads();
+    if (s_ctl[5]) return;  // the last sweep's wait gave up
     flush_acc(p, s_acc, tid, nt);
 
     if (BITS) {
