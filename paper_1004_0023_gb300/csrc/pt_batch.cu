@@ -122,6 +122,8 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
     uint32_t* thr_g = s_thr + (size_t)grp * L.thr_words;
     long long* red_g = s_red + (size_t)grp * (gsize / 32) * 3;
     const int lane = tid & 31, gwarp = gtid >> 5;
+    const bool g_fixed = (gsize & gmask) == 0;
+    const int g_own = gtid & gmask, q_lane = gtid >> lg, q_step = gsize >> lg;
 
     for (int s = 0; s < I.n_sweeps; ++s) {
         const uint32_t t = (uint32_t)(I.t0 + s);
@@ -136,13 +138,23 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
             int sumL = 0, sumC = 0, nf = 0;
             for (int lev = 0; lev < I.n_levels; ++lev) {
                 const int base = s_loff[lev];
-                const int units = (s_loff[lev + 1] - base) << lg;
-                for (int u = gtid; u < units; u += gsize) {
-                    const int g = u & gmask;
-                    if (g >= G) continue;
-                    const int q = base + (u >> lg);
-                    packed_unit<DC, false>(buf, s_sdesc, s_items[q], nullptr, q, g, G, P, t, (uint32_t)rho, key,
-                                           thr_c, sumL, sumC, nf);
+                if (g_fixed) {
+                    // this thread's column g never changes (see the single-problem kernel)
+                    if (g_own < G) {
+                        const int end = s_loff[lev + 1];
+                        for (int q = base + q_lane; q < end; q += q_step)
+                            packed_unit<DC, false>(buf, s_sdesc, s_items[q], nullptr, q, g_own, G, P, t,
+                                                   (uint32_t)rho, key, thr_c, sumL, sumC, nf);
+                    }
+                } else {
+                    const int units = (s_loff[lev + 1] - base) << lg;
+                    for (int u = gtid; u < units; u += gsize) {
+                        const int g = u & gmask;
+                        if (g >= G) continue;
+                        const int q = base + (u >> lg);
+                        packed_unit<DC, false>(buf, s_sdesc, s_items[q], nullptr, q, g, G, P, t, (uint32_t)rho, key,
+                                               thr_c, sumL, sumC, nf);
+                    }
                 }
                 named_barrier(bar, gsize);
             }

@@ -471,6 +471,10 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     const int units0 = (s_loff[1] - s_loff[0]) << lg;
     const bool spec_ok = !BITS && p.tables_in_smem && NC > 32 && units0 <= 2 * (NC - 32);
     bool spec_done = false;  // level 0 of sweep s was applied at the end of sweep s - 1
+    // units u = tid + k NC of a level have the same column g = u mod 2^lg when NC is a
+    // multiple of 2^lg: the thread then walks items q = base + (tid >> lg) + k (NC >> lg)
+    const bool g_fixed = (NC & gmask) == 0;
+    const int g_own = tid & gmask, q_lane = tid >> lg, q_step = NC >> lg;
     int sumL = 0, sumC = 0, nf = 0;
     SwapSide side;  // thread 0
     side.active = 0;
@@ -482,17 +486,32 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
             if (!spec_done) sumL = sumC = nf = 0;
             for (int lev = spec_done ? 1 : 0; lev < p.n_levels; ++lev) {
                 const int base = s_loff[lev];
-                const int units = (s_loff[lev + 1] - base) << lg;
-                for (int u = tid; u < units; u += NC) {
-                    const int g = u & gmask;
-                    if (g >= G) continue;
-                    const int q = base + (u >> lg);
-                    if (BITS)
-                        packed_unit_bits<DC, PRE>(bp, s_desc, s_items[q], rb, q, g, G, s_lut, t, (uint32_t)slot, key,
-                                                  thr_c, sumL, sumC, nf);
-                    else
-                        packed_unit<DC, PRE>(sp, s_desc, s_items[q], rb, q, g, G, P, t, (uint32_t)slot, key, thr_c,
-                                             sumL, sumC, nf);
+                if (g_fixed) {
+                    // this thread's column g never changes: its row offsets are loop invariants
+                    if (g_own < G) {
+                        const int end = s_loff[lev + 1];
+                        for (int q = base + q_lane; q < end; q += q_step) {
+                            if (BITS)
+                                packed_unit_bits<DC, PRE>(bp, s_desc, s_items[q], rb, q, g_own, G, s_lut, t,
+                                                          (uint32_t)slot, key, thr_c, sumL, sumC, nf);
+                            else
+                                packed_unit<DC, PRE>(sp, s_desc, s_items[q], rb, q, g_own, G, P, t, (uint32_t)slot,
+                                                     key, thr_c, sumL, sumC, nf);
+                        }
+                    }
+                } else {
+                    const int units = (s_loff[lev + 1] - base) << lg;
+                    for (int u = tid; u < units; u += NC) {
+                        const int g = u & gmask;
+                        if (g >= G) continue;
+                        const int q = base + (u >> lg);
+                        if (BITS)
+                            packed_unit_bits<DC, PRE>(bp, s_desc, s_items[q], rb, q, g, G, s_lut, t, (uint32_t)slot,
+                                                      key, thr_c, sumL, sumC, nf);
+                        else
+                            packed_unit<DC, PRE>(sp, s_desc, s_items[q], rb, q, g, G, P, t, (uint32_t)slot, key,
+                                                 thr_c, sumL, sumC, nf);
+                    }
                 }
                 if (PRE) named_barrier(1, NC); else __syncthreads();
             }
