@@ -383,7 +383,7 @@ __device__ __forceinline__ void produce_words(uint4* buf, uint32_t t, const uint
 // random words of sweep s+1 into one shared buffer while the consumer warps run the levels
 // of sweep s out of the other; consumers synchronise levels on named barrier 1 and both
 // groups meet once per sweep.
-template <int DC, bool PRE, bool BITS = false>
+template <int DC, bool PRE, bool BITS = false, bool SPEC = true>
 __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot, long long t0, long long q0,
                                                   int n_sweeps, int sweeps_per_swap, long long timeout_ns,
                                                   int n_consumer, unsigned char* smem) {
@@ -469,7 +469,7 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     // Up to two level-0 units per consumer thread are held in registers.
     // Warp 0 takes no level-0 unit, so that thread 0 can poll the partner's mailbox at once.
     const int units0 = (s_loff[1] - s_loff[0]) << lg;
-    const bool spec_ok = !BITS && p.tables_in_smem && NC > 32 && units0 <= 2 * (NC - 32);
+    const bool spec_ok = SPEC && !BITS && p.tables_in_smem && NC > 32 && units0 <= 2 * (NC - 32);
     bool spec_done = false;  // level 0 of sweep s was applied at the end of sweep s - 1
     // units u = tid + k NC of a level have the same column g = u mod 2^lg when NC is a
     // multiple of 2^lg: the thread then walks items q = base + (tid >> lg) + k (NC >> lg)
@@ -625,8 +625,9 @@ __global__ void __launch_bounds__(MAXT, 1)
 sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
                     long long timeout_ns, int n_consumer) {
     extern __shared__ __align__(16) unsigned char smem[];
-    sweep_packed_body<DC, PRE, BITS>(p, blockIdx.x, t0, q0, n_sweeps, sweeps_per_swap, timeout_ns, n_consumer,
-                                     smem);
+    // the held level-0 units do not fit the 64 registers of a 1024-thread block
+    sweep_packed_body<DC, PRE, BITS, (MAXT <= 512)>(p, blockIdx.x, t0, q0, n_sweeps, sweeps_per_swap, timeout_ns,
+                                                    n_consumer, smem);
 }
 
 // Several problems in one cooperative launch (all chains resident at once): block b sweeps
