@@ -240,10 +240,12 @@ const char* pt_batch_last_error(const pt_batch* b);
  * arrival order while a slot (max_active) and room in the device arena are free. An
  * admitted request's state and counters live in the arena; all of its sweeps are launched
  * at once on one stream of a pool (one CTA per chain), so requests that arrive while others
- * run overlap with them on the device. In stepped mode each step instead advances every
- * admitted request by quantum_sweeps sweeps in one launch and waits for it. Results are read with
- * pt_server_read_result and the arena room is returned by pt_server_release. Each result
- * equals pt_create + pt_run of that request alone. Same request limits as pt_batch. */
+ * run overlap with them on the device. When a backlog of 8 or more requests waits, they
+ * start together in one persistent batched launch (as pt_batch_run) instead. In stepped
+ * mode each step instead advances every admitted request by quantum_sweeps sweeps in one
+ * launch and waits for it. Results are read with pt_server_read_result and the arena room
+ * is returned by pt_server_release. Each result equals pt_create + pt_run of that request
+ * alone. Same request limits as pt_batch. */
 typedef struct pt_server pt_server;
 
 typedef struct {
@@ -263,6 +265,7 @@ typedef struct {
     int64_t steps;
     int64_t kernel_launches;
     int64_t wide_steps;     /* steps that ran one CTA per chain (the rest packed chains) */
+    int64_t group_launches; /* streamed mode: backlogs started together in one batched launch */
 } pt_server_info;
 
 int pt_server_create(const pt_server_options* opt, void* cuda_stream, pt_server** out);

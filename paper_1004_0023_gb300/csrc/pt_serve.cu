@@ -11,9 +11,11 @@
 // Default (streamed) mode: every admitted request is launched at once, with all of its
 // sweeps, on one stream of a pool -- one CTA per chain, the launch plan pt_create would
 // choose -- and its completion is tracked with an event. Requests that arrive while others
-// run start as soon as a slot and arena room free up, and the GPU runs their kernels side
-// by side as SMs become free, so the device does the continuous batching at CTA
-// granularity. Stepped mode (pt_server_options.reserved[1] = 1) instead advances all
+// run start as soon as a slot, arena room and the in-flight chain budget allow, and the
+// GPU runs their kernels side by side as SMs become free, so the device does the
+// continuous batching at CTA granularity. A backlog (kGroupMin or more waiting requests)
+// starts together in one persistent batched launch, which packs chains onto clusters and
+// sustains a higher rate under overload. Stepped mode (pt_server_options.reserved[1] = 1) instead advances all
 // admitted requests by a quantum of sweeps per launch, one CTA per chain when they all fit
 // (wide), chains packed onto clusters otherwise (packed).
 // A request's arithmetic never depends on what else runs or on the launch shape: its
@@ -81,6 +83,13 @@ class ArenaAllocator {
     size_t size_, used_ = 0;
 };
 
+// Requests launched together as one persistent batched launch share a device block holding
+// their records, the work order, the work counter and a status word.
+struct ServeGroup {
+    size_t off = 0, bytes = 0, status_off = 0;
+    int refs = 0;
+};
+
 struct ServeReq {
     int64_t id;
     pt_request req;  // pointers cleared after preparation
@@ -92,10 +101,18 @@ struct ServeReq {
     // streamed mode
     cudaEvent_t done = nullptr;
     int stream_idx = 0;
+    ServeGroup* group = nullptr;  // set while the request runs in a batched launch
 };
 
 // Streamed mode launches a request's sweeps in pieces of at most this many swap passes.
 constexpr int kStreamedPasses = 256;
+
+// Streamed mode under backlog: once this many requests wait, they start together in one
+// persistent batched launch (chains packed onto thread-block clusters), which sustains a
+// higher rate than one launch per request. Below it, a request starts on its own launch
+// while the chains already in flight number less than kChainBudgetPerSm per SM.
+constexpr int kGroupMin = 8;
+constexpr int kChainBudgetPerSm = 2;
 
 }  // namespace
 
@@ -114,6 +131,8 @@ struct pt_server {
     bool streamed;
     std::vector<cudaStream_t> pool;
     int next_stream;
+    long long inflight_chains;  // streamed mode: chains of the requests on the device
+    int64_t group_launches;
     size_t smem_cap;
     std::map<int64_t, ServeReq*> reqs;
     std::deque<int64_t> queued;
@@ -179,6 +198,8 @@ extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream,
     s->streamed = !(opt && (opt->reserved[1] == 1 || opt->reserved[0] == 1));  // reserved[1] == 1: stepped
     s->next_stream = 0;
     s->wide_steps = 0;
+    s->inflight_chains = 0;
+    s->group_launches = 0;
     if (s->cluster > 16 || s->max_active > 65536) {
         delete s;
         return sfail(nullptr, PT_EINVAL, "cluster_size <= 16 and max_active <= 65536");
@@ -341,10 +362,8 @@ static int admit(pt_server* s) {
 }
 
 // Streamed mode: place a request in the arena and launch all of its sweeps on a pool stream.
-static int launch_streamed(pt_server* s, ServeReq* q) {
-    cudaStream_t st = s->pool[s->next_stream];
-    q->stream_idx = s->next_stream;
-    s->next_stream = (s->next_stream + 1) % (int)s->pool.size();
+// A newly admitted request's constants, zeroed state and initial spins, on stream st.
+static int upload_request(pt_server* s, ServeReq* q, cudaStream_t st) {
     unsigned char* base = s->arena + q->block_off;
     const Prepared& pr = q->prep;
     const int gthreads = q->inst.group_threads, resident = q->inst.resident;
@@ -370,6 +389,18 @@ static int launch_streamed(pt_server* s, ServeReq* q) {
                                st)) != cudaSuccess)
         return sfail(s, PT_ECUDA, "streamed admission: %s", cudaGetErrorString(e));
     s->launches += 1;
+    return PT_OK;
+}
+
+static int launch_streamed(pt_server* s, ServeReq* q) {
+    cudaStream_t st = s->pool[s->next_stream];
+    q->stream_idx = s->next_stream;
+    s->next_stream = (s->next_stream + 1) % (int)s->pool.size();
+    int rc = upload_request(s, q, st);
+    if (rc) return rc;
+    unsigned char* base = s->arena + q->block_off;
+    const Prepared& pr = q->prep;
+    cudaError_t e;
 
     // the single-problem packed kernel, as pt_create would plan it
     DevProblem p;
@@ -475,6 +506,73 @@ static int launch_streamed(pt_server* s, ServeReq* q) {
     return PT_OK;
 }
 
+// Requests g, admitted together, in one persistent batched launch on one stream of the pool.
+// Returns 1 (nothing launched) when the arena has no room for the group's block.
+static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
+    const int n = (int)g.size();
+    ServeGroup* grp = new ServeGroup();
+    const size_t order_off = ((size_t)n * sizeof(BatchInstance) + 255) & ~(size_t)255;
+    const size_t ctr_off = order_off + (((size_t)n * sizeof(int32_t) + 255) & ~(size_t)255);
+    grp->status_off = ctr_off + 16;
+    grp->bytes = ctr_off + 256;
+    if (!s->alloc->alloc(grp->bytes, &grp->off)) {
+        delete grp;
+        return 1;
+    }
+    cudaStream_t st = s->pool[s->next_stream];
+    const int sidx = s->next_stream;
+    s->next_stream = (s->next_stream + 1) % (int)s->pool.size();
+    std::vector<BatchInstance> insts(n);
+    size_t smem = 0;
+    for (int k = 0; k < n; ++k) {
+        ServeReq* q = g[k];
+        int rc = upload_request(s, q, st);
+        if (rc) return rc;
+        q->inst.n_sweeps = (int)q->remaining;
+        choose_groups(q->inst, s->cluster, s->threads, s->smem_cap);
+        smem = std::max(smem, batch_smem_bytes(q->inst, s->cluster, s->threads));
+        insts[k] = q->inst;
+    }
+    std::vector<int32_t> order(n);
+    for (int k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const double wx = (double)insts[x].N * insts[x].P * insts[x].R * (double)insts[x].n_sweeps;
+        const double wy = (double)insts[y].N * insts[y].P * insts[y].R * (double)insts[y].n_sweeps;
+        return wx > wy;
+    });
+    unsigned char* gb = s->arena + grp->off;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(gb, insts.data(), (size_t)n * sizeof(BatchInstance), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(gb + order_off, order.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(gb + ctr_off, 0, 256, st)) != cudaSuccess)
+        return sfail(s, PT_ECUDA, "group upload: %s", cudaGetErrorString(e));
+    BatchParams bp;
+    bp.inst = (BatchInstance*)gb;
+    bp.order = (const int32_t*)(gb + order_off);
+    bp.count = n;
+    bp.next_job = (int*)(gb + ctr_off);
+    bp.status = (int*)(gb + grp->status_off);
+    if ((e = launch_batch(bp, s->cluster, std::min(s->n_clusters, n), s->threads, smem, st)) != cudaSuccess)
+        return sfail(s, PT_ECUDA, "group launch: %s", cudaGetErrorString(e));
+    s->launches += 1;
+    s->group_launches += 1;
+    for (ServeReq* q : g) {
+        if (!q->done && (e = cudaEventCreateWithFlags(&q->done, cudaEventDisableTiming)) != cudaSuccess)
+            return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+        if ((e = cudaEventRecord(q->done, st)) != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+        q->stream_idx = sidx;
+        q->inst.t0 += q->remaining;
+        if (q->inst.sweeps_per_swap > 0) q->inst.q0 += q->remaining / q->inst.sweeps_per_swap;
+        q->remaining = 0;
+        q->state = 1;
+        q->group = grp;
+        grp->refs += 1;
+    }
+    return PT_OK;
+}
+
 static int step_streamed(pt_server* s) {
     // completions first, so their arena room can go to queued requests
     std::vector<int64_t> still;
@@ -487,24 +585,59 @@ static int step_streamed(pt_server* s) {
         }
         if (e != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
         int st = 0;
-        const cudaError_t e2 =
-            cudaMemcpy(&st, s->arena + q->block_off + q->prep.off_status, sizeof(int), cudaMemcpyDeviceToHost);
+        const size_t status_at = q->group ? q->group->off + q->group->status_off : q->block_off + q->prep.off_status;
+        const cudaError_t e2 = cudaMemcpy(&st, s->arena + status_at, sizeof(int), cudaMemcpyDeviceToHost);
         if (e2 != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e2));
         if (st == PT_ETIMEDOUT) return sfail(s, PT_ETIMEDOUT, "a swap wait timed out");
         if (st) return sfail(s, PT_ECUDA, "device status %d", st);
+        if (q->group && --q->group->refs == 0) {
+            s->alloc->release(q->group->off, q->group->bytes);
+            delete q->group;
+        }
+        q->group = nullptr;
+        s->inflight_chains -= q->prep.R;
         q->state = 2;
         s->finished_unreported.push_back(id);
     }
     s->active.swap(still);
-    while (!s->queued.empty() && (int)s->active.size() < s->max_active) {
-        ServeReq* q = s->reqs[s->queued.front()];
-        size_t off = 0;
-        if (!s->alloc->alloc(q->block_bytes, &off)) break;
-        q->block_off = off;
-        s->queued.pop_front();
-        const int rc = launch_streamed(s, q);
-        if (rc) return rc;
-        s->active.push_back(q->id);
+    const long long budget = (long long)kChainBudgetPerSm * s->n_sm;
+    if ((int)s->queued.size() >= kGroupMin) {
+        // backlog: every queued request that gets a slot and arena room starts in one launch
+        std::vector<ServeReq*> g;
+        while (!s->queued.empty() && (int)s->active.size() < s->max_active) {
+            ServeReq* q = s->reqs[s->queued.front()];
+            size_t off = 0;
+            if (!s->alloc->alloc(q->block_bytes, &off)) break;
+            q->block_off = off;
+            s->queued.pop_front();
+            s->active.push_back(q->id);
+            s->inflight_chains += q->prep.R;
+            g.push_back(q);
+        }
+        if (!g.empty()) {
+            const int rc = launch_group(s, g);
+            if (rc > 0) {
+                for (ServeReq* q : g) {  // no room for the group's block: one launch each
+                    const int rc2 = launch_streamed(s, q);
+                    if (rc2) return rc2;
+                }
+            } else if (rc) {
+                return rc;
+            }
+        }
+    } else {
+        while (!s->queued.empty() && (int)s->active.size() < s->max_active) {
+            ServeReq* q = s->reqs[s->queued.front()];
+            if (!s->active.empty() && s->inflight_chains + q->prep.R > budget) break;
+            size_t off = 0;
+            if (!s->alloc->alloc(q->block_bytes, &off)) break;
+            q->block_off = off;
+            s->queued.pop_front();
+            const int rc = launch_streamed(s, q);
+            if (rc) return rc;
+            s->active.push_back(q->id);
+            s->inflight_chains += q->prep.R;
+        }
     }
     s->steps += 1;
     return PT_OK;
@@ -751,6 +884,7 @@ extern "C" int pt_server_get_info(const pt_server* s, pt_server_info* o) {
     o->steps = s->steps;
     o->kernel_launches = s->launches;
     o->wide_steps = s->wide_steps;
+    o->group_launches = s->group_launches;
     return PT_OK;
 }
 

@@ -70,7 +70,7 @@ class pt_server_options(ctypes.Structure):
 
 class pt_server_info(ctypes.Structure):
     _fields_ = [("active", _i32), ("queued", _i32), ("arena_bytes", _i64), ("arena_used", _i64), ("steps", _i64),
-                ("kernel_launches", _i64), ("wide_steps", _i64)]
+                ("kernel_launches", _i64), ("wide_steps", _i64), ("group_launches", _i64)]
 
 
 class pt_device_problem(ctypes.Structure):

@@ -81,7 +81,8 @@ def replay_batched(trace, quantum_sweeps=100, max_active=512, arena_bytes=0, clu
     info = srv.info()
     out = _summary(lat, sum(attempts[r] for r in done_t), wall,
                    {"mode": "stepped" if stepped else "streamed", "submitted": k, "max_active_seen": max_mix, "steps": int(info.steps),
-                    "wide_steps": int(info.wide_steps), "kernel_launches": int(info.kernel_launches),
+                    "wide_steps": int(info.wide_steps), "group_launches": int(info.group_launches),
+                    "kernel_launches": int(info.kernel_launches),
                     "quantum_sweeps": quantum_sweeps})
     srv.close()
     return out

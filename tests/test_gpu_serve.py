@@ -76,6 +76,28 @@ def test_results_are_the_same_alone_and_in_the_mix(arena_bytes, max_active, step
     srv.close()
 
 
+def test_backlog_starts_as_one_batched_launch_with_the_same_bits():
+    """Twenty requests submitted before the first step form a backlog: they start together
+    in one persistent batched launch, and each result still equals the request run alone."""
+    probs = _requests(20, 9, (30, 120))
+    srv = pt.Server()
+    ids = {srv.submit(p): k for k, p in enumerate(probs)}
+    results = {}
+    while len(results) < len(probs):
+        for rid in srv.step():
+            results[ids[rid]] = srv.result(rid)
+            srv.release(rid)
+    info = srv.info()
+    assert info.group_launches >= 1
+    assert info.active == 0 and info.queued == 0 and info.arena_used == 0
+    for k, p in enumerate(probs):
+        alone = pt.PT.from_problem(p)
+        alone.run(p.n_sweeps, p.sweeps_per_swap)
+        _same(results[k][0], results[k][1], alone.read_state(), alone.obs(), "request %d vs alone" % k)
+        alone.close()
+    srv.close()
+
+
 def test_server_rejects_a_request_larger_than_its_arena():
     srv = pt.Server(arena_bytes=1 << 16, max_active=4, quantum_sweeps=8)
     rng = np.random.default_rng(3)
