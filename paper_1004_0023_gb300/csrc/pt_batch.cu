@@ -135,7 +135,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
             for (int x = gtid; x < I.nL3; x += gsize) thr_g[x] = I.thr[(size_t)rung * I.nL3 + x];
             named_barrier(bar, gsize);
             const uint32_t* thr_c = thr_g + 3 * I.Lmax;
-            int sumL = 0, sumC = 0, nf = 0;
+            int sumL = 0, sumC = 0, nf = 0;  // sumC and nf count twice (see unit_commit)
             for (int lev = 0; lev < I.n_levels; ++lev) {
                 const int base = s_loff[lev];
                 if (g_fixed) {
@@ -159,8 +159,8 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
                 named_barrier(bar, gsize);
             }
             const int dE = __reduce_add_sync(0xFFFFFFFFu, -2 * sumL);
-            const int dM = __reduce_add_sync(0xFFFFFFFFu, -4 * (sumC - nf));
-            nf = __reduce_add_sync(0xFFFFFFFFu, nf);
+            const int dM = __reduce_add_sync(0xFFFFFFFFu, -2 * (sumC - nf));  // both counted twice
+            nf = __reduce_add_sync(0xFFFFFFFFu, nf) >> 1;
             if (lane == 0) {
                 red_g[gwarp * 3 + 0] = dE;
                 red_g[gwarp * 3 + 1] = dM;

@@ -247,6 +247,14 @@ __device__ __forceinline__ void field_times_spin(const uint32_t* a, uint32_t S, 
     }
 }
 
+// Threshold entry thr_c[3 L + col] of copy w, col = byte w of Z: the byte offset
+// 4 (3 L + col) comes out of one dp4a (Z's byte w times 4, plus 12 L), keeping the byte
+// extraction and the index arithmetic off the ALU pipe.
+__device__ __forceinline__ uint32_t thr_entry(const uint32_t* thr_c, uint32_t Z, int L, int w) {
+    const int off = __dp4a((int)Z, 4 << (8 * w), 12 * L);
+    return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(thr_c) + off);
+}
+
 // The packed unit in three steps, so that a unit can be evaluated before the threshold row
 // it needs is known: evaluate (loads, fields, Trotter columns, random words), decide the
 // flips against one threshold row, commit (flip store and the sweep's sums).
@@ -292,9 +300,10 @@ __device__ __forceinline__ UnitEval packed_unit_eval(int8_t* sp, const uint32_t*
     const uint32_t S = *e.own;
     const uint32_t O = *reinterpret_cast<const uint32_t*>(sp + row + (half - par * half) + w4);
     // the one Trotter neighbour outside the word: odd copy 8g-1 for even copies, even copy
-    // 8g+8 for odd ones (periodic)
-    const uint32_t eoff = par ? ((w4 + 4u == half) ? 0u : w4 + 4u) : (half + (g == 0 ? half - 1u : w4 - 1u));
-    const uint32_t edge = (uint8_t)sp[row + eoff];
+    // 8g+8 for odd ones (periodic); parity selects by multiply-add, not by select
+    const uint32_t e_even = half + (g == 0 ? half - 1u : w4 - 1u);
+    const uint32_t e_odd = (w4 + 4u == half) ? 0u : w4 + 4u;
+    const uint32_t edge = (uint8_t)sp[row + e_even + par * (e_odd - e_even)];
     uint32_t a[DC];
 #pragma unroll
     for (int d = 0; d < DC; ++d) a[d] = *reinterpret_cast<const uint32_t*>(sp + nrow[d] + own_off);
@@ -309,8 +318,10 @@ __device__ __forceinline__ UnitEval packed_unit_eval(int8_t* sp, const uint32_t*
     e.u[2] = r4.z;
     e.u[3] = r4.w;
 
-    const uint32_t Ln = par ? O : __byte_perm(O, edge, 0x2104u);
-    const uint32_t Rn = par ? __byte_perm(O, edge, 0x4321u) : O;
+    // left / right Trotter neighbours: the opposite-parity word itself or shifted by one byte
+    // with the edge copy (selectors 0x3210 = itself, 0x2104 = up, 0x4321 = down)
+    const uint32_t Ln = __byte_perm(O, edge, 0x2104u + par * (0x3210u - 0x2104u));
+    const uint32_t Rn = __byte_perm(O, edge, 0x3210u + par * (0x4321u - 0x3210u));
     const uint32_t X = (S ^ Ln) & 0x02020202u;
     const uint32_t Y = (S ^ Rn) & 0x02020202u;
     e.Z = 0x02020202u - ((X + Y) >> 1);
@@ -326,41 +337,42 @@ __device__ __forceinline__ uint32_t unit_flips(const UnitEval& e, const uint32_t
     uint32_t F = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const int col = (int)__byte_perm(e.Z, 0u, 0x4440u | (uint32_t)w);
-        const uint32_t th = thr_c[3 * e.L[w] + col];
+        const uint32_t th = thr_entry(thr_c, e.Z, e.L[w], w);
         const bool acc = PRE ? (e.u[w] < th) : ((e.u[w] < th) | (th == 0xFFFFFFFFu));
         F |= acc ? (0xFEu << (8 * w)) : 0u;
     }
     return F;
 }
 
-__device__ __forceinline__ void unit_commit(const UnitEval& e, uint32_t F, int& sumL, int& sumC, int& nflip) {
+// sumC2 and nflip2 count twice the Trotter columns and the flips: the flip mask bytes
+// (F & 0x02020202 = 2 per flip) feed dp4a directly.
+__device__ __forceinline__ void unit_commit(const UnitEval& e, uint32_t F, int& sumL, int& sumC2, int& nflip2) {
 #pragma unroll
     for (int w = 0; w < 4; ++w) sumL += ((F >> (8 * w)) & 0x2u) ? e.L[w] : 0;
-    // flips and their Trotter columns from the packed flip mask
-    nflip += __popc(F & 0x02020202u);
-    sumC = __dp4a((int)(e.Z & (F >> 1)), 0x01010101, sumC);
+    const uint32_t Fm = F & 0x02020202u;
+    nflip2 = __dp4a((int)Fm, 0x01010101, nflip2);
+    sumC2 = __dp4a((int)e.Z, (int)Fm, sumC2);
     if (F) *e.own = e.S ^ F;
 }
 
 template <int DC, bool PRE>
 __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc, uint32_t item, const uint4* rb,
                                             int q, int g, int G, int P, uint32_t t, uint32_t slot,
-                                            const PhiloxKey& key, const uint32_t* thr_c, int& sumL, int& sumC,
-                                            int& nflip) {
+                                            const PhiloxKey& key, const uint32_t* thr_c, int& sumL, int& sumC2,
+                                            int& nflip2) {
     const UnitEval e = packed_unit_eval<DC, PRE>(sp, s_sdesc, item, rb, q, g, G, P, t, slot, key);
     // flips and sums in one pass (the acceptance predicate feeds both)
     uint32_t F = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const int col = (int)__byte_perm(e.Z, 0u, 0x4440u | (uint32_t)w);
-        const uint32_t th = thr_c[3 * e.L[w] + col];
+        const uint32_t th = thr_entry(thr_c, e.Z, e.L[w], w);
         const bool acc = PRE ? (e.u[w] < th) : ((e.u[w] < th) | (th == 0xFFFFFFFFu));
         F |= acc ? (0xFEu << (8 * w)) : 0u;
         sumL += acc ? e.L[w] : 0;
     }
-    nflip += __popc(F & 0x02020202u);
-    sumC = __dp4a((int)(e.Z & (F >> 1)), 0x01010101, sumC);
+    const uint32_t Fm = F & 0x02020202u;
+    nflip2 = __dp4a((int)Fm, 0x01010101, nflip2);
+    sumC2 = __dp4a((int)e.Z, (int)Fm, sumC2);
     if (F) *e.own = e.S ^ F;
 }
 
@@ -376,7 +388,7 @@ template <int DC, bool PRE>
 __device__ __forceinline__ void packed_unit_bits(uint8_t* bp, const uint32_t* s_sdesc, uint32_t item,
                                                  const uint4* rb, int q, int g, int G, const uint32_t* lut,
                                                  uint32_t t, uint32_t slot, const PhiloxKey& key,
-                                                 const uint32_t* thr_c, int& sumL, int& sumC, int& nflip) {
+                                                 const uint32_t* thr_c, int& sumL, int& sumC2, int& nflip2) {
     const uint32_t par = item & 1u;
     const uint32_t* desc = s_sdesc + (item >> 1) * SiteDesc<DC>::DW;
     const uint4 d0 = *reinterpret_cast<const uint4*>(desc);
@@ -431,15 +443,15 @@ __device__ __forceinline__ void packed_unit_bits(uint8_t* bp, const uint32_t* s_
     uint32_t F = 0, flipbits = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const int col = (int)__byte_perm(Z, 0u, 0x4440u | (uint32_t)w);
-        const uint32_t th = thr_c[3 * L[w] + col];
+        const uint32_t th = thr_entry(thr_c, Z, L[w], w);
         const bool acc = PRE ? (u[w] < th) : ((u[w] < th) | (th == 0xFFFFFFFFu));
         F |= acc ? (0xFEu << (8 * w)) : 0u;
         flipbits |= acc ? (1u << (2 * w)) : 0u;
         sumL += acc ? L[w] : 0;
     }
-    nflip += __popc(F & 0x02020202u);
-    sumC = __dp4a((int)(Z & (F >> 1)), 0x01010101, sumC);
+    const uint32_t Fm = F & 0x02020202u;
+    nflip2 = __dp4a((int)Fm, 0x01010101, nflip2);
+    sumC2 = __dp4a((int)Z, (int)Fm, sumC2);
     if (flipbits) bp[row + ug] = (uint8_t)(own ^ (flipbits << par));
 }
 

@@ -475,7 +475,7 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     // multiple of 2^lg: the thread then walks items q = base + (tid >> lg) + k (NC >> lg)
     const bool g_fixed = (NC & gmask) == 0;
     const int g_own = tid & gmask, q_lane = tid >> lg, q_step = NC >> lg;
-    int sumL = 0, sumC = 0, nf = 0;
+    int sumL = 0, sumC = 0, nf = 0;  // sumC and nf count twice (see unit_commit)
     SwapSide side;  // thread 0
     side.active = 0;
 
@@ -516,8 +516,8 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
                 if (PRE) named_barrier(1, NC); else __syncthreads();
             }
             const int dE = __reduce_add_sync(0xFFFFFFFFu, -2 * sumL);
-            const int dM = __reduce_add_sync(0xFFFFFFFFu, -4 * (sumC - nf));
-            const int dF = __reduce_add_sync(0xFFFFFFFFu, nf);
+            const int dM = __reduce_add_sync(0xFFFFFFFFu, -2 * (sumC - nf));  // both counted twice
+            const int dF = __reduce_add_sync(0xFFFFFFFFu, nf) >> 1;
             if (lane == 0) {
                 s_red[warp * 3 + 0] = dE;
                 s_red[warp * 3 + 1] = dM;
