@@ -87,8 +87,10 @@ size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass) {
 
 
 // ------------------------------------------------------------------------- end of a sweep
-__device__ __forceinline__ unsigned long long mbox_tag(long long q) {
-    return (unsigned long long)(q % kTagPeriod) + 1ull;
+// Tag of pass q0 + pass, from qmod0 = q0 mod kTagPeriod (taken once per launch): a 32-bit
+// remainder by a constant instead of a 64-bit one on the path to the partner.
+__device__ __forceinline__ unsigned long long mbox_tag(uint32_t qmod0, int pass) {
+    return (unsigned long long)((qmod0 + (uint32_t)pass) % (uint32_t)kTagPeriod) + 1ull;
 }
 
 // A chain's side of the swap pass that follows a sweep: rl is the lower rung of its pair,
@@ -102,11 +104,39 @@ struct SwapSide {
 // Thread 0 of a chain's CTA, after the sweep's changes are reduced: update E and M, add the
 // statistics of the rung the chain sits on (to `acc`, shared or global) and, when a swap
 // pass follows this sweep, publish (E, M) in the pass's mailbox. Does not wait.
-__device__ SwapSide eos_publish(const DevProblem& p, unsigned long long* acc, int rung, long long& E, long long& M,
-                                long long dE, long long dM, long long nflip, int s, long long q0,
-                                int sweeps_per_swap) {
+// pass >= 0: a swap pass with this index (within the launch) follows the sweep.
+__device__ SwapSide eos_publish(const DevProblem& p, int rung, long long& E, long long& M, long long dE,
+                                long long dM, int pass, long long q0, uint32_t qmod0) {
     E += dE;
     M += dM;
+    SwapSide w;
+    w.active = 0;
+    if (pass >= 0) {
+        const int R = p.R;
+        w.pass = pass;
+        w.q = q0 + w.pass;
+        w.tag = mbox_tag(qmod0, w.pass);
+        Mailbox* mb = p.mbox + (size_t)w.pass * R;
+        if (rung != p.withhold_rung) {
+            st_relaxed_u64(&mb[rung].a, ((unsigned long long)E << 24) | w.tag);
+            st_relaxed_u64(&mb[rung].b, ((unsigned long long)(uint32_t)(int32_t)M << 32) | w.tag);
+        }
+        if ((rung & 1) == (int)(w.q & 1)) {
+            w.rl = rung;
+            w.partner = rung + 1;
+        } else {
+            w.rl = rung - 1;
+            w.partner = rung - 1;
+        }
+        w.active = (w.rl >= 0 && w.rl + 1 < R) ? 1 : 0;
+    }
+    return w;
+}
+
+// Thread 0: the statistics of the rung the chain sat on during the sweep (to `acc`, shared or
+// global), from the updated E and M.
+__device__ __forceinline__ void eos_stats(const DevProblem& p, unsigned long long* acc, int rung, long long E,
+                                          long long M, long long nflip) {
     unsigned long long* a = acc + (size_t)rung * kAccCount;
     if (p.acc_in_smem) {
         a[kAccN] += 1ull;
@@ -123,27 +153,6 @@ __device__ SwapSide eos_publish(const DevProblem& p, unsigned long long* acc, in
         atomicAdd(a + kAccM2, (unsigned long long)(M * M));
         atomicAdd(a + kAccFlip, (unsigned long long)nflip);
     }
-    SwapSide w;
-    w.active = 0;
-    if (sweeps_per_swap <= 0 || (s + 1) % sweeps_per_swap != 0) return w;
-    const int R = p.R;
-    w.pass = (s + 1) / sweeps_per_swap - 1;
-    w.q = q0 + w.pass;
-    w.tag = mbox_tag(w.q);
-    Mailbox* mb = p.mbox + (size_t)w.pass * R;
-    if (rung != p.withhold_rung) {
-        st_relaxed_u64(&mb[rung].a, ((unsigned long long)E << 24) | w.tag);
-        st_relaxed_u64(&mb[rung].b, ((unsigned long long)(uint32_t)(int32_t)M << 32) | w.tag);
-    }
-    if ((rung & 1) == (int)(w.q & 1)) {
-        w.rl = rung;
-        w.partner = rung + 1;
-    } else {
-        w.rl = rung - 1;
-        w.partner = rung - 1;
-    }
-    w.active = (w.rl >= 0 && w.rl + 1 < R) ? 1 : 0;
-    return w;
 }
 
 // Thread 0 again: wait for the partner's mailbox (bounded by timeout_ns) and take the
@@ -187,7 +196,9 @@ __device__ int eos_decide(const DevProblem& p, const SwapSide& w, int rung, long
 __device__ int end_of_sweep(const DevProblem& p, unsigned long long* acc, int rung, long long& E, long long& M,
                             long long dE, long long dM, long long nflip, int s, long long q0, int sweeps_per_swap,
                             long long timeout_ns, const PhiloxKey& key, int* abort) {
-    const SwapSide w = eos_publish(p, acc, rung, E, M, dE, dM, nflip, s, q0, sweeps_per_swap);
+    const int pass = (sweeps_per_swap > 0 && (s + 1) % sweeps_per_swap == 0) ? (s + 1) / sweeps_per_swap - 1 : -1;
+    const SwapSide w = eos_publish(p, rung, E, M, dE, dM, pass, q0, (uint32_t)(q0 % kTagPeriod));
+    eos_stats(p, acc, rung, E, M, nflip);
     return eos_decide(p, w, rung, E, M, timeout_ns, key, abort);
 }
 
@@ -457,6 +468,8 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     if (tid == 0) {
         s_ctl[4] = -1;  // partner rung of the pending swap pass
         s_ctl[5] = 0;   // a swap wait gave up
+        int* s_sum = reinterpret_cast<int*>(s_red);
+        s_sum[0] = s_sum[1] = s_sum[2] = 0;  // the sweep's dE, dM and flips
     }
     __syncthreads();
     if (PRE && !consumer)
@@ -478,6 +491,8 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     int sumL = 0, sumC = 0, nf = 0;  // sumC and nf count twice (see unit_commit)
     SwapSide side;  // thread 0
     side.active = 0;
+    const uint32_t qmod0 = (uint32_t)(q0 % kTagPeriod);
+    int since_pass = 0, next_pass = 0, sweep_flips = 0;  // thread 0
 
     for (int s = 0; s < n_sweeps; ++s) {
         const uint32_t t = (uint32_t)(t0 + s);
@@ -515,26 +530,30 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
                 }
                 if (PRE) named_barrier(1, NC); else __syncthreads();
             }
+            // a chain's per-sweep changes fit in 32 bits: each warp adds its sums to three
+            // shared counters, which thread 0 reads and clears
             const int dE = __reduce_add_sync(0xFFFFFFFFu, -2 * sumL);
             const int dM = __reduce_add_sync(0xFFFFFFFFu, -2 * (sumC - nf));  // both counted twice
             const int dF = __reduce_add_sync(0xFFFFFFFFu, nf) >> 1;
+            int* s_sum = reinterpret_cast<int*>(s_red);
             if (lane == 0) {
-                s_red[warp * 3 + 0] = dE;
-                s_red[warp * 3 + 1] = dM;
-                s_red[warp * 3 + 2] = dF;
+                atomicAdd(s_sum + 0, dE);
+                atomicAdd(s_sum + 1, dM);
+                atomicAdd(s_sum + 2, dF);
             }
             if (PRE) named_barrier(1, NC); else __syncthreads();
-            if (warp == 0) {
-                // one partial per consumer warp; a chain's per-sweep changes fit in 32 bits
-                const bool has = lane < (NC >> 5);
-                const int sE = __reduce_add_sync(0xFFFFFFFFu, has ? (int)s_red[lane * 3 + 0] : 0);
-                const int sM = __reduce_add_sync(0xFFFFFFFFu, has ? (int)s_red[lane * 3 + 1] : 0);
-                const int sF = __reduce_add_sync(0xFFFFFFFFu, has ? (int)s_red[lane * 3 + 2] : 0);
-                if (lane == 0) {
-                    side = eos_publish(p, p.acc_in_smem ? s_acc : p.acc, rung, E, M, sE, sM, sF, s, q0,
-                                       sweeps_per_swap);
-                    s_ctl[4] = side.active ? side.partner : -1;
+            if (tid == 0) {
+                const int sE = s_sum[0], sM = s_sum[1];
+                sweep_flips = s_sum[2];
+                s_sum[0] = s_sum[1] = s_sum[2] = 0;
+                // a swap pass follows every sweeps_per_swap-th sweep (counted, not divided)
+                int pass = -1;
+                if (sweeps_per_swap > 0 && ++since_pass == sweeps_per_swap) {
+                    since_pass = 0;
+                    pass = next_pass++;
                 }
+                side = eos_publish(p, rung, E, M, sE, sM, pass, q0, qmod0);
+                s_ctl[4] = side.active ? side.partner : -1;
             }
         } else if (s + 1 < n_sweeps) {
             produce_words(rbuf + (size_t)((s + 1) & 1) * n_items * G, t + 1u, s_items, n_items, G, lg, gmask,
@@ -570,6 +589,9 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
             }
         }
         if (tid == 0) {
+            // the statistics of sweep s (rung unchanged until the decision below), while
+            // the partner's mailbox may still be on its way
+            eos_stats(p, p.acc_in_smem ? s_acc : p.acc, rung, E, M, sweep_flips);
             int abort_flag = 0;
             s_ctl[2 * (s & 1)] = eos_decide(p, side, rung, E, M, timeout_ns, key, &abort_flag);
             if (abort_flag) s_ctl[5] = 1;  // a partner never arrived
