@@ -62,8 +62,8 @@ size_t batch_smem_bytes(const BatchInstance& I, int cluster, int threads) {
 }
 
 template <int DC>
-__device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::cluster_group& cluster, int rank,
-                            int K) {
+__device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* s_keys, cg::cluster_group& cluster,
+                            int rank, int K) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const BatchLayout L(I, K, nt);
     uint32_t* s_sdesc = reinterpret_cast<uint32_t*>(smem + L.sdesc);
@@ -84,8 +84,10 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
     const int gsize = I.group_threads, ngroups = L.ngroups;
     const int grp = tid / gsize, gtid = tid - grp * gsize;
 
-    // ---- the problem's schedule, descriptors and rung permutation; this CTA's chains
+    // ---- the problem's schedule, descriptors, round keys and rung permutation; this CTA's chains
     {
+        if (tid < 10)
+            s_keys[tid] = make_uint2(I.key0 + (uint32_t)tid * 0x9E3779B9u, I.key1 + (uint32_t)tid * 0xBB67AE85u);
         const int4* src = reinterpret_cast<const int4*>(I.sdesc);
         int4* dst = reinterpret_cast<int4*>(s_sdesc);
         for (int x = tid; x < N * L.DW / 4; x += nt) dst[x] = src[x];
@@ -112,7 +114,8 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
     }
     __syncthreads();
 
-    const PhiloxKey key = philox_schedule(I.key0, I.key1);
+    const PhiloxKey key = philox_schedule(I.key0, I.key1);  // swap decisions
+    const PhiloxKeyShared skey{s_keys};                     // update units: round keys in shared memory
     const int G = P >> 3;
     const uint32_t ginv = chunk_ginv(G);
     int lg = 0;
@@ -144,7 +147,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
                         const int end = s_loff[lev + 1];
                         for (int q = base + q_lane; q < end; q += q_step)
                             packed_unit<DC, false>(buf, s_sdesc, s_items[q], nullptr, q, g_own, G, P, t,
-                                                   (uint32_t)rho, key, thr_c, sumL, sumC, nf);
+                                                   (uint32_t)rho, skey, thr_c, sumL, sumC, nf);
                     }
                 } else {
                     const int units = (s_loff[lev + 1] - base) << lg;
@@ -152,7 +155,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
                         const int g = u & gmask;
                         if (g >= G) continue;
                         const int q = base + (u >> lg);
-                        packed_unit<DC, false>(buf, s_sdesc, s_items[q], nullptr, q, g, G, P, t, (uint32_t)rho, key,
+                        packed_unit<DC, false>(buf, s_sdesc, s_items[q], nullptr, q, g, G, P, t, (uint32_t)rho, skey,
                                                thr_c, sumL, sumC, nf);
                     }
                 }
@@ -238,6 +241,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, cg::clu
 __global__ void __launch_bounds__(512, 1) batch_kernel(BatchParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_job;
+    __shared__ uint2 s_keys[10];
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int K = (int)cluster.num_blocks();
@@ -249,9 +253,9 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchParams bp) {
         if (job >= bp.count) break;
         const BatchInstance I = bp.inst[bp.order[job]];
         if (I.dc == 4)
-            run_problem<4>(I, smem, cluster, rank, K);
+            run_problem<4>(I, smem, s_keys, cluster, rank, K);
         else
-            run_problem<8>(I, smem, cluster, rank, K);
+            run_problem<8>(I, smem, s_keys, cluster, rank, K);
         cluster.sync();  // peers are done reading this CTA's published (E, M)
         if (rank == 0 && threadIdx.x == 0) {
             // a finished problem's counters advance on the device, so the same launch can be

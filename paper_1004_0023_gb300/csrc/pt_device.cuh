@@ -17,6 +17,16 @@ namespace ptq {
 struct PhiloxKey {
     uint32_t k0[10];
     uint32_t k1[10];
+    __device__ __forceinline__ uint32_t a(int r) const { return k0[r]; }
+    __device__ __forceinline__ uint32_t b(int r) const { return k1[r]; }
+};
+
+// The same round keys read from shared memory ((k0, k1) of round r at k[r]), for kernels
+// that cannot spare 20 registers per thread for them.
+struct PhiloxKeyShared {
+    const uint2* k;
+    __device__ __forceinline__ uint32_t a(int r) const { return k[r].x; }
+    __device__ __forceinline__ uint32_t b(int r) const { return k[r].y; }
 };
 
 __device__ __forceinline__ PhiloxKey philox_schedule(uint32_t key0, uint32_t key1) {
@@ -29,13 +39,14 @@ __device__ __forceinline__ PhiloxKey philox_schedule(uint32_t key0, uint32_t key
     return k;
 }
 
-__device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKey& k) {
+template <typename Key>
+__device__ __forceinline__ uint4 philox(uint4 c, const Key& k) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
         const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.k0[r], (uint32_t)p1,
-                       (uint32_t)(p0 >> 32) ^ c.w ^ k.k1[r], (uint32_t)p0);
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.a(r), (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ k.b(r), (uint32_t)p0);
     }
     return c;
 }
@@ -266,10 +277,10 @@ struct UnitEval {
     uint32_t u[4];  // random words
 };
 
-template <int DC, bool PRE>
+template <int DC, bool PRE, typename Key = PhiloxKey>
 __device__ __forceinline__ UnitEval packed_unit_eval(int8_t* sp, const uint32_t* s_sdesc, uint32_t item,
                                                      const uint4* rb, int q, int g, int G, int P, uint32_t t,
-                                                     uint32_t slot, const PhiloxKey& key) {
+                                                     uint32_t slot, const Key& key) {
     UnitEval e;
     const uint32_t par = item & 1u;
     const uint32_t* desc = s_sdesc + (item >> 1) * SiteDesc<DC>::DW;
@@ -355,12 +366,12 @@ __device__ __forceinline__ void unit_commit(const UnitEval& e, uint32_t F, int& 
     if (F) *e.own = e.S ^ F;
 }
 
-template <int DC, bool PRE>
+template <int DC, bool PRE, typename Key = PhiloxKey>
 __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc, uint32_t item, const uint4* rb,
                                             int q, int g, int G, int P, uint32_t t, uint32_t slot,
-                                            const PhiloxKey& key, const uint32_t* thr_c, int& sumL, int& sumC2,
+                                            const Key& key, const uint32_t* thr_c, int& sumL, int& sumC2,
                                             int& nflip2) {
-    const UnitEval e = packed_unit_eval<DC, PRE>(sp, s_sdesc, item, rb, q, g, G, P, t, slot, key);
+    const UnitEval e = packed_unit_eval<DC, PRE, Key>(sp, s_sdesc, item, rb, q, g, G, P, t, slot, key);
     // flips and sums in one pass (the acceptance predicate feeds both)
     uint32_t F = 0;
 #pragma unroll
