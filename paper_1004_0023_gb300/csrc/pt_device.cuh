@@ -187,13 +187,28 @@ __device__ __forceinline__ void load_split(int8_t* dst, const int8_t* src, int N
                                            int tid0, int nthr) {
     const uint2* s2 = reinterpret_cast<const uint2*>(src);
     const int half = P >> 1;
-    for (int x = tid0; x < N * G; x += nthr) {
-        const int g = chunk_of_row(x, G, ginv);
-        const int row = 8 * x - 8 * g;  // i * P
-        uint32_t ev, od;
-        split_chunk(s2[x], ev, od);
-        *reinterpret_cast<uint32_t*>(dst + row + 4 * g) = ev;
-        *reinterpret_cast<uint32_t*>(dst + row + half + 4 * g) = od;
+    const int n = N * G;
+    // eight loads in flight per thread before any shared store (the stores could alias the
+    // loads as far as the compiler knows, which would otherwise serialise every load)
+    for (int x0 = tid0; x0 < n; x0 += 8 * nthr) {
+        uint2 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int x = x0 + k * nthr;
+            v[k] = x < n ? s2[x] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int x = x0 + k * nthr;
+            if (x < n) {
+                const int g = chunk_of_row(x, G, ginv);
+                const int row = 8 * x - 8 * g;  // i * P
+                uint32_t ev, od;
+                split_chunk(v[k], ev, od);
+                *reinterpret_cast<uint32_t*>(dst + row + 4 * g) = ev;
+                *reinterpret_cast<uint32_t*>(dst + row + half + 4 * g) = od;
+            }
+        }
     }
 }
 __device__ __forceinline__ void store_split(int8_t* dst, const int8_t* src, int N, int P, int G, uint32_t ginv,

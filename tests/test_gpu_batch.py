@@ -140,3 +140,37 @@ def test_batch_rejects_unsupported_requests():
     with pytest.raises(pt.PTError) as e:
         pt.Batch([odd_p])
     assert e.value.code == pt.PT_EINVAL
+
+
+def _energy_and_trotter(prob, state):
+    """E (summed over copies) and M of every rung of a rung-ordered state, recomputed."""
+    s = state.astype(np.int64)  # [R, N, P]
+    E = np.einsum("rep,e->r", s[:, prob.ei, :] * s[:, prob.ej, :], np.asarray(prob.J, np.int64))
+    E += np.einsum("rip,i->r", s, np.asarray(prob.h, np.int64))
+    M = (s * np.roll(s, -1, axis=2)).sum(axis=(1, 2))
+    return E, M
+
+
+def test_full_batched_workload_sampled_requests_and_invariants():
+    """The bench's batched workload at full size and launch configuration (512 requests of
+    the size mix, 1000 sweeps each, autotuned layout, graph replay): the smallest, a median
+    and the largest request against the oracle bit for bit, and for every request E and M
+    recomputed from its final state equal the accumulated values and the counters add up."""
+    probs = instances.batch_problems(count=512, index=1, n_sweeps=1000)
+    b = pt.Batch(probs)
+    b.run()
+    b.sync()
+    work = [p.attempts_per_sweep * p.n_sweeps for p in probs]
+    order = np.argsort(work, kind="stable")
+    for k in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        o = Oracle.from_problem(probs[k], threads=THREADS)
+        o.run(probs[k].n_sweeps, probs[k].sweeps_per_swap)
+        _same(b.read_state(k), b.obs(k), o.read_state(), o.obs(), "request %d" % k)
+    for k, p in enumerate(probs):
+        ob = b.obs(k)
+        E, M = _energy_and_trotter(p, b.read_state(k))
+        assert np.array_equal(E, np.asarray(ob["E"])) and np.array_equal(M, np.asarray(ob["M"])), k
+        assert ob["t"] == p.n_sweeps and ob["q"] == p.n_sweeps // p.sweeps_per_swap, k
+        assert np.all(np.asarray(ob["n_meas"]) == p.n_sweeps), k
+        assert np.all(np.asarray(ob["swap_acc"]) <= np.asarray(ob["swap_att"])), k
+        assert sorted(np.asarray(ob["replica_at"]).tolist()) == list(range(p.R)), k
