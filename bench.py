@@ -47,7 +47,7 @@ KERNEL_NAMES = {1: "sweep_kernel (byte-wise)", 2: "sweep_packed_kernel (int8, in
 # DRAM bytes (read + write) per launch of the sweep kernel, from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum: (workload, kernel path, sweeps per launch)
 # -> bytes. Must be retaken (or removed) whenever that kernel changes.
-MEASURED_TRAFFIC = {("regular3_n256_p64_r64", 3, 1000): 1990528}
+MEASURED_TRAFFIC = {("regular3_n256_p64_r64", 3, 1000): 1637248}
 
 
 def parse_args(argv=None):
