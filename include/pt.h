@@ -59,7 +59,8 @@ typedef struct {
     const int32_t* h;
 } pt_instance;
 
-/* One rung of the ladder: temperature T > 0 and transverse field gamma > 0. */
+/* One rung of the ladder: temperature T > 0 and transverse field gamma > 0 (gamma = 0 for
+ * classical parallel tempering, P = 1). */
 typedef struct {
     double T;
     double gamma;
@@ -122,7 +123,10 @@ typedef struct {
 /* Create a PT-QMC problem on the current CUDA device (Sec. 2: chains and temperatures
  * are fixed before the run, Sec. 5 / Fig. 6: data moved to the device once).
  *   inst        Ising instance (copied).
- *   P           Trotter copies, even, 2 <= P <= 4096.
+ *   P           Trotter copies, even, 2 <= P <= 4096; or P = 1 with gamma = 0 on every rung:
+ *               classical parallel tempering over the temperatures (one copy per chain,
+ *               no Trotter coupling: K = 0, m = 0, M = N). Classical chains run on the
+ *               byte-wise kernel; batched launches and the server need P % 8 == 0.
  *   ladder, R   R >= 1 rungs (copied), 1 <= R <= 65535.
  *   flip_thr    NULL to build the Metropolis table in FP64 on the host, or R*(2*Lmax+1)*3
  *               uint32 thresholds [r][L+Lmax][m/2+1] (accept iff thr == 0xFFFFFFFF or
@@ -301,7 +305,7 @@ const char* pt_server_last_error(const pt_server* s);
 #define PT_NOALLOC_MAILBOXES 16384  /* swap passes x rungs one launch can hold */
 
 typedef struct {
-    int32_t n, P, R;            /* sites, Trotter copies (even), rungs (R <= PT_NOALLOC_MAILBOXES) */
+    int32_t n, P, R;            /* sites, Trotter copies (even, or 1: classical), rungs (R <= PT_NOALLOC_MAILBOXES) */
     int32_t lmax;               /* max_i(|h_i| + sum_j |J_ij|) <= 127 */
     int32_t row_stride;         /* entries per row of nbr: 4, 8 or 32, >= the largest degree */
     int32_t n_levels;           /* level count returned by pt_make_schedule */

@@ -163,7 +163,8 @@ static void build_tables(orc* o, const double* T, const double* gamma) {
     for (int32_t r = 0; r < o->R; r++) {
         double beta = 1.0 / T[r];
         double a = beta * gamma[r] / (double)o->P;
-        K[r] = -0.5 * log(tanh(a));
+        /* classical (P = 1): no Trotter coupling */
+        K[r] = o->P == 1 ? 0.0 : -0.5 * log(tanh(a));
         b[r] = beta / (double)o->P;
         double c1 = 2.0 * beta / (double)o->P;
         double c2 = 2.0 * K[r];
@@ -197,8 +198,8 @@ orc* orc_create(int32_t n, int32_t n_edges, const int32_t* ei, const int32_t* ej
                 const int32_t* J, const int32_t* h, int32_t P, int32_t R,
                 const double* T, const double* gamma, const uint32_t* flip_thr,
                 const double* swap_coef, uint64_t seed) {
-    if (n < 1 || n_edges < 0 || P < 2 || (P & 1) || R < 1) {
-        set_err("need n >= 1, n_edges >= 0, even P >= 2, R >= 1");
+    if (n < 1 || n_edges < 0 || (P != 1 && (P < 2 || (P & 1))) || R < 1) {
+        set_err("need n >= 1, n_edges >= 0, P = 1 or even P >= 2, R >= 1");
         return NULL;
     }
     for (int32_t b = 0; b < n_edges; b++) {
@@ -212,10 +213,12 @@ orc* orc_create(int32_t n, int32_t n_edges, const int32_t* ei, const int32_t* ej
                 return NULL;
             }
     }
+    /* P >= 2: the Suzuki-Trotter chain of the transverse-field problem, Gamma > 0 (K finite).
+     * P = 1: classical parallel tempering over T, Gamma = 0 (one copy, no Trotter coupling). */
     if (!flip_thr || !swap_coef)
         for (int32_t r = 0; r < R; r++)
-            if (!(T[r] > 0.0) || !(gamma[r] > 0.0)) {
-                set_err("T and Gamma must be positive");
+            if (!(T[r] > 0.0) || (P == 1 ? !(gamma[r] == 0.0) : !(gamma[r] > 0.0))) {
+                set_err("T must be positive; Gamma positive for P >= 2 and zero for P = 1");
                 return NULL;
             }
 
@@ -349,7 +352,9 @@ static void sweep_chain(orc* o, int32_t rep, int64_t t, int64_t* flips_out) {
                 for (int32_t a = o->adj_off[i]; a < o->adj_off[i + 1]; a++)
                     field += o->adj_J[a] * *spin_ptr(o, rep, o->adj_j[a], k);
                 int32_t L = si * field;
-                int32_t m = si * (*spin_ptr(o, rep, i, (k + P - 1) % P) + *spin_ptr(o, rep, i, (k + 1) % P));
+                /* the lone copy of a classical chain (P = 1) has no Trotter neighbours */
+                int32_t m = P == 1 ? 0
+                                   : si * (*spin_ptr(o, rep, i, (k + P - 1) % P) + *spin_ptr(o, rep, i, (k + 1) % P));
                 uint32_t th = thr[(size_t)(L + o->Lmax) * 3 + (size_t)(m / 2 + 1)];
                 if (th == 0xFFFFFFFFu || u[hh & 3] < th) {
                     *spin_ptr(o, rep, i, k) = (int8_t)(-si);

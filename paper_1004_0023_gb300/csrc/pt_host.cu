@@ -68,6 +68,7 @@ static int create_fail(int code, const char* fmt, ...) {
 // min(floor(exp(x)*2^32), 0xFFFFFFFF); for swaps a_r = beta_r/P - beta_{r+1}/P and
 // c_r = K_{r+1} - K_r. Flipping copy k of site i changes the action S by
 // -(2 beta/P) L + 2 K m, with L = s(h + sum J s_j) and m = s(s^{k-1} + s^{k+1}).
+// P = 1 is classical parallel tempering over T (Gamma = 0): K = 0 and m = 0.
 void ptq::build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vector<uint32_t>& thr,
                          std::vector<double>& coef) {
     const int nL = 2 * Lmax + 1;
@@ -77,7 +78,7 @@ void ptq::build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vecto
     for (int r = 0; r < R; ++r) {
         const double beta = 1.0 / ladder[r].T;
         const double a = beta * ladder[r].gamma / (double)P;
-        K[r] = -0.5 * log(tanh(a));
+        K[r] = P == 1 ? 0.0 : -0.5 * log(tanh(a));  // classical chains (P = 1): no Trotter coupling
         b[r] = beta / (double)P;
         const double c_flip = 2.0 * beta / (double)P;
         const double c_trot = 2.0 * K[r];
@@ -210,14 +211,17 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     if (N < 1 || N > 65535) return create_fail(PT_EINVAL, "n must be in [1, 65535]");
     if (nE < 0 || (nE > 0 && (!inst->ei || !inst->ej || !inst->J)) || !inst->h)
         return create_fail(PT_EINVAL, "bad edge arrays");
-    if (P < 2 || (P & 1) || P > 4096) return create_fail(PT_EINVAL, "P must be even and in [2, 4096]");
+    if (P != 1 && (P < 2 || (P & 1) || P > 4096))
+        return create_fail(PT_EINVAL, "P must be 1 (classical) or even and in [2, 4096]");
     if (R < 1 || R > 65535) return create_fail(PT_EINVAL, "R must be in [1, 65535]");
     const bool need_ladder = !flip_thr || !swap_coef;
     if (need_ladder)
-        for (int r = 0; r < R; ++r)
-            if (!(ladder[r].T > 0.0) || !(ladder[r].gamma > 0.0) || !isfinite(ladder[r].T) ||
-                !isfinite(ladder[r].gamma))
-                return create_fail(PT_EINVAL, "rung %d: T and gamma must be finite and > 0", r);
+        for (int r = 0; r < R; ++r) {
+            const bool gamma_ok = P == 1 ? ladder[r].gamma == 0.0 : ladder[r].gamma > 0.0;
+            if (!(ladder[r].T > 0.0) || !gamma_ok || !isfinite(ladder[r].T) || !isfinite(ladder[r].gamma))
+                return create_fail(PT_EINVAL, "rung %d: T must be finite and > 0; gamma > 0 for P >= 2, 0 for P = 1",
+                                   r);
+        }
 
     // adjacency, duplicate / self-loop checks
     std::vector<std::vector<int>> adj(N);
@@ -683,9 +687,10 @@ extern "C" int pt_get_info(const pt_ctx* c, pt_info* o) {
 
 extern "C" int pt_make_tables(int32_t P, const pt_rung* ladder, int32_t R, int32_t lmax, uint32_t* thr,
                               double* coef) {
-    if (!ladder || P < 2 || (P & 1) || R < 1 || lmax < 0 || lmax > 127) return PT_EINVAL;
+    if (!ladder || (P != 1 && (P < 2 || (P & 1))) || R < 1 || lmax < 0 || lmax > 127) return PT_EINVAL;
     for (int r = 0; r < R; ++r)
-        if (!(ladder[r].T > 0.0) || !(ladder[r].gamma > 0.0)) return PT_EINVAL;
+        if (!(ladder[r].T > 0.0) || (P == 1 ? !(ladder[r].gamma == 0.0) : !(ladder[r].gamma > 0.0)))
+            return PT_EINVAL;
     std::vector<uint32_t> t;
     std::vector<double> c;
     build_tables(R, P, lmax, ladder, t, c);

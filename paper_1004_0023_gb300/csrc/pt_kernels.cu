@@ -263,8 +263,7 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
     const uint32_t* thr = thr_row(p, s_thr, rung);
 
     const PhiloxKey key = philox_schedule(p.key0, p.key1);
-    const int half = P >> 1;
-    const int G = (half + 3) >> 2;  // 4-copy groups per parity
+    const int G = (((P + 1) >> 1) + 3) >> 2;  // 4-copy groups per parity (P = 1: one even copy)
     int lg = 0;
     while ((1 << lg) < G) ++lg;
     const int gmask = (1 << lg) - 1;
@@ -290,10 +289,11 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
                 for (int d = 0; d < DCLASS; ++d) nb[d] = s_nbr[i * DCLASS + d];
                 const int hi = s_h[i];
                 int8_t* row = sp + (size_t)i * P;
+                const int n_par = (P + 1 - par) >> 1;  // copies of this parity
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
                     const int hh = 4 * g + w;
-                    if (hh < half) {
+                    if (hh < n_par) {
                         const int k = par + 2 * hh;
                         const int sk = row[k];
                         int f = hi;
@@ -306,7 +306,8 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
                         const int Lf = sk * f;
                         const int km1 = (k == 0) ? P - 1 : k - 1;
                         const int kp1 = (k + 1 == P) ? 0 : k + 1;
-                        const int m = sk * ((int)row[km1] + (int)row[kp1]);
+                        // a classical chain's lone copy (P = 1) has no Trotter neighbours
+                        const int m = P == 1 ? 0 : sk * ((int)row[km1] + (int)row[kp1]);
                         const uint32_t th = thr[(Lf + Lmax) * 3 + (m >> 1) + 1];
                         if (th == 0xFFFFFFFFu || rw[w] < th) {
                             row[k] = (int8_t)(-sk);

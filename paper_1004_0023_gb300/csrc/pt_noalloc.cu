@@ -60,7 +60,7 @@ static int mailbox_address(void** out) {
 extern "C" int pt_run_noalloc(const pt_device_problem* q, int64_t n_sweeps, int32_t sweeps_per_swap,
                               int32_t wait_timeout_ms, void* cuda_stream) {
     if (!q) return fail(PT_EINVAL, "null problem");
-    if (q->n < 1 || q->n > 65535 || q->P < 2 || (q->P & 1) || q->P > 4096 || q->R < 1 || q->R > 65535)
+    if (q->n < 1 || q->n > 65535 || (q->P != 1 && (q->P < 2 || (q->P & 1) || q->P > 4096)) || q->R < 1 || q->R > 65535)
         return fail(PT_EINVAL, "need 1 <= n <= 65535, even 2 <= P <= 4096, 1 <= R <= 65535");
     if (q->lmax < 0 || q->lmax > 127) return fail(PT_EINVAL, "lmax must be in [0, 127]");
     if (q->row_stride != 4 && q->row_stride != 8 && q->row_stride != 32)

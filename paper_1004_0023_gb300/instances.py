@@ -122,6 +122,10 @@ WORKLOADS = {
     "chimera16_n2048_p128_r96": dict(graph="chimera", rows=16, cols=16,
                                      J=(-4, -3, -2, -1, 1, 2, 3, 4), h=(0,), P=128, R=96,
                                      ladder="geometric", g0=0.05, g1=4.0, T=0.02, n_sweeps=500),
+    # classical parallel tempering (P = 1, Gamma = 0) on the N=256 graph family: R=64
+    # temperatures geometric 0.1..3.0, 2000 sweeps, one swap pass per sweep
+    "classical_regular3_n256_r64": dict(graph="regular", n=256, degree=3, J=(-2, -1, 1, 2), h=(-1, 0, 1),
+                                        P=1, R=64, ladder="temperature", g0=0.1, g1=3.0, n_sweeps=2000),
 }
 
 
@@ -138,8 +142,13 @@ def make_problem(graph: str, rng: np.random.Generator, *, n=None, degree=3, rows
         raise ValueError(graph)
     Jv = _draw(J, ei.size, rng)
     hv = _draw(h, nn, rng)
-    gam = gamma_ladder(ladder, g0, g1, int(R))
-    Tv = np.full(int(R), float(T), np.float64)
+    if ladder == "temperature":
+        # classical parallel tempering (P = 1): geometric temperatures g0..g1, Gamma = 0
+        Tv = gamma_ladder("geometric", g0, g1, int(R))
+        gam = np.zeros(int(R), np.float64)
+    else:
+        gam = gamma_ladder(ladder, g0, g1, int(R))
+        Tv = np.full(int(R), float(T), np.float64)
     return Problem(nn, ei, ej, Jv, hv, int(P), Tv, gam, int(seed), int(n_sweeps),
                    int(sweeps_per_swap), name)
 

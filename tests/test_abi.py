@@ -46,7 +46,8 @@ def test_create_without_device_fails_loudly(libpt):
     assert e.value.code in (pt.PT_ENODEV, pt.PT_ECUDA)
 
 
-@pytest.mark.parametrize("name", ["regular3_n16_p32_r16", "regular3_n256_p64_r64", "chimera16_n2048_p128_r96"])
+@pytest.mark.parametrize("name", ["regular3_n16_p32_r16", "regular3_n256_p64_r64", "chimera16_n2048_p128_r96",
+                                  "classical_regular3_n256_r64"])
 def test_host_tables_bit_identical_to_oracle(libpt, name):
     prob = instances.workload(name, 1)
     o = Oracle.from_problem(prob)
@@ -60,6 +61,10 @@ def test_host_tables_reject_bad_ladder(libpt):
         pt.make_tables(4, [1.0, 0.0], [1.0, 1.0], 3)
     with pytest.raises(pt.PTError):
         pt.make_tables(3, [1.0], [1.0], 3)
+    with pytest.raises(pt.PTError):  # classical chains (P = 1) need gamma = 0
+        pt.make_tables(1, [1.0, 2.0], [0.0, 0.5], 3)
+    with pytest.raises(pt.PTError):  # Trotter chains need gamma > 0
+        pt.make_tables(2, [1.0, 2.0], [0.0, 0.0], 3)
 
 
 def _check_schedule(n, ei, ej):

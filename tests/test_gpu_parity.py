@@ -193,6 +193,35 @@ def test_packed_row_lengths(P, path):
         assert_same(g, o, "%s P=%d after 200 more" % (graph, P))
 
 
+def test_classical_tiny_problem_every_sweep():
+    """Classical parallel tempering (P = 1, Gamma = 0, temperature ladder) on the byte-wise
+    kernel: bits after every sweep, then after 500 more with a swap every third sweep."""
+    edges = [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 0), (0, 3), (1, 4)]
+    prob = instances.tiny_problem(6, edges, [1, -2, 1, -1, 2, -1, 1, -2], [1, 0, -1, 0, 1, 0], 1,
+                                  [0.7, 1.4, 3.0], [0.0, 0.0, 0.0], seed=31)
+    g, o = both(prob)
+    assert g.info.kernel_path == 1
+    for s in range(30):
+        g.run(1, 1)
+        o.run(1, 1)
+        assert_same(g, o, "sweep %d" % (s + 1))
+    g.run(500, 3)
+    o.run(500, 3)
+    assert_same(g, o, "after 500 more")
+
+
+def test_classical_workload_full_length():
+    """Random 3-regular N=256, P=1, R=64 temperatures geometric 0.1..3.0, 2000 sweeps with a
+    swap pass after every sweep; checked every 200 sweeps."""
+    prob = instances.workload("classical_regular3_n256_r64", 1)
+    g, o = both(prob)
+    for chunk in range(prob.n_sweeps // 200):
+        g.run(200, 1)
+        o.run(200, 1)
+        assert_same(g, o, "sweep %d" % (200 * (chunk + 1)))
+    assert np.all(np.asarray(g.obs()["M"]) == prob.n)
+
+
 def test_exact_swap_rule_and_fast_pre_decision_agree_on_the_medium_workload():
     """Every swap decided by the FP32 pre-decision equals the FP64 rule (both vs the oracle)."""
     prob = instances.workload("regular3_n256_p64_r64", 5)

@@ -24,7 +24,7 @@ MUTANTS = {
     "odd_copies_first": ("int32_t k = p + 2 * hh;", "int32_t k = (1 - p) + 2 * hh;"),
     "sites_in_reverse": ("int32_t si = *spin_ptr(o, rep, i, k);", "i = o->N - 1 - i; int32_t si = *spin_ptr(o, rep, i, k); i = o->N - 1 - i;"),
     "table_sign_of_m": ("double x = c1 * (double)L - c2 * (double)m;", "double x = c1 * (double)L + c2 * (double)m;"),
-    "coupling_K_factor": ("K[r] = -0.5 * log(tanh(a));", "K[r] = -1.0 * log(tanh(a));"),
+    "coupling_K_factor": (": -0.5 * log(tanh(a));", ": -1.0 * log(tanh(a));"),
     "energy_update_uses_m": ("dE -= 2 * (int64_t)L;", "dE -= 2 * (int64_t)m;"),
     "swap_delta_sign": ("double delta = a[r] * dE + c[r] * dM;", "double delta = a[r] * dE - c[r] * dM;"),
     "swap_coef_transposed": ("o->coef[r] = b[r] - b[r + 1];", "o->coef[r] = b[r + 1] - b[r];"),
@@ -35,6 +35,8 @@ MUTANTS = {
     "philox_key_bump": ("k1 += PHILOX_W1;", "k1 += PHILOX_W0;"),
     "det_exp_short_series": ("double p = inv_fact[13];\n    for (int k = 12;", "double p = inv_fact[9];\n    for (int k = 8;"),
     "flip_word_shared": ("u[hh & 3] < th", "u[0] < th"),
+    "classical_keeps_trotter_term": ("int32_t m = P == 1 ? 0", "int32_t m = P == 0 ? 0"),
+    "classical_keeps_coupling": ("K[r] = o->P == 1 ? 0.0 :", "K[r] = o->P == 0 ? 0.0 :"),
 }
 
 
@@ -143,7 +145,28 @@ def _battery(lib):
         y = orc.det_exp(x, lib=lib)
         return (np.abs(y - np.exp(x)) / np.spacing(np.exp(x))).max() <= 2.0
 
-    for name, fn in (("greedy", greedy), ("invariants", invariants), ("moments", moments),
+    def classical():
+        edges = [(0, 1), (1, 2), (2, 3), (3, 0), (0, 2)]
+        prob = instances.tiny_problem(4, edges, [1, -2, 1, 2, -1], [1, 0, -1, 0], 1, [0.8, 2.0], [0.0, 0.0], seed=9)
+        o = orc.Oracle.from_problem(prob, lib=lib)
+        s, E = exact.slice_energies(prob.n, prob.ei, prob.ej, prob.J, prob.h)
+        rows, prev = [], o.obs()
+        for _ in range(20):
+            o.run(3000, 1)
+            cur = o.obs()
+            if not np.all(np.asarray(cur["M"]) == prob.n):
+                return False
+            rows.append((cur["sum_E"] - prev["sum_E"]) / (cur["n_meas"] - prev["n_meas"]).astype(float))
+            prev = cur
+        a = np.asarray(rows)
+        mean, se = a.mean(0), a.std(0, ddof=1) / np.sqrt(a.shape[0])
+        for r in range(prob.R):
+            w = np.exp(-(E - E.min()) / prob.T[r])
+            if abs(mean[r] - float(w @ E) / w.sum()) > 5 * se[r] + 1e-9:
+                return False
+        return True
+
+    for name, fn in (("greedy", greedy), ("invariants", invariants), ("moments", moments), ("classical", classical),
                      ("equal_rungs", equal_rungs), ("swap_frequency", swap_frequency),
                      ("philox", philox_curand), ("det_exp", det_exp_ulp)):
         check(name, fn)

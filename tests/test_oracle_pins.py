@@ -403,3 +403,61 @@ def test_create_rejects_invalid_input():
         kw = dict(good, **bad)
         with pytest.raises(ValueError):
             Oracle(**kw)
+
+
+# ----------------------------------------------------------------------------- classical PT
+# P = 1 with Gamma = 0: classical parallel tempering over T (one copy per chain, no Trotter
+# coupling). Pinned to the Boltzmann distribution exp(-beta E) enumerated over all 2^N states.
+
+def _classical_problem(seed=31):
+    edges = [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 0), (0, 3), (1, 4)]
+    return instances.tiny_problem(6, edges, [1, -2, 1, -1, 2, -1, 1, -2], [1, 0, -1, 0, 1, 0], 1,
+                                  [0.7, 1.4, 3.0], [0.0, 0.0, 0.0], seed=seed)
+
+
+def test_classical_pt_samples_the_boltzmann_distribution_at_every_temperature():
+    prob = _classical_problem()
+    s, E = exact.slice_energies(prob.n, prob.ei, prob.ej, prob.J, prob.h)
+    o = Oracle.from_problem(prob)
+    o.run(2000, 1)
+    rows, rows2 = [], []
+    prev = o.obs()
+    for _ in range(40):
+        o.run(2000, 1)
+        cur = o.obs()
+        dn = np.asarray(cur["n_meas"]) - np.asarray(prev["n_meas"])
+        rows.append((np.asarray(cur["sum_E"]) - np.asarray(prev["sum_E"])) / dn)
+        rows2.append((np.asarray(cur["sum_E2"]) - np.asarray(prev["sum_E2"])) / dn)
+        assert np.all(np.asarray(cur["M"]) == prob.n)  # one copy: M = sum_i s_i s_i
+        prev = cur
+    rows, rows2 = np.asarray(rows), np.asarray(rows2)
+    for r in range(prob.R):
+        w = np.exp(-(E - E.min()) / prob.T[r])
+        w /= w.sum()
+        for got, want in ((rows[:, r], float(w @ E)), (rows2[:, r], float(w @ E ** 2))):
+            se = got.std(ddof=1) / np.sqrt(got.size)
+            assert abs(got.mean() - want) < 5 * se + 1e-12, (r, got.mean(), want, se)
+    assert np.all(np.asarray(prev["swap_acc"]) > 0)
+
+
+def test_classical_table_ignores_the_trotter_column_and_swaps_see_only_energy():
+    prob = _classical_problem()
+    o = Oracle.from_problem(prob)
+    thr = o.flip_table().reshape(prob.R, -1, 3)
+    assert np.all(thr[:, :, 0] == thr[:, :, 1]) and np.all(thr[:, :, 1] == thr[:, :, 2])
+    coef = o.swap_coef()
+    assert np.all(coef[prob.R - 1:] == 0.0) and np.all(coef[: prob.R - 1] > 0.0)
+    # L >= 0 always flips; the least favourable move is the rarest at the coldest rung
+    lmax = (thr.shape[1] - 1) // 2
+    assert np.all(thr[:, lmax:, :] == 0xFFFFFFFF)
+    assert thr[0, 0, 0] < thr[-1, 0, 0]
+
+
+def test_classical_mode_needs_gamma_zero_and_quantum_mode_needs_gamma_positive():
+    prob = _classical_problem()
+    bad = instances.tiny_problem(6, list(zip(prob.ei, prob.ej)), prob.J, prob.h, 1, prob.T, [0.0, 0.5, 0.0])
+    with pytest.raises(Exception):
+        Oracle.from_problem(bad)
+    quantum_zero = instances.tiny_problem(6, list(zip(prob.ei, prob.ej)), prob.J, prob.h, 2, prob.T, [0.0] * 3)
+    with pytest.raises(Exception):
+        Oracle.from_problem(quantum_zero)
