@@ -170,6 +170,16 @@ int pt_write_state(pt_ctx* ctx, const int8_t* in, size_t bytes);
 /* Fill the caller's arrays with the current statistics. Synchronises. */
 int pt_read_observables(pt_ctx* ctx, pt_observables* out);
 
+/* Checkpoint restore: put a context back into the state that pt_read_state (into `in`) and
+ * pt_read_observables (into `snap`) captured from a context of the same problem and seed.
+ * The chains return to their rungs (snap->replica_at; the random streams belong to the
+ * chains), the statistics and the sweep / pass counters (snap->t, snap->q) are restored,
+ * and E and M are recomputed from the spins. The following sweeps and swaps are then
+ * bit-identical to those of the context the snapshot came from. Every array of `snap`
+ * except E and M is required. PT_EINVAL for a bad buffer or permutation, PT_EOVERFLOW
+ * for counters out of range. Synchronises. */
+int pt_restore(pt_ctx* ctx, const int8_t* in, size_t bytes, const pt_observables* snap);
+
 /* Copy the tables the context uses: thr (R*(2*Lmax+1)*3) and coef (2*(R-1)); either
  * pointer may be NULL. Host data, no synchronisation. */
 int pt_read_tables(const pt_ctx* ctx, uint32_t* thr, size_t thr_count, double* coef,

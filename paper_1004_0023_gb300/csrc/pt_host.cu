@@ -615,6 +615,59 @@ extern "C" int pt_write_state(pt_ctx* c, const int8_t* in, size_t bytes) {
     return check_status(c);
 }
 
+extern "C" int pt_restore(pt_ctx* c, const int8_t* in, size_t bytes, const pt_observables* snap) {
+    int g = guard(c);
+    if (g) return g;
+    const int R = c->dp.R;
+    const size_t need = (size_t)R * c->dp.N * c->dp.P;
+    if (!in || bytes != need) return ctx_fail(c, PT_EINVAL, "state buffer must be %zu bytes", need);
+    if (!snap || !snap->replica_at || !snap->n_meas || !snap->sum_E || !snap->sum_E2 || !snap->sum_M ||
+        !snap->sum_M2 || !snap->flip_acc || (R > 1 && (!snap->swap_att || !snap->swap_acc)))
+        return ctx_fail(c, PT_EINVAL, "the snapshot needs the permutation, every statistic and both counters");
+    for (size_t x = 0; x < need; ++x)
+        if (in[x] != 1 && in[x] != -1) return ctx_fail(c, PT_EINVAL, "spins must be +1 or -1");
+    if (snap->t < 0 || snap->t > c->sweep_limit || snap->q < 0 || snap->q > 0xFFFFFFFFll)
+        return ctx_fail(c, PT_EOVERFLOW, "snapshot counters out of range");
+    std::vector<int32_t> slot_of(R), rung_of(R, -1);
+    for (int r = 0; r < R; ++r) {
+        const int slot = snap->replica_at[r];
+        if (slot < 0 || slot >= R || rung_of[slot] >= 0) return ctx_fail(c, PT_EINVAL, "replica_at is not a permutation");
+        slot_of[r] = slot;
+        rung_of[slot] = r;
+    }
+    std::vector<unsigned long long> acc((size_t)R * kAccCount, 0ull), sw(2 * (size_t)R, 0ull);
+    for (int r = 0; r < R; ++r) {
+        unsigned long long* a = &acc[(size_t)r * kAccCount];
+        a[kAccN] = (unsigned long long)snap->n_meas[r];
+        a[kAccE] = (unsigned long long)snap->sum_E[r];
+        a[kAccE2] = (unsigned long long)snap->sum_E2[r];
+        a[kAccM] = (unsigned long long)snap->sum_M[r];
+        a[kAccM2] = (unsigned long long)snap->sum_M2[r];
+        a[kAccFlip] = (unsigned long long)snap->flip_acc[r];
+    }
+    for (int r = 0; r + 1 < R; ++r) {
+        sw[2 * r] = (unsigned long long)snap->swap_att[r];
+        sw[2 * r + 1] = (unsigned long long)snap->swap_acc[r];
+    }
+    cudaStream_t s = c->stream;
+    // the random streams belong to the chains, so each chain returns to its own slot; stale
+    // mailboxes could carry the tags of the restored passes and are cleared
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dp.slot_of_rung, slot_of.data(), R * 4, cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dp.rung_of_slot, rung_of.data(), R * 4, cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dp.acc, acc.data(), acc.size() * 8, cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->dp.swap_stats, sw.data(), sw.size() * 8, cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->staging, in, need, cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->dp.mbox, 0, (size_t)c->max_passes * R * sizeof(Mailbox), s));
+    CUDA_OR_FAIL(c, launch_scatter_state(c->dp, c->staging, s));
+    CUDA_OR_FAIL(c, launch_energy(c->dp, s));
+    c->launches += 2;
+    c->h2d_bytes += (int64_t)(need + R * 8 + acc.size() * 8 + sw.size() * 8);
+    c->t = snap->t;
+    c->q = snap->q;
+    c->mbox_clear_q = snap->q;
+    return check_status(c);
+}
+
 extern "C" int pt_read_observables(pt_ctx* c, pt_observables* o) {
     int g = guard(c);
     if (g) return g;

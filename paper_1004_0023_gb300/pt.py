@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
     lib.pt_read_state.argtypes = [_vp, _vp, _sz]
     lib.pt_write_state.argtypes = [_vp, _vp, _sz]
     lib.pt_read_observables.argtypes = [_vp, ctypes.POINTER(pt_observables)]
+    lib.pt_restore.argtypes = [_vp, _vp, _sz, ctypes.POINTER(pt_observables)]
     lib.pt_read_tables.argtypes = [_vp, _vp, _sz, _vp, _sz]
     lib.pt_get_info.argtypes = [_vp, ctypes.POINTER(pt_info)]
     lib.pt_sync.argtypes = [_vp]
@@ -273,6 +274,26 @@ class PT:
 
     def obs(self):
         return _read_obs(self.R, lambda o: self.lib.pt_read_observables(self.ctx, ctypes.byref(o)), self._check)
+
+    def checkpoint(self):
+        """(state, observables) to hand to `restore` (pt_read_state + pt_read_observables)."""
+        return self.read_state(), self.obs()
+
+    def restore(self, state, obs):
+        """pt_restore: continue bit for bit from a checkpoint of a context of the same problem."""
+        xa = np.ascontiguousarray(state, np.int8)
+        keep = {k: np.ascontiguousarray(obs[k], np.int64) for k in
+                ("E", "M", "n_meas", "sum_E", "sum_E2", "sum_M", "sum_M2", "flip_acc")}
+        att = np.zeros(max(self.R - 1, 1), np.int64)
+        acc = np.zeros(max(self.R - 1, 1), np.int64)
+        att[: self.R - 1] = obs["swap_att"]
+        acc[: self.R - 1] = obs["swap_acc"]
+        at = np.ascontiguousarray(obs["replica_at"], np.int32)
+        o = pt_observables(int(obs["t"]), int(obs["q"]),
+                           *(keep[k].ctypes.data_as(_p_i64) for k in
+                             ("E", "M", "n_meas", "sum_E", "sum_E2", "sum_M", "sum_M2", "flip_acc")),
+                           att.ctypes.data_as(_p_i64), acc.ctypes.data_as(_p_i64), at.ctypes.data_as(_p_i32))
+        self._check(self.lib.pt_restore(self.ctx, _ptr(xa), xa.nbytes, ctypes.byref(o)))
 
     def tables(self):
         info = self.info

@@ -249,6 +249,45 @@ def test_run_equals_sweep_and_swap_calls():
         assert np.array_equal(np.asarray(oa[k]), np.asarray(ob[k])), k
 
 
+def test_checkpoint_restore_continues_bit_for_bit():
+    """A checkpoint of one context restored into a fresh context of the same problem (after
+    swaps have moved the chains between rungs) continues exactly like the original; also
+    after restoring an older checkpoint into a context that ran further."""
+    prob = instances.workload("regular3_n16_p32_r16", 5)
+    a = pt.PT.from_problem(prob)
+    a.run(300, 1)
+    state, ob = a.checkpoint()
+    assert not np.array_equal(ob["replica_at"], np.arange(prob.R))  # some swaps were accepted
+    b = pt.PT.from_problem(prob)
+    b.run(1000, 1)  # further than the checkpoint: its mailboxes hold later passes
+    b.restore(state, ob)
+    assert_same(b, _Frozen(state, ob), "right after restore")
+    a.run(250, 1)
+    b.run(250, 1)
+    assert_same(b, _Frozen(*a.checkpoint()), "250 sweeps after restore")
+    o = Oracle.from_problem(prob, threads=THREADS)
+    o.run(550, 1)
+    assert_same(b, o, "vs oracle")
+    with pytest.raises(pt.PTError) as e:
+        bad = dict(ob)
+        bad["replica_at"] = np.zeros(prob.R, np.int32)
+        b.restore(state, bad)
+    assert e.value.code == pt.PT_EINVAL
+
+
+class _Frozen:
+    """A checkpoint seen through the read_state / obs interface of assert_same."""
+
+    def __init__(self, state, ob):
+        self._s, self._o = state, ob
+
+    def read_state(self):
+        return self._s
+
+    def obs(self):
+        return self._o
+
+
 def test_tables_read_back_equal_oracle():
     prob = instances.workload("regular3_n256_p64_r64", 1)
     g, o = both(prob)
