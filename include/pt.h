@@ -226,7 +226,9 @@ typedef struct {
     int64_t kernel_launches;
     int64_t h2d_bytes;
     int32_t tuned_layouts;      /* layouts the autotuner timed (0 = layout given) */
-    int32_t group_widen;        /* chosen threads-per-chain doubling (0 = default width) */
+    int32_t group_widen;        /* threads per chain: doublings (> 0) or halvings (< 0) of the
+                                   width that gives about one update unit per thread in an
+                                   average level; fixed layouts use -4 (narrowest that fits) */
     int32_t graph;              /* 1 = runs replay a captured CUDA graph */
     int32_t reserved;
 } pt_batch_info;

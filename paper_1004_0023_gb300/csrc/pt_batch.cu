@@ -61,6 +61,14 @@ size_t batch_smem_bytes(const BatchInstance& I, int cluster, int threads) {
     return BatchLayout(I, cluster, threads).total;
 }
 
+// A chain group's barrier: a named barrier of its warps, or just the warp for one-warp groups.
+__device__ __forceinline__ void group_sync(int bar, int gsize) {
+    if (gsize == 32)
+        __syncwarp();
+    else
+        named_barrier(bar, gsize);
+}
+
 template <int DC>
 __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* s_keys, cg::cluster_group& cluster,
                             int rank, int K) {
@@ -136,7 +144,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
             if (!I.resident) load_split(buf, I.spins + (size_t)rho * I.slot_stride, N, P, G, ginv, gtid, gsize);
             const int rung = s_rung[rho];
             for (int x = gtid; x < I.nL3; x += gsize) thr_g[x] = I.thr[(size_t)rung * I.nL3 + x];
-            named_barrier(bar, gsize);
+            group_sync(bar, gsize);
             const uint32_t* thr_c = thr_g + 3 * I.Lmax;
             int sumL = 0, sumC = 0, nf = 0;  // sumC and nf count twice (see unit_commit)
             for (int lev = 0; lev < I.n_levels; ++lev) {
@@ -159,7 +167,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
                                                thr_c, sumL, sumC, nf);
                     }
                 }
-                named_barrier(bar, gsize);
+                group_sync(bar, gsize);
             }
             const int dE = __reduce_add_sync(0xFFFFFFFFu, -2 * sumL);
             const int dM = __reduce_add_sync(0xFFFFFFFFu, -2 * (sumC - nf));  // both counted twice
@@ -170,7 +178,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
                 red_g[gwarp * 3 + 2] = nf;
             }
             if (!I.resident) store_split(I.spins + (size_t)rho * I.slot_stride, buf, N, P, G, ginv, gtid, gsize);
-            named_barrier(bar, gsize);
+            group_sync(bar, gsize);
             if (gtid == 0) {
                 long long sE = 0, sM = 0, sF = 0;
                 for (int w = 0; w < gsize / 32; ++w) {
@@ -189,7 +197,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
                 atomicAdd(a + kAccM2, (unsigned long long)(M * M));
                 atomicAdd(a + kAccFlip, (unsigned long long)sF);
             }
-            named_barrier(bar, gsize);
+            group_sync(bar, gsize);
         }
         __syncthreads();
         if (I.sweeps_per_swap > 0 && (s + 1) % I.sweeps_per_swap == 0) {
@@ -579,7 +587,9 @@ void ptq::fill_instance(BatchInstance& I, const Prepared& p, unsigned char* base
 void ptq::choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_cap, int widen) {
     // threads per chain: about one 4-copy unit per thread in an average level, at least two
     // warps, and no more groups than a CTA has chains; chains stay resident when they fit.
-    // widen doubles the group that many times (fewer chains at once, shorter levels).
+    // widen > 0 doubles the group that many times (fewer chains at once, shorter levels);
+    // widen < 0 halves it (more chains at once, each with more rounds per level), as long as
+    // the CTA's chain buffers still fit.
     const long long units = 2ll * I.N * (I.P / 8);
     const long long avg = (units + I.n_levels - 1) / I.n_levels;
     const int C = (I.R + cluster - 1) / cluster;
@@ -587,9 +597,16 @@ void ptq::choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_
     while (g < 512 && g < avg) g <<= 1;
     while (g < 512 && threads / g > C) g <<= 1;
     for (int w = 0; w < widen && g < 512 && g < threads; ++w) g <<= 1;
-    I.group_threads = g;
-    I.resident = 1;
-    if (batch_smem_bytes(I, cluster, threads) > smem_cap) I.resident = 0;
+    for (int w = 0; w < -widen && g > 32; ++w) g >>= 1;  // down to one warp per chain
+    while (g < threads && threads / g > C) g <<= 1;      // still no more groups than chains
+    for (;;) {
+        I.group_threads = g;
+        I.resident = 1;
+        if (batch_smem_bytes(I, cluster, threads) <= smem_cap) break;
+        I.resident = 0;
+        if (batch_smem_bytes(I, cluster, threads) <= smem_cap || g >= 512 || g >= threads) break;
+        g <<= 1;  // one streaming buffer per group: fewer, larger groups
+    }
 }
 
 // Groups per request, the CTA's shared memory and the persistent grid for one layout.
@@ -669,7 +686,7 @@ static int autotune(pt_batch* b) {
     int best_c = 0, best_w = 0, timed = 0;
     char why[200];
     for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
-        for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
+        for (int w = -4; w < 2 && e == cudaSuccess; ++w) {
             if (plan_layout(b, kClusters[ci], w, why, sizeof(why)) != PT_OK) continue;
             for (int rep = 0; rep < (timed == 0 ? 2 : 1) && e == cudaSuccess; ++rep) {  // first: one warm-up
                 for (BatchInstance& I : b->h_inst) I.t0 = I.q0 = 0;
@@ -796,8 +813,9 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
     {
         // the given layout, or (autotuning) the smallest cluster, which needs the most
         // shared memory per CTA: a request that fits nowhere is rejected before allocating
-        const int rc = plan_layout(b, fixed_cluster ? fixed_cluster : 1, 0, why, sizeof(why));
-        if (rc != PT_OK && (fixed_cluster || plan_layout(b, 8, 0, why, sizeof(why)) != PT_OK)) {
+        const int rc = plan_layout(b, fixed_cluster ? fixed_cluster : 1, kGroupWidenDefault, why, sizeof(why));
+        if (rc != PT_OK &&
+            (fixed_cluster || plan_layout(b, 8, kGroupWidenDefault, why, sizeof(why)) != PT_OK)) {
             free_batch(b);
             return bfail(nullptr, PT_EINVAL, "%s", why);
         }

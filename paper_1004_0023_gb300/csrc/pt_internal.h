@@ -153,7 +153,10 @@ struct Prepared {
 int prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len);
 size_t request_block_layout(Prepared& p, size_t mailbox_entries = 0);
 void fill_instance(BatchInstance& I, const Prepared& p, unsigned char* base, const pt_request& r);
-void choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_cap, int widen = 0);
+// Group width of a fixed layout: narrowest that fits (one warp per chain where possible),
+// which the autotuner picks on the batched size mix.
+constexpr int kGroupWidenDefault = -4;
+void choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_cap, int widen = kGroupWidenDefault);
 
 // Batched launchers (pt_batch.cu).
 size_t batch_smem_bytes(const BatchInstance& I, int cluster, int threads);
