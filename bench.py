@@ -48,6 +48,8 @@ KERNEL_NAMES = {1: "sweep_kernel (byte-wise)", 2: "sweep_packed_kernel (int8, in
 # dram__bytes_read.sum + dram__bytes_write.sum: (workload, kernel path, sweeps per launch)
 # -> bytes. Must be retaken (or removed) whenever that kernel changes.
 MEASURED_TRAFFIC = {("regular3_n256_p64_r64", 3, 1000): 1637248}
+# The same for the batched launch: (requests, sweeps each) -> DRAM bytes per launch.
+MEASURED_BATCH_TRAFFIC = {(512, 1000): 1297127729664 + 1345044210688}
 
 
 def parse_args(argv=None):
@@ -325,7 +327,9 @@ def run_batched(args, pt, instances, torch, n_sm, sm_max):
             "group_widen": info.group_widen, "autotuned_layouts": info.tuned_layouts,
             "create_and_autotune_s": create_s, "graph_replay": bool(b_graph),
             "roofline": {"bound": "alu", "achieved": ialg * value / 1e12, "peak": peak, "unit": "Tinstr/s",
-                         "frac": ialg * value / 1e12 / peak, "kernel": "batch_kernel"}}
+                         "frac": ialg * value / 1e12 / peak, "kernel": "batch_kernel",
+                         "traffic": MEASURED_BATCH_TRAFFIC.get((args.batch_count, args.batch_sweeps)),
+                         "traffic_unit": "DRAM bytes per launch (ncu)"}}
 
 
 def run_serving(args, torch, batched):
