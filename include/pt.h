@@ -78,9 +78,12 @@ typedef struct {
     int32_t kernel_path;        /* 0 = auto, 1 = byte-wise, 2 = packed with inline random
                                    words, 3 = packed with random words produced one sweep
                                    ahead by dedicated warps, 4 = packed with one bit per
-                                   copy in shared memory (paths 2-4 need P % 8 == 0 and
-                                   degree <= 7) */
-    int32_t producer_threads;   /* path 3: threads producing random words (0 = auto) */
+                                   copy in shared memory (paths 2-5 need P % 8 == 0 and
+                                   degree <= 7), 5 = path 3 with each chain split over a
+                                   cluster of two CTAs, one half of the Trotter copies each
+                                   (needs P % 16 == 0 and all R chains resident at once;
+                                   for short ladders that leave SMs idle) */
+    int32_t producer_threads;   /* paths 3 and 5: threads producing random words (0 = auto) */
     int32_t test_exact_swaps;   /* test hook: 1 = skip the FP32 pre-decision of swaps and always
                                    evaluate the FP64 rule (results are identical either way) */
     int32_t cluster_size;       /* batched launches: CTAs per thread-block cluster (1..16), or

@@ -156,6 +156,13 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 // ------------------------------------------------------------------------- misc
 __host__ __device__ inline size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Every thread of every CTA of the cluster: release this CTA's shared-memory writes (own and
+// remote) and acquire the others'. The non-.aligned form, so threads of a warp may arrive
+// from different branches.
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
 __device__ __forceinline__ void named_barrier(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
@@ -388,6 +395,82 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc,
                                             int& nflip2) {
     const UnitEval e = packed_unit_eval<DC, PRE, Key>(sp, s_sdesc, item, rb, q, g, G, P, t, slot, key);
     // flips and sums in one pass (the acceptance predicate feeds both)
+    uint32_t F = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const uint32_t th = thr_entry(thr_c, e.Z, e.L[w], w);
+        const bool acc = PRE ? (e.u[w] < th) : ((e.u[w] < th) | (th == 0xFFFFFFFFu));
+        F |= acc ? (0xFEu << (8 * w)) : 0u;
+        sumL += acc ? e.L[w] : 0;
+    }
+    const uint32_t Fm = F & 0x02020202u;
+    nflip2 = __dp4a((int)Fm, 0x01010101, nflip2);
+    sumC2 = __dp4a((int)e.Z, (int)Fm, sumC2);
+    if (F) *e.own = e.S ^ F;
+}
+
+// Byte offsets, within a shared-memory row, of what a unit of one fixed column reads: its
+// own word, the opposite-parity word at the same copies, and the one Trotter neighbour
+// outside that word. [0] for an even-copy unit, [1] for an odd one. Used by the split
+// kernel, whose rows also hold copies of the neighbouring CTA.
+struct UnitOffsets {
+    uint32_t own[2], opp[2], edge[2];
+};
+
+// The packed unit evaluated from precomputed row offsets (the split kernel's rows).
+template <int DC>
+__device__ __forceinline__ UnitEval split_unit_eval(int8_t* sp, const uint32_t* s_sdesc, uint32_t item,
+                                                    const uint4* rbq, const UnitOffsets& o) {
+    UnitEval e;
+    const uint32_t par = item & 1u;
+    const uint32_t* desc = s_sdesc + (item >> 1) * SiteDesc<DC>::DW;
+    const uint4 d0 = *reinterpret_cast<const uint4*>(desc);
+    uint32_t nrow[DC];
+    uint32_t jpack[DC / 4];
+    {
+        const uint4 d1 = *reinterpret_cast<const uint4*>(desc + 4);
+        nrow[0] = d1.x;
+        nrow[1] = d1.y;
+        nrow[2] = d1.z;
+        nrow[3] = d1.w;
+        jpack[0] = d0.z;
+        if (DC == 8) {
+            const uint4 d2 = *reinterpret_cast<const uint4*>(desc + 8);
+            nrow[DC > 4 ? 4 : 0] = d2.x;
+            nrow[DC > 5 ? 5 : 0] = d2.y;
+            nrow[DC > 6 ? 6 : 0] = d2.z;
+            nrow[DC > 7 ? 7 : 0] = d2.w;
+            jpack[DC > 4 ? 1 : 0] = d0.w;
+        }
+    }
+    const uint32_t row = d0.x;
+    const uint32_t own_off = o.own[0] + par * (o.own[1] - o.own[0]);
+    e.own = reinterpret_cast<uint32_t*>(sp + row + own_off);
+    const uint32_t S = *e.own;
+    const uint32_t O = *reinterpret_cast<const uint32_t*>(sp + row + o.opp[0] + par * (o.opp[1] - o.opp[0]));
+    const uint32_t edge = (uint8_t)sp[row + o.edge[0] + par * (o.edge[1] - o.edge[0])];
+    uint32_t a[DC];
+#pragma unroll
+    for (int d = 0; d < DC; ++d) a[d] = *reinterpret_cast<const uint32_t*>(sp + nrow[d] + own_off);
+    const uint4 r4 = *rbq;
+    e.u[0] = r4.x;
+    e.u[1] = r4.y;
+    e.u[2] = r4.z;
+    e.u[3] = r4.w;
+    const uint32_t Ln = __byte_perm(O, edge, 0x2104u + par * (0x3210u - 0x2104u));
+    const uint32_t Rn = __byte_perm(O, edge, 0x3210u + par * (0x4321u - 0x3210u));
+    const uint32_t X = (S ^ Ln) & 0x02020202u;
+    const uint32_t Y = (S ^ Rn) & 0x02020202u;
+    e.Z = 0x02020202u - ((X + Y) >> 1);
+    e.S = S;
+    field_times_spin<DC>(a, S, jpack, e.L);
+    return e;
+}
+
+// Decide and commit in one pass (PRE: produced words, u < thr alone is the rule).
+template <bool PRE>
+__device__ __forceinline__ void unit_decide_commit(const UnitEval& e, const uint32_t* thr_c, int& sumL, int& sumC2,
+                                                   int& nflip2) {
     uint32_t F = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {

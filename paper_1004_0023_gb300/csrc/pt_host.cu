@@ -324,13 +324,18 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     const int packed_dc = (dmax + 1 <= 4) ? 4 : ((dmax + 1 <= 8) ? 8 : 0);
     const bool packed_ok = (P % 8 == 0) && packed_dc > 0;
     const int want_path = opt ? opt->kernel_path : 0;
-    if (want_path < 0 || want_path > 4) {
+    if (want_path < 0 || want_path > 5) {
         free_ctx(c);
-        return create_fail(PT_EINVAL, "kernel_path must be 0..4");
+        return create_fail(PT_EINVAL, "kernel_path must be 0..5");
     }
-    if ((want_path == kPathPacked || want_path == kPathPackedInline || want_path == kPathBits) && !packed_ok) {
+    if ((want_path == kPathPacked || want_path == kPathPackedInline || want_path == kPathBits ||
+         want_path == kPathSplit) && !packed_ok) {
         free_ctx(c);
         return create_fail(PT_EINVAL, "the packed kernel needs P %% 8 == 0 and degree <= 7");
+    }
+    if (want_path == kPathSplit && P % 16 != 0) {
+        free_ctx(c);
+        return create_fail(PT_EINVAL, "the split kernel needs P %% 16 == 0");
     }
     // statistics in shared memory for ladders up to 341 rungs (16 KB); all threshold rows in
     // shared memory when they take at most 48 KB and the chosen layout still fits
@@ -347,12 +352,35 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         q.acc_in_smem = 0;
         return sweep_smem_bytes(q, pth, packed_dc) <= (size_t)max_smem;
     };
+    // the split kernel when a chain and its produced random words do not fit one CTA but do
+    // fit two, and every chain's cluster can be resident at once
+    auto split_fits = [&]() {
+        if (P % 16 != 0 || !(want_threads == 0 || (want_threads >= 64 && want_threads <= 512)) || !fits(kPathSplit))
+            return false;
+        DevProblem q = p;
+        if (sweep_smem_bytes(q, kPathSplit, packed_dc) > (size_t)max_smem) q.tables_in_smem = 0;
+        if (sweep_smem_bytes(q, kPathSplit, packed_dc) > (size_t)max_smem) q.acc_in_smem = 0;
+        LaunchPlan probe;
+        probe.path = kPathSplit;
+        probe.dclass = packed_dc;
+        probe.threads = want_threads > 0 ? want_threads : 512;
+        probe.n_consumer = probe.threads - probe.threads / 4;
+        probe.smem_bytes = sweep_smem_bytes(q, kPathSplit, packed_dc);
+        long long resident = 0;
+        if (prepare_sweep_kernel(probe) != cudaSuccess || sweep_resident_chains(q, probe, &resident) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        return resident >= R;
+    };
     if (path == 0) {
         path = kPathGeneric;
         if (packed_ok) {
             // producer warps need a block of at least two warps; int8 chains before bit-packed ones
             if ((want_threads == 0 || want_threads >= 64) && fits(kPathPacked))
                 path = kPathPacked;
+            else if (split_fits())
+                path = kPathSplit;
             else if (fits(kPathPackedInline))
                 path = kPathPackedInline;
             else if (fits(kPathBits))
@@ -370,13 +398,13 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                            c->plan.smem_bytes, max_smem);
     }
     if (opt && opt->threads_per_block > 0) {
-        const int tmax = (path == kPathGeneric) ? 512 : 1024;
+        const int tmax = (path == kPathGeneric || path == kPathSplit) ? 512 : 1024;
         if (opt->threads_per_block % 32 || opt->threads_per_block > tmax) {
             free_ctx(c);
             return create_fail(PT_EINVAL, "threads_per_block must be a multiple of 32 <= %d for this kernel", tmax);
         }
         c->plan.threads = opt->threads_per_block;
-    } else if (path == kPathPacked) {
+    } else if (path == kPathPacked || path == kPathSplit) {
         c->plan.threads = 512;
     } else {
         // enough threads for the average level (units = items * padded groups per parity)
@@ -388,7 +416,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         c->plan.threads = (int)std::min<long long>(512, std::max<long long>(128, avg));
     }
     c->plan.n_consumer = c->plan.threads;
-    if (path == kPathPacked) {
+    if (path == kPathPacked || path == kPathSplit) {
         int prod = (opt && opt->producer_threads > 0) ? opt->producer_threads
                                                       : std::max(32, (c->plan.threads / 4) / 32 * 32);
         if (prod % 32 || prod >= c->plan.threads) {
@@ -396,6 +424,12 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             return create_fail(PT_EINVAL, "producer_threads must be a multiple of 32 below threads_per_block");
         }
         c->plan.n_consumer = c->plan.threads - prod;
+        // the split kernel gives each of its P/16 + 1 word columns at least one thread
+        if (path == kPathSplit && (c->plan.n_consumer < P / 16 + 1 || prod < P / 16 + 1)) {
+            free_ctx(c);
+            return create_fail(PT_EINVAL, "the split kernel needs at least P/16 + 1 = %d consumer and producer threads",
+                               P / 16 + 1);
+        }
     }
 
     // packed-path site descriptors: row offset i*P, i, packed J bytes (two words), then the
@@ -491,16 +525,22 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
 #undef CREATE_CUDA
 
     // cooperative launch (swaps inside one launch) needs every chain resident at once
-    int per_sm = 0;
+    long long resident = 0;
     int coop_ok = 0;
     cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, c->device);
-    if (sweep_kernel_occupancy(p, c->plan, &per_sm) != cudaSuccess) per_sm = 0;
+    if (sweep_resident_chains(p, c->plan, &resident) != cudaSuccess) resident = 0;
     const int mode = opt ? opt->swap_mode : 0;
-    c->cooperative = coop_ok && (long long)per_sm * n_sm >= R && mode != 2;
+    c->cooperative = coop_ok && resident >= R && mode != 2;
     if (mode == 1 && !c->cooperative) {
         free_ctx(c);
-        return create_fail(PT_EINVAL, "swap_mode 1 needs all %d chains resident at once (%d per SM x %d SMs)", R,
-                           per_sm, n_sm);
+        return create_fail(PT_EINVAL, "swap_mode 1 needs all %d chains resident at once (%lld fit on %d SMs)", R,
+                           resident, n_sm);
+    }
+    if (path == kPathSplit && resident < R) {
+        // the two CTAs of a chain always run together, but the swap passes need every chain
+        free_ctx(c);
+        return create_fail(PT_EINVAL, "the split kernel needs all %d chains resident at once (%lld fit)", R,
+                           resident);
     }
     *out = c;
     return PT_OK;

@@ -62,8 +62,9 @@ struct DevProblem {
 };
 
 // Sweep kernel variants: byte-wise (any shape), packed with Philox inline, packed with the
-// random words produced one sweep ahead by dedicated warps.
-enum { kPathGeneric = 1, kPathPackedInline = 2, kPathPacked = 3, kPathBits = 4 };
+// random words produced one sweep ahead by dedicated warps, bit-packed, and the produced-words
+// kernel with each chain split over a cluster of two CTAs.
+enum { kPathGeneric = 1, kPathPackedInline = 2, kPathPacked = 3, kPathBits = 4, kPathSplit = 5 };
 
 struct LaunchPlan {
     int path;            // kPath*
@@ -118,6 +119,8 @@ cudaError_t launch_swap(const DevProblem& p, long long q, cudaStream_t s);
 cudaError_t launch_gather_state(const DevProblem& p, int8_t* out, cudaStream_t s);
 cudaError_t launch_scatter_state(const DevProblem& p, const int8_t* in, cudaStream_t s);
 cudaError_t sweep_kernel_occupancy(const DevProblem& p, const LaunchPlan& plan, int* blocks_per_sm);
+// Chains that can be resident at once for a plan (CTAs, or clusters of the split kernel).
+cudaError_t sweep_resident_chains(const DevProblem& p, const LaunchPlan& plan, long long* chains);
 cudaError_t prepare_sweep_kernel(const LaunchPlan& plan);
 
 // One problem of a multi-problem cooperative launch (one CTA per chain of every problem).

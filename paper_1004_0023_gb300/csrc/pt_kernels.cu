@@ -14,6 +14,7 @@
 // Swap (Sec. 2: neighbouring chains, disjoint pairs): inside a cooperative launch each
 // chain publishes (E, M) for pass q in a per-(pass, rung) mailbox and waits, with a time
 // limit, only for its pair partner; both partners evaluate the same decision.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,6 +23,8 @@
 #include "pt_internal.h"
 
 namespace ptq {
+
+namespace cg = cooperative_groups;
 
 // ------------------------------------------------------------------------- smem layouts
 
@@ -80,8 +83,11 @@ struct FastLayout {
     }
 };
 
+size_t split_smem_bytes(const DevProblem& p, int dclass);
+
 size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass) {
     if (path == kPathGeneric) return GenericLayout(p).total;
+    if (path == kPathSplit) return split_smem_bytes(p, dclass);
     return FastLayout(p, dclass, path == kPathPacked, path == kPathBits).total;
 }
 
@@ -105,8 +111,9 @@ struct SwapSide {
 // statistics of the rung the chain sits on (to `acc`, shared or global) and, when a swap
 // pass follows this sweep, publish (E, M) in the pass's mailbox. Does not wait.
 // pass >= 0: a swap pass with this index (within the launch) follows the sweep.
+// write = false: a CTA that shares the chain with the one that publishes (split kernel).
 __device__ SwapSide eos_publish(const DevProblem& p, int rung, long long& E, long long& M, long long dE,
-                                long long dM, int pass, long long q0, uint32_t qmod0) {
+                                long long dM, int pass, long long q0, uint32_t qmod0, bool write = true) {
     E += dE;
     M += dM;
     SwapSide w;
@@ -117,7 +124,7 @@ __device__ SwapSide eos_publish(const DevProblem& p, int rung, long long& E, lon
         w.q = q0 + w.pass;
         w.tag = mbox_tag(qmod0, w.pass);
         Mailbox* mb = p.mbox + (size_t)w.pass * R;
-        if (rung != p.withhold_rung) {
+        if (write && rung != p.withhold_rung) {
             st_relaxed_u64(&mb[rung].a, ((unsigned long long)E << 24) | w.tag);
             st_relaxed_u64(&mb[rung].b, ((unsigned long long)(uint32_t)(int32_t)M << 32) | w.tag);
         }
@@ -157,9 +164,10 @@ __device__ __forceinline__ void eos_stats(const DevProblem& p, unsigned long lon
 
 // Thread 0 again: wait for the partner's mailbox (bounded by timeout_ns) and take the
 // decision both chains of the pair take. Returns the chain's rung for the next sweep; sets
-// *abort when the partner's mailbox never arrived within the time limit.
+// *abort when the partner's mailbox never arrived within the time limit. count = false: the
+// pair's attempt and acceptance are counted by another CTA of the chain (split kernel).
 __device__ int eos_decide(const DevProblem& p, const SwapSide& w, int rung, long long E, long long M,
-                          long long timeout_ns, const PhiloxKey& key, int* abort) {
+                          long long timeout_ns, const PhiloxKey& key, int* abort, bool count = true) {
     *abort = 0;
     if (!w.active) return rung;
     const int R = p.R;
@@ -185,7 +193,7 @@ __device__ int eos_decide(const DevProblem& p, const SwapSide& w, int rung, long
     const bool acc_swap = swap_accept_fast(lower ? E : pE, lower ? pE : E, lower ? M : pM, lower ? pM : M,
                                            p.coef[rl], p.coef[(R - 1) + rl], (uint32_t)w.q, (uint32_t)rl, key,
                                            p.exact_swaps != 0);
-    if (lower) {
+    if (lower && count) {
         atomicAdd(p.swap_stats + 2 * rl, 1ull);
         if (acc_swap) atomicAdd(p.swap_stats + 2 * rl + 1, 1ull);
     }
@@ -687,6 +695,341 @@ cudaError_t launch_multi(const MultiProblem* probs, const int2* map, int n_block
                                        smem, s);
 }
 
+// ------------------------------------------------------------------------- split sweep
+// One chain on a cluster of two CTAs (P % 16 == 0), for ladders short enough that a CTA per
+// chain would leave SMs idle. CTA h owns copies [h P/2, (h+1) P/2): W = P/16 four-copy words
+// per parity. Updates couple a copy only to its Trotter neighbours k +- 1 (Eq. 3), so the
+// only copies a CTA needs from its peer are
+//   - the peer's first even word (copies h P/2 + P/2 .. +6): recomputed here every sweep,
+//     with the same inputs, random words and order as the peer, so bit for bit the same;
+//   - the peer's first odd word and its last odd copy as of the previous sweep, which the
+//     recomputed word and the own first even word read; the peer writes them into this
+//     CTA's shared memory once per sweep, into one of two buffers by sweep parity.
+// Each CTA therefore runs the whole level schedule on 2W + 1 words per site, and the two meet
+// once per sweep at a cluster barrier, where they also add their halves of dE, dM and the
+// flip count. Both CTAs take the swap decision from the same mailbox values; the first CTA
+// alone publishes, counts and writes the chain's statistics.
+//
+// Row layout (bytes) of site i, RB = 8W + 16 per row:
+//   [0, 4W+4)         even words 0..W-1 (own), word W = the peer's first even word
+//   [4W+4, 8W+4)      odd words 0..W-1 (own)
+//   [8W+4, 8W+12)     the peer's first odd word, previous sweep, buffers 0 and 1
+//   [8W+12, 8W+14)    the peer's last odd copy, previous sweep, buffers 0 and 1
+// and one row of +1 copies after the last site (the field's h slot).
+struct SplitLayout {
+    size_t spins, desc, items, loff, thr, acc, red, ctl, xch, rbuf, total;
+    int W, RB, Gc;
+    __host__ __device__ SplitLayout(const DevProblem& p, int dc) {
+        const int N = p.N;
+        W = p.P / 16;
+        RB = 8 * W + 16;
+        Gc = W + 1;  // word columns of an even item; odd items use W of them
+        size_t o = 0;
+        spins = o; o += up16((size_t)(N + 1) * RB);
+        desc = o;  o += (size_t)N * (dc == 4 ? 32 : 48);
+        items = o; o += up16((size_t)2 * N * 4);
+        loff = o;  o += up16((size_t)(p.n_levels + 1) * 4);
+        thr = o;   o += thr_bytes(p);
+        acc = o;   o += acc_bytes(p);
+        red = o;   o += 32 * 3 * 8;
+        ctl = o;   o += 32;
+        xch = o;   o += 64;  // written by the peer: [sweep parity][dE, dM, flips, abort], final abort
+        rbuf = o;  o += (size_t)2 * (2 * N) * Gc * 16;
+        total = o;
+    }
+};
+
+size_t split_smem_bytes(const DevProblem& p, int dclass) { return SplitLayout(p, dclass).total; }
+
+// Global copy held at byte c of a split row of CTA h, or -1 for padding.
+__device__ __forceinline__ int split_copy(int c, int W, int h, int P) {
+    const int hs = 4 * W + 4;
+    if (c < hs) return 8 * ((h * W + (c >> 2)) % (2 * W)) + 2 * (c & 3);
+    if (c < 8 * W + 4) return 8 * (h * W + ((c - hs) >> 2)) + 2 * (c & 3) + 1;
+    if (c < 8 * W + 12) return 8 * (((h + 1) * W) % (2 * W)) + 2 * (c & 3) + 1;
+    if (c < 8 * W + 14) return (8 * h * W - 1 + P) % P;
+    return -1;
+}
+
+// Offsets of column g's reads (see UnitOffsets) while the peer's previous-sweep copies sit
+// in buffer b.
+__device__ __forceinline__ UnitOffsets split_offsets(int g, int W, int b) {
+    const uint32_t hs = 4u * W + 4u, w4 = 4u * (uint32_t)g;
+    UnitOffsets o;
+    o.own[0] = w4;
+    o.own[1] = hs + w4;
+    o.opp[0] = g < W ? hs + w4 : 8u * W + 4u + 4u * (uint32_t)b;
+    o.opp[1] = w4;
+    o.edge[0] = g >= 1 ? hs + w4 - 1u : 8u * W + 12u + (uint32_t)b;
+    o.edge[1] = w4 + 4u;
+    return o;
+}
+
+template <int DC>
+__global__ void __launch_bounds__(512, 1)
+sweep_split_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
+                   long long timeout_ns, int n_consumer) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int h = (int)cluster.block_rank();
+    const bool lead = h == 0;
+    const int slot = blockIdx.x >> 1;
+    const int N = p.N, P = p.P;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const SplitLayout L(p, DC);
+    const int W = L.W, RB = L.RB, Gc = L.Gc;
+    const int hs = 4 * W + 4;
+    int8_t* sp = reinterpret_cast<int8_t*>(smem + L.spins);
+    uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem + L.desc);
+    uint32_t* s_items = reinterpret_cast<uint32_t*>(smem + L.items);
+    int32_t* s_loff = reinterpret_cast<int32_t*>(smem + L.loff);
+    uint32_t* s_thr = reinterpret_cast<uint32_t*>(smem + L.thr);
+    long long* s_red = reinterpret_cast<long long*>(smem + L.red);
+    int* s_ctl = reinterpret_cast<int*>(smem + L.ctl);
+    int* s_xch = reinterpret_cast<int*>(smem + L.xch);
+    uint4* rbuf = reinterpret_cast<uint4*>(smem + L.rbuf);
+    unsigned long long* s_acc = reinterpret_cast<unsigned long long*>(smem + L.acc);
+    int8_t* peer_sp = cluster.map_shared_rank(sp, h ^ 1);
+    int* peer_xch = cluster.map_shared_rank(s_xch, h ^ 1);
+    const int NC = n_consumer;
+    const bool consumer = tid < NC;
+    const int DW = SiteDesc<DC>::DW;
+
+    {
+        const int8_t* src = p.spins + (size_t)slot * p.slot_stride;
+        for (int x = tid; x < N * RB; x += nt) {
+            const int i = x / RB, c = x - i * RB;
+            const int k = split_copy(c, W, h, P);
+            sp[x] = k >= 0 ? src[(size_t)i * P + k] : (int8_t)0;
+        }
+        for (int x = tid; x < RB; x += nt) sp[(size_t)N * RB + x] = 1;
+        // descriptors with the row offsets rescaled from P to RB bytes per row
+        const uint32_t NP = (uint32_t)N * (uint32_t)P;
+        for (int x = tid; x < N * DW; x += nt) {
+            const int f = x % DW;
+            uint32_t v = p.desc[x];
+            if (f == 0 || f >= 4) v = v >= NP ? (uint32_t)N * RB : (v / (uint32_t)P) * (uint32_t)RB;
+            s_desc[x] = v;
+        }
+        for (int x = tid; x < 2 * N; x += nt) s_items[x] = p.items[x];
+        for (int x = tid; x <= p.n_levels; x += nt) s_loff[x] = p.level_off[x];
+        for (int x = tid; x < 16; x += nt) s_xch[x] = 0;
+    }
+    int rung = p.rung_of_slot[slot];
+    load_thr(p, s_thr, rung, tid, nt);
+    if (p.acc_in_smem)
+        for (int x = tid; x < p.R * kAccCount; x += nt) s_acc[x] = 0ull;
+    long long E = p.E[slot], M = p.M[slot];  // meaningful in thread 0 only
+
+    const PhiloxKey key = philox_schedule(p.key0, p.key1);
+    const uint32_t* thr_c = thr_row(p, s_thr, rung) + 3 * p.Lmax;
+    const int n_items = 2 * N;
+    const int lane = tid & 31;
+    if (tid == 0) {
+        s_ctl[4] = -1;  // partner rung of the pending swap pass
+        s_ctl[5] = 0;   // this CTA's swap wait gave up
+        s_ctl[6] = 0;   // either CTA's wait gave up (known at the last cluster barrier)
+        int* s_sum = reinterpret_cast<int*>(s_red);
+        s_sum[0] = s_sum[1] = s_sum[2] = 0;
+    }
+    // every CTA of the cluster is running and initialised before any shared-memory exchange
+    cluster_barrier();
+
+    // random words of sweep t for this CTA's columns (global chunk (hW + g) mod 2W)
+    auto produce = [&](uint4* buf, uint32_t t) {
+        const int ptid = tid - NC, np = nt - NC;
+        const int pg = ptid % Gc, pstep = np / Gc;
+        if (ptid / Gc >= pstep) return;
+        const uint32_t gg = (uint32_t)((h * W + pg) % (2 * W));
+        for (int q = ptid / Gc; q < n_items; q += pstep) {
+            const uint32_t it = s_items[q];
+            if ((it & 1u) && pg == W) continue;
+            const uint4 r = philox(make_uint4(t, it >> 1, (uint32_t)slot, ((it & 1u) << 24) | gg), key);
+            buf[q * Gc + pg] = make_uint4(min(r.x, 0xFFFFFFFEu), min(r.y, 0xFFFFFFFEu), min(r.z, 0xFFFFFFFEu),
+                                          min(r.w, 0xFFFFFFFEu));
+        }
+    };
+    if (!consumer) produce(rbuf, (uint32_t)t0);
+    __syncthreads();
+
+    // consumers: a fixed column g_own per thread, items q_lane, q_lane + q_step, ... of a level
+    const int g_own = tid % Gc, q_lane = tid / Gc, q_step = NC / Gc;
+    const bool lane_ok = consumer && q_lane < q_step;
+    const bool ghost_col = g_own == W;  // the recomputed peer word: its flips are the peer's
+    // level 0 of the next sweep during the swap wait: units v, v + (NC - 32) of the level
+    // (v = tid - 32), so that warp 0 is free to poll the partner's mailbox
+    const int units0 = (s_loff[1] - s_loff[0]) * Gc;
+    const bool spec_ok = p.tables_in_smem && NC > 32 && units0 <= 2 * (NC - 32);
+    int sq[2], sg[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int u = (tid - 32) + k * (NC - 32);
+        sg[k] = u % Gc;
+        sq[k] = (tid >= 32 && consumer && u < units0) ? s_loff[0] + u / Gc : -1;
+    }
+    bool spec_done = false;
+    int lL = 0, lC = 0, lF = 0;  // this sweep's own units in the levels (counts twice, see unit_commit)
+    int pL = 0, pC = 0, pF = 0;  // the level-0 units applied early
+    SwapSide side;
+    side.active = 0;
+    const uint32_t qmod0 = (uint32_t)(q0 % kTagPeriod);
+    int since_pass = 0, next_pass = 0;  // thread 0
+    long long sE = 0, sM = 0, sF = 0;   // thread 0: this CTA's half of the sweep's changes
+
+    for (int s = 0; s < n_sweeps; ++s) {
+        const uint32_t t = (uint32_t)(t0 + s);
+        const int b = s & 1;
+        const bool dead = (s_ctl[5] | s_ctl[6]) != 0;
+        if (consumer) {
+            if (!dead) {
+                const uint4* rb = rbuf + (size_t)b * n_items * Gc;
+                const UnitOffsets off = split_offsets(g_own, W, b);
+                if (!spec_done) pL = pC = pF = 0;
+                lL = lC = lF = 0;
+                for (int lev = spec_done ? 1 : 0; lev < p.n_levels; ++lev) {
+                    if (lane_ok) {
+                        const int end = s_loff[lev + 1];
+                        for (int q = s_loff[lev] + q_lane; q < end; q += q_step) {
+                            const uint32_t it = s_items[q];
+                            if (ghost_col && (it & 1u)) continue;
+                            const UnitEval e = split_unit_eval<DC>(sp, s_desc, it, rb + q * Gc + g_own, off);
+                            unit_decide_commit<true>(e, thr_c, lL, lC, lF);
+                        }
+                    }
+                    named_barrier(1, NC);
+                }
+                if (ghost_col) lL = lC = lF = 0;
+                const int mL = lL + pL, mC = lC + pC, mF = lF + pF;
+                const int dE = __reduce_add_sync(0xFFFFFFFFu, -2 * mL);
+                const int dM = __reduce_add_sync(0xFFFFFFFFu, -2 * (mC - mF));
+                const int dF = __reduce_add_sync(0xFFFFFFFFu, mF) >> 1;
+                int* s_sum = reinterpret_cast<int*>(s_red);
+                if (lane == 0) {
+                    atomicAdd(s_sum + 0, dE);
+                    atomicAdd(s_sum + 1, dM);
+                    atomicAdd(s_sum + 2, dF);
+                }
+                named_barrier(1, NC);
+                // the peer's next sweep reads this sweep's first odd word and last odd copy
+                const int bn = b ^ 1;
+                for (int i = tid; i < N; i += NC) {
+                    const int8_t* r = sp + (size_t)i * RB;
+                    int8_t* pr = peer_sp + (size_t)i * RB;
+                    *reinterpret_cast<uint32_t*>(pr + 8 * W + 4 + 4 * bn) = *reinterpret_cast<const uint32_t*>(r + hs);
+                    pr[8 * W + 12 + bn] = r[hs + 4 * W - 1];
+                }
+            }
+            if (tid == 0) {
+                int* s_sum = reinterpret_cast<int*>(s_red);
+                sE = s_sum[0];
+                sM = s_sum[1];
+                sF = s_sum[2];
+                s_sum[0] = s_sum[1] = s_sum[2] = 0;
+                int* x = peer_xch + 4 * b;
+                x[0] = (int)sE;
+                x[1] = (int)sM;
+                x[2] = (int)sF;
+                x[3] = s_ctl[5];
+            }
+        } else if (!dead && s + 1 < n_sweeps) {
+            produce(rbuf + (size_t)(b ^ 1) * n_items * Gc, t + 1u);
+        }
+        // both halves of the sweep are done, the exchanged words and sums are visible and
+        // the next sweep's random words are complete
+        cluster_barrier();
+        if (tid == 0) {
+            const int* x = s_xch + 4 * b;
+            if (x[3] || s_ctl[5]) s_ctl[6] = 1;
+            if (!s_ctl[6]) {
+                int pass = -1;
+                if (sweeps_per_swap > 0 && ++since_pass == sweeps_per_swap) {
+                    since_pass = 0;
+                    pass = next_pass++;
+                }
+                side = eos_publish(p, rung, E, M, sE + x[0], sM + x[1], pass, q0, qmod0, lead);
+                sF += x[2];
+                s_ctl[4] = side.active ? side.partner : -1;
+            }
+        }
+        __syncthreads();
+        if (s_ctl[6] || !consumer) continue;
+
+        // level 0 of sweep s + 1 under both candidate rungs
+        const bool spec = spec_ok && s + 1 < n_sweeps;
+        const int prung = s_ctl[4];
+        UnitEval ev[2];
+        uint32_t Fa[2] = {0u, 0u}, Fb[2] = {0u, 0u};
+        bool valid[2] = {false, false};
+        if (spec) {
+            const uint4* rb1 = rbuf + (size_t)(b ^ 1) * n_items * Gc;
+            const uint32_t* thr_b = prung >= 0 ? thr_row(p, s_thr, prung) + 3 * p.Lmax : thr_c;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (sq[k] < 0) continue;
+                const uint32_t it = s_items[sq[k]];
+                valid[k] = !((it & 1u) && sg[k] == W);
+                if (valid[k]) {
+                    ev[k] = split_unit_eval<DC>(sp, s_desc, it, rb1 + sq[k] * Gc + sg[k],
+                                                split_offsets(sg[k], W, b ^ 1));
+                    Fa[k] = unit_flips<true>(ev[k], thr_c);
+                    Fb[k] = prung >= 0 ? unit_flips<true>(ev[k], thr_b) : Fa[k];
+                }
+            }
+        }
+        if (tid == 0) {
+            if (lead) eos_stats(p, p.acc_in_smem ? s_acc : p.acc, rung, E, M, sF);
+            int abort_flag = 0;
+            s_ctl[2 * b] = eos_decide(p, side, rung, E, M, timeout_ns, key, &abort_flag, lead);
+            if (abort_flag) s_ctl[5] = 1;
+        }
+        named_barrier(1, NC);
+        if (s_ctl[5]) continue;  // the next sweep is skipped; the cluster barriers go on
+        const int nr = s_ctl[2 * b];
+        const bool moved = nr != rung;
+        if (moved) {
+            rung = nr;
+            if (!p.tables_in_smem) load_thr(p, s_thr, rung, tid, NC);
+            thr_c = thr_row(p, s_thr, rung) + 3 * p.Lmax;
+        }
+        spec_done = spec;
+        if (spec) {
+            pL = pC = pF = 0;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!valid[k]) continue;
+                int jL = 0, jC = 0, jF = 0;
+                unit_commit(ev[k], moved ? Fb[k] : Fa[k], jL, jC, jF);
+                if (sg[k] != W) {
+                    pL += jL;
+                    pC += jC;
+                    pF += jF;
+                }
+            }
+        }
+        named_barrier(1, NC);
+    }
+    // both CTAs agree whether a swap wait gave up before either writes anything back
+    if (tid == 0) peer_xch[8] = s_ctl[5] | s_ctl[6];
+    cluster_barrier();
+    if (tid == 0 && (s_xch[8] || s_ctl[5] || s_ctl[6])) s_ctl[6] = 1;
+    __syncthreads();
+    if (s_ctl[6]) return;
+    if (lead) flush_acc(p, s_acc, tid, nt);
+    {
+        int8_t* dst = p.spins + (size_t)slot * p.slot_stride;
+        for (int x = tid; x < N * RB; x += nt) {
+            const int i = x / RB, c = x - i * RB;
+            if (c < 4 * W || (c >= hs && c < hs + 4 * W)) dst[(size_t)i * P + split_copy(c, W, h, P)] = sp[x];
+        }
+    }
+    if (tid == 0 && lead) {
+        p.E[slot] = E;
+        p.M[slot] = M;
+        p.rung_of_slot[slot] = rung;
+        p.slot_of_rung[rung] = slot;
+    }
+}
+
 // ------------------------------------------------------------------------- init / energy
 // Initial spins: copy k of site i of chain rho is -1 iff bit 31 of word k%4 of
 // philox((0, i, rho, INIT<<28 | k/4)) is set.
@@ -792,6 +1135,8 @@ static const void* sweep_fn(const LaunchPlan& plan) {
             default: return (const void*)sweep_kernel<32>;
         }
     }
+    if (plan.path == kPathSplit)
+        return plan.dclass == 4 ? (const void*)sweep_split_kernel<4> : (const void*)sweep_split_kernel<8>;
     if (plan.path == kPathBits) {
         if (plan.threads > 512)
             return plan.dclass == 4 ? (const void*)sweep_packed_kernel<4, false, 1024, true>
@@ -826,6 +1171,43 @@ cudaError_t sweep_kernel_occupancy(const DevProblem& p, const LaunchPlan& plan, 
                                                          plan.smem_bytes);
 }
 
+// The split kernel's launch: R clusters of two CTAs; cooperative when swap passes run inside.
+static cudaLaunchConfig_t split_config(const DevProblem& p, const LaunchPlan& plan, bool cooperative,
+                                       cudaStream_t s, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * p.R);
+    cfg.blockDim = dim3(plan.threads);
+    cfg.dynamicSmemBytes = plan.smem_bytes;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeCooperative;
+    attr[1].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = cooperative ? 2 : 1;
+    return cfg;
+}
+
+cudaError_t sweep_resident_chains(const DevProblem& p, const LaunchPlan& plan, long long* chains) {
+    *chains = 0;
+    if (plan.path == kPathSplit) {
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = split_config(p, plan, false, 0, attr);
+        int clusters = 0;
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, sweep_fn(plan), &cfg);
+        if (e == cudaSuccess) *chains = clusters;
+        return e;
+    }
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = sweep_kernel_occupancy(p, plan, &per_sm);
+    if (e == cudaSuccess) *chains = (long long)per_sm * n_sm;
+    return e;
+}
+
 cudaError_t launch_sweeps(const DevProblem& p, const LaunchPlan& plan, long long t0, long long q0,
                           int n_sweeps, int sweeps_per_swap, long long timeout_ns, bool cooperative,
                           cudaStream_t s) {
@@ -833,6 +1215,13 @@ cudaError_t launch_sweeps(const DevProblem& p, const LaunchPlan& plan, long long
     int n_consumer = plan.n_consumer;
     void* args[] = {&pp, &t0, &q0, &n_sweeps, &sweeps_per_swap, &timeout_ns, &n_consumer};
     const void* fn = sweep_fn(plan);
+    if (plan.path == kPathSplit) {
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = split_config(p, plan, cooperative, s, attr);
+        const cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
+        if (e != cudaSuccess) (void)cudaGetLastError();  // a rejected launch leaves no error for the next one
+        return e;
+    }
     if (cooperative)
         return cudaLaunchCooperativeKernel(fn, dim3(p.R), dim3(plan.threads), args, plan.smem_bytes, s);
     return cudaLaunchKernel(fn, dim3(p.R), dim3(plan.threads), args, plan.smem_bytes, s);
