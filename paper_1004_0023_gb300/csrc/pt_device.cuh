@@ -280,6 +280,19 @@ __device__ __forceinline__ void field_times_spin(const uint32_t* a, uint32_t S, 
     }
 }
 
+// All ones when the attempt with random word u is accepted against threshold th, else zero:
+// u < th, read off the borrow of u - th (one subtract with carry out, one subtract of the
+// carry), so that the flip mask and the sums below are formed by multiply-adds on the FMA
+// pipe instead of compares and selects on the ALU pipe. Inline words (PRE = false) are first
+// capped at 2^32 - 2, which folds in the "accept always" entry 0xFFFFFFFF exactly.
+template <bool PRE>
+__device__ __forceinline__ uint32_t accept_mask(uint32_t u, uint32_t th) {
+    if (!PRE) u = min(u, 0xFFFFFFFEu);
+    uint32_t d, m;
+    asm("sub.cc.u32 %0, %2, %3;\n\tsubc.u32 %1, 0, 0;" : "=r"(d), "=r"(m) : "r"(u), "r"(th));
+    return m;
+}
+
 // Threshold entry thr_c[3 L + col] of copy w, col = byte w of Z: the byte offset
 // 4 (3 L + col) comes out of one dp4a (Z's byte w times 4, plus 12 L), keeping the byte
 // extraction and the index arithmetic off the ALU pipe.
@@ -370,9 +383,7 @@ __device__ __forceinline__ uint32_t unit_flips(const UnitEval& e, const uint32_t
     uint32_t F = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const uint32_t th = thr_entry(thr_c, e.Z, e.L[w], w);
-        const bool acc = PRE ? (e.u[w] < th) : ((e.u[w] < th) | (th == 0xFFFFFFFFu));
-        F |= acc ? (0xFEu << (8 * w)) : 0u;
+        F -= accept_mask<PRE>(e.u[w], thr_entry(thr_c, e.Z, e.L[w], w)) * (0xFEu << (8 * w));
     }
     return F;
 }
@@ -398,10 +409,9 @@ __device__ __forceinline__ void packed_unit(int8_t* sp, const uint32_t* s_sdesc,
     uint32_t F = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const uint32_t th = thr_entry(thr_c, e.Z, e.L[w], w);
-        const bool acc = PRE ? (e.u[w] < th) : ((e.u[w] < th) | (th == 0xFFFFFFFFu));
-        F |= acc ? (0xFEu << (8 * w)) : 0u;
-        sumL += acc ? e.L[w] : 0;
+        const uint32_t m = accept_mask<PRE>(e.u[w], thr_entry(thr_c, e.Z, e.L[w], w));
+        F -= m * (0xFEu << (8 * w));
+        sumL -= (int)m * e.L[w];
     }
     const uint32_t Fm = F & 0x02020202u;
     nflip2 = __dp4a((int)Fm, 0x01010101, nflip2);
@@ -474,10 +484,9 @@ __device__ __forceinline__ void unit_decide_commit(const UnitEval& e, const uint
     uint32_t F = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const uint32_t th = thr_entry(thr_c, e.Z, e.L[w], w);
-        const bool acc = PRE ? (e.u[w] < th) : ((e.u[w] < th) | (th == 0xFFFFFFFFu));
-        F |= acc ? (0xFEu << (8 * w)) : 0u;
-        sumL += acc ? e.L[w] : 0;
+        const uint32_t m = accept_mask<PRE>(e.u[w], thr_entry(thr_c, e.Z, e.L[w], w));
+        F -= m * (0xFEu << (8 * w));
+        sumL -= (int)m * e.L[w];
     }
     const uint32_t Fm = F & 0x02020202u;
     nflip2 = __dp4a((int)Fm, 0x01010101, nflip2);
@@ -552,11 +561,10 @@ __device__ __forceinline__ void packed_unit_bits(uint8_t* bp, const uint32_t* s_
     uint32_t F = 0, flipbits = 0;
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const uint32_t th = thr_entry(thr_c, Z, L[w], w);
-        const bool acc = PRE ? (u[w] < th) : ((u[w] < th) | (th == 0xFFFFFFFFu));
-        F |= acc ? (0xFEu << (8 * w)) : 0u;
-        flipbits |= acc ? (1u << (2 * w)) : 0u;
-        sumL += acc ? L[w] : 0;
+        const uint32_t m = accept_mask<PRE>(u[w], thr_entry(thr_c, Z, L[w], w));
+        F -= m * (0xFEu << (8 * w));
+        flipbits -= m * (1u << (2 * w));
+        sumL -= (int)m * L[w];
     }
     const uint32_t Fm = F & 0x02020202u;
     nflip2 = __dp4a((int)Fm, 0x01010101, nflip2);
