@@ -199,6 +199,15 @@ int pt_make_tables(int32_t P, const pt_rung* ladder, int32_t R, int32_t lmax, ui
                    double* coef);
 int pt_make_schedule(const pt_instance* inst, uint32_t* items, int32_t* level_off,
                      int32_t* n_levels);
+/* The same dependencies and the same number of levels, with the updates spread over the
+ * levels for a kernel that takes items_per_round items of a level at a time: each update
+ * lies between the earliest level its predecessors allow and the latest its successors
+ * allow, and levels are filled in whole rounds, most urgent updates first. Any such
+ * assignment replays the sequential order exactly (Sec. 5's regions, swept in dependency
+ * order), so results do not depend on it. items_per_round = 0 gives pt_make_schedule's
+ * as-early-as-possible levels. pt_create uses this with its kernel's round size. */
+int pt_make_schedule_balanced(const pt_instance* inst, int32_t items_per_round, uint32_t* items,
+                              int32_t* level_off, int32_t* n_levels);
 
 /* ---- Many independent problems in one launch ----------------------------------------
  * The paper solves many problem instances (Sec. 1) one application run at a time; here a

@@ -447,7 +447,7 @@ static cudaError_t balloc(pt_batch* b, T** ptr, size_t bytes) {
     return cudaSuccess;
 }
 
-int ptq::prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len) {
+int ptq::prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len, int per_round) {
     const pt_instance* inst = &r.inst;
     const int N = inst->n, nE = inst->n_edges, P = r.P, R = r.R;
     if (N < 1 || N > 65535 || nE < 0 || !inst->h || (nE > 0 && (!inst->ei || !inst->ej || !inst->J))) {
@@ -523,7 +523,7 @@ int ptq::prepare_request(const pt_request& r, Prepared& pr, char* why, size_t wh
     pr.slot_stride = (int)(((size_t)N * P + 15) & ~(size_t)15);
     build_tables(R, P, Lmax, r.ladder, pr.thr, pr.coef);
     if (pr.coef.size() < 2) pr.coef.assign(2, 0.0);
-    level_schedule(N, adj, pr.items, pr.level_off);
+    level_schedule(N, adj, pr.items, pr.level_off, per_round);
     pr.n_levels = (int)pr.level_off.size() - 1;
     build_site_desc(N, P, pr.dc, adj, adjJ, inst->h, pr.sdesc);
     return PT_OK;

@@ -109,7 +109,8 @@ void ptq::build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vecto
 // they are (i,0) and (i,1), or (i,p) and (j,p) with i, j adjacent; the level of an update
 // is one more than the largest level of the earlier updates it conflicts with.
 void ptq::level_schedule(int N, const std::vector<std::vector<int>>& adj, std::vector<uint32_t>& items,
-                           std::vector<int32_t>& level_off) {
+                           std::vector<int32_t>& level_off, int per_round) {
+    // as early as possible: l0 / l1 = the longest chain of predecessors of (i, 0) / (i, 1)
     std::vector<int> l0(N), l1(N);
     int nlev = 0;
     for (int i = 0; i < N; ++i) {
@@ -122,6 +123,66 @@ void ptq::level_schedule(int N, const std::vector<std::vector<int>>& adj, std::v
         l0[i] = a;
         l1[i] = std::max(b, a + 1);
         nlev = std::max(nlev, l1[i] + 1);
+    }
+    if (per_round > 0) {
+        // Balanced: the same number of levels, each update between its earliest level and
+        // the latest one its successors allow (b0 / b1), the levels filled in whole rounds
+        // of per_round items, most urgent first. Items (i, p) are numbered 2i + p; the
+        // successors of (i, p) are (j, p) for neighbours j > i, and (i, 1) when p = 0.
+        std::vector<int> b0(N), b1(N);
+        for (int i = N - 1; i >= 0; --i) {
+            int a = nlev - 1, b = nlev - 1;
+            for (int j : adj[i])
+                if (j > i) {
+                    a = std::min(a, b0[j] - 1);
+                    b = std::min(b, b1[j] - 1);
+                }
+            b1[i] = b;
+            b0[i] = std::min(a, b - 1);
+        }
+        auto latest = [&](int x) { return (x & 1) ? b1[x >> 1] : b0[x >> 1]; };
+        std::vector<int> waiting(2 * (size_t)N, 0), level(2 * (size_t)N, -1);
+        for (int i = 0; i < N; ++i) {
+            for (int j : adj[i])
+                if (j < i) {
+                    waiting[2 * i]++;
+                    waiting[2 * i + 1]++;
+                }
+            waiting[2 * i + 1]++;
+        }
+        std::vector<int> ready, next;
+        for (int x = 0; x < 2 * N; ++x)
+            if (waiting[x] == 0) ready.push_back(x);
+        int left = 2 * N;
+        for (int l = 0; l < nlev; ++l) {
+            std::sort(ready.begin(), ready.end(), [&](int x, int y) {
+                const int bx = latest(x), by = latest(y);
+                return bx != by ? bx < by : x < y;
+            });
+            int must = 0;
+            while (must < (int)ready.size() && latest(ready[must]) == l) ++must;
+            const int even_share = (left + (nlev - l) - 1) / (nlev - l);
+            const int cap = std::max(must, (even_share + per_round - 1) / per_round * per_round);
+            const int take = std::min(cap, (int)ready.size());
+            next.clear();
+            for (int k = 0; k < take; ++k) {
+                const int x = ready[k], i = x >> 1;
+                level[x] = l;
+                auto release = [&](int y) {
+                    if (--waiting[y] == 0) next.push_back(y);
+                };
+                for (int j : adj[i])
+                    if (j > i) release(2 * j + (x & 1));
+                if (!(x & 1)) release(x + 1);
+            }
+            left -= take;
+            ready.erase(ready.begin(), ready.begin() + take);
+            ready.insert(ready.end(), next.begin(), next.end());
+        }
+        for (int i = 0; i < N; ++i) {
+            l0[i] = level[2 * i];
+            l1[i] = level[2 * i + 1];
+        }
     }
     std::vector<int> count(nlev + 1, 0);
     for (int i = 0; i < N; ++i) {
@@ -430,6 +491,20 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             return create_fail(PT_EINVAL, "the split kernel needs at least P/16 + 1 = %d consumer and producer threads",
                                P / 16 + 1);
         }
+    }
+
+    // the levels, rebalanced for the items this plan's kernel takes per round: consumer
+    // threads over word columns per item (a power of two for the one-CTA kernels, W + 1 for
+    // the split one); the level count and the dependencies stay the same
+    {
+        int cols = 1;
+        if (path == kPathSplit) {
+            cols = P / 16 + 1;
+        } else {
+            const int G = (path == kPathGeneric) ? ((P / 2) + 3) / 4 : P / 8;
+            while (cols < G) cols <<= 1;
+        }
+        level_schedule(N, adj, items, level_off, std::max(1, c->plan.n_consumer / cols));
     }
 
     // packed-path site descriptors: row offset i*P, i, packed J bytes (two words), then the
@@ -793,7 +868,12 @@ extern "C" int pt_make_tables(int32_t P, const pt_rung* ladder, int32_t R, int32
 }
 
 extern "C" int pt_make_schedule(const pt_instance* inst, uint32_t* items, int32_t* level_off, int32_t* n_levels) {
-    if (!inst || !items || !level_off || !n_levels || inst->n < 1) return PT_EINVAL;
+    return pt_make_schedule_balanced(inst, 0, items, level_off, n_levels);
+}
+
+extern "C" int pt_make_schedule_balanced(const pt_instance* inst, int32_t items_per_round, uint32_t* items,
+                                         int32_t* level_off, int32_t* n_levels) {
+    if (!inst || !items || !level_off || !n_levels || inst->n < 1 || items_per_round < 0) return PT_EINVAL;
     std::vector<std::vector<int>> adj(inst->n);
     for (int b = 0; b < inst->n_edges; ++b) {
         const int u = inst->ei[b], v = inst->ej[b];
@@ -803,7 +883,7 @@ extern "C" int pt_make_schedule(const pt_instance* inst, uint32_t* items, int32_
     }
     std::vector<uint32_t> it;
     std::vector<int32_t> off;
-    level_schedule(inst->n, adj, it, off);
+    level_schedule(inst->n, adj, it, off, items_per_round);
     memcpy(items, it.data(), it.size() * 4);
     memcpy(level_off, off.data(), off.size() * 4);
     *n_levels = (int32_t)off.size() - 1;

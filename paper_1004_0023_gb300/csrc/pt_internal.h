@@ -138,8 +138,10 @@ cudaError_t launch_multi(const MultiProblem* probs, const int2* map, int n_block
 // Host-side preparation shared by single and batched problems (pt_host.cu).
 void build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vector<uint32_t>& thr,
                   std::vector<double>& coef);
+// per_round > 0: levels balanced for a kernel that takes per_round items of a level at a
+// time (same level count, same dependencies); 0: every update as early as possible.
 void level_schedule(int N, const std::vector<std::vector<int>>& adj, std::vector<uint32_t>& items,
-                    std::vector<int32_t>& level_off);
+                    std::vector<int32_t>& level_off, int per_round = 0);
 void build_site_desc(int N, int row_bytes, int dclass, const std::vector<std::vector<int>>& adj,
                      const std::vector<std::vector<int>>& adjJ, const int32_t* h, std::vector<uint32_t>& desc);
 
@@ -153,7 +155,8 @@ struct Prepared {
         off_sw, off_mbox = 0, off_inst = 0, off_map = 0, off_status = 0;
     long long sweep_limit;
 };
-int prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len);
+// per_round > 0: the level schedule is balanced for a kernel taking per_round items at a time.
+int prepare_request(const pt_request& r, Prepared& pr, char* why, size_t why_len, int per_round = 0);
 size_t request_block_layout(Prepared& p, size_t mailbox_entries = 0);
 void fill_instance(BatchInstance& I, const Prepared& p, unsigned char* base, const pt_request& r);
 // Group width of a fixed layout: narrowest that fits (one warp per chain where possible),

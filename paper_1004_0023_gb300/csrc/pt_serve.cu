@@ -272,7 +272,12 @@ extern "C" int pt_server_submit(pt_server* s, const pt_request* r, int64_t* id) 
     if (s->err) return s->err;
     ServeReq* q = new ServeReq();
     char why[200];
-    const int rc = prepare_request(*r, q->prep, why, sizeof(why));
+    // levels balanced for the one-CTA-per-chain kernel of a streamed launch (384 consumer
+    // threads over the power-of-two word columns of an item); any valid schedule serves
+    // the batched kernel of a backlog launch as well
+    int cols = 1;
+    while (cols < r->P / 8) cols <<= 1;
+    const int rc = prepare_request(*r, q->prep, why, sizeof(why), r->P >= 8 ? std::max(1, 384 / cols) : 0);
     if (rc) {
         delete q;
         return sfail(s, rc, "%s", why);

@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
     lib.pt_last_error.restype = ctypes.c_char_p
     lib.pt_make_tables.argtypes = [_i32, ctypes.POINTER(pt_rung), _i32, _i32, _vp, _vp]
     lib.pt_make_schedule.argtypes = [ctypes.POINTER(pt_instance), _vp, _vp, _p_i32]
+    lib.pt_make_schedule_balanced.argtypes = [ctypes.POINTER(pt_instance), _i32, _vp, _vp, _p_i32]
     lib.pt_run_noalloc.argtypes = [ctypes.POINTER(pt_device_problem), _i64, _i32, _i32, _vp]
     lib.pt_batch_create.argtypes = [ctypes.POINTER(pt_request), _i32, ctypes.POINTER(pt_options), _vp,
                                     ctypes.POINTER(_vp)]
@@ -143,7 +144,7 @@ def exported_symbols():
     """Names of the entry points declared in include/pt.h."""
     return ["pt_create", "pt_sweep", "pt_swap", "pt_run", "pt_read_state", "pt_write_state",
             "pt_read_observables", "pt_read_tables", "pt_get_info", "pt_sync", "pt_destroy",
-            "pt_last_error", "pt_make_tables", "pt_make_schedule", "pt_run_noalloc",
+            "pt_last_error", "pt_make_tables", "pt_make_schedule", "pt_make_schedule_balanced", "pt_run_noalloc",
             "pt_noalloc_last_error", "pt_batch_create", "pt_batch_run", "pt_batch_read_state",
             "pt_batch_read_observables", "pt_batch_get_info", "pt_batch_sync", "pt_batch_destroy",
             "pt_batch_last_error", "pt_server_create", "pt_server_submit", "pt_server_step",
@@ -172,8 +173,9 @@ def make_tables(P, T, gamma, lmax):
     return thr, coef[: 2 * (R - 1)]
 
 
-def make_schedule(n, ei, ej):
-    """Host-only: the sweep's dependency-level schedule (items grouped by level)."""
+def make_schedule(n, ei, ej, items_per_round=0):
+    """Host-only: the sweep's dependency-level schedule (items grouped by level); as early as
+    possible, or balanced for a kernel taking items_per_round items of a level at a time."""
     lib = load()
     keep = []
     ei = np.asarray(ei, np.int32)
@@ -181,7 +183,11 @@ def make_schedule(n, ei, ej):
     items = np.zeros(2 * int(n), np.uint32)
     off = np.zeros(2 * int(n) + 1, np.int32)
     nlev = _i32()
-    rc = lib.pt_make_schedule(ctypes.byref(inst), _ptr(items), _ptr(off), ctypes.byref(nlev))
+    if items_per_round:
+        rc = lib.pt_make_schedule_balanced(ctypes.byref(inst), int(items_per_round), _ptr(items), _ptr(off),
+                                           ctypes.byref(nlev))
+    else:
+        rc = lib.pt_make_schedule(ctypes.byref(inst), _ptr(items), _ptr(off), ctypes.byref(nlev))
     if rc != PT_OK:
         raise PTError(rc, "pt_make_schedule rejected its arguments")
     return items, off[: nlev.value + 1]

@@ -97,6 +97,60 @@ def _check_schedule(n, ei, ej):
     return off.size - 1
 
 
+def _levels(items, off):
+    level = np.empty(items.size, np.int64)
+    for l in range(off.size - 1):
+        level[items[off[l]:off[l + 1]]] = l
+    return level
+
+
+def _rounds(off, per_round):
+    return int(sum(-(-int(c) // per_round) for c in np.diff(off)))
+
+
+@pytest.mark.parametrize("name,per_round,expect", [("regular3_n256_p64_r64", 48, 12),
+                                                   ("chimera16_n2048_p128_r96", 32, 128),
+                                                   ("regular3_n16_p32_r16", 96, 6)])
+def test_balanced_schedule_keeps_dependencies_and_level_count(name, per_round, expect):
+    """Rebalanced levels: a permutation of the updates, every dependency strictly earlier,
+    the same level count as the as-early-as-possible schedule, and fewer kernel rounds
+    (N=256: 16 -> 12 rounds of 48; the K4,4 lattice: 144 -> 128 rounds of 32, the bound
+    4096 / 32)."""
+    prob = instances.workload(name, 1)
+    n = prob.n
+    items0, off0 = pt.make_schedule(n, prob.ei, prob.ej)
+    items, off = pt.make_schedule(n, prob.ei, prob.ej, items_per_round=per_round)
+    assert sorted(items.tolist()) == list(range(2 * n))
+    assert off.size == off0.size
+    level = _levels(items, off)
+    adj = [set() for _ in range(n)]
+    for a, b in zip(prob.ei, prob.ej):
+        adj[a].add(b)
+        adj[b].add(a)
+    for i in range(n):
+        assert level[2 * i] < level[2 * i + 1]
+        for j in adj[i]:
+            if j < i:
+                assert level[2 * j] < level[2 * i]
+                assert level[2 * j + 1] < level[2 * i + 1]
+    assert _rounds(off, per_round) <= _rounds(off0, per_round)
+    assert _rounds(off, per_round) == expect
+
+
+def test_balanced_schedule_degenerate_graphs():
+    # no edges: two levels whatever the round size; a path: fully sequential, nothing to move
+    for per_round in (1, 3, 100):
+        items, off = pt.make_schedule(5, [], [], items_per_round=per_round)
+        assert off.size == 3 and sorted(items.tolist()) == list(range(10))
+        n = 6
+        items, off = pt.make_schedule(n, list(range(n - 1)), list(range(1, n)), items_per_round=per_round)
+        assert off.size - 1 == n + 1
+        level = _levels(items, off)
+        assert all(level[2 * i] == i and level[2 * i + 1] == i + 1 for i in range(n))
+    with pytest.raises(pt.PTError):
+        pt.make_schedule(4, [0], [1], items_per_round=-1)
+
+
 def test_schedule_respects_sequential_order():
     for name in ("regular3_n16_p32_r16", "regular3_n256_p64_r64", "chimera16_n2048_p128_r96"):
         prob = instances.workload(name, 1)
