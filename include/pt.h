@@ -89,7 +89,13 @@ typedef struct {
     int32_t cluster_size;       /* batched launches: CTAs per thread-block cluster (1..16), or
                                    0 = autotune (pt_batch_create times a short run of each
                                    layout and keeps the fastest; results never depend on it) */
-    int32_t reserved[4];
+    int32_t no_autotune;        /* 0: when kernel_path and threads_per_block are automatic and
+                                   the chains are int8 in shared memory, pt_create times a
+                                   short run of each candidate plan (paths 2, 3 and 5, block
+                                   sizes 256-512), keeps the fastest and resets the context
+                                   to its initial state; the choice is remembered per shape
+                                   for the process. Results never depend on it. 1: off. */
+    int32_t reserved[3];
 } pt_options;
 
 /* Statistics (Fig. 4 "gather statistics"; Sec. 5 accumulates in high precision).
@@ -121,6 +127,8 @@ typedef struct {
     int64_t device_bytes;      /* device memory held by the context */
     int64_t kernel_launches;   /* kernels this context has launched so far */
     int64_t h2d_bytes;         /* bytes copied host -> device so far */
+    int32_t tuned_plans;       /* candidate plans timed by pt_create (0: none, or cached) */
+    int32_t reserved;
 } pt_info;
 
 /* Create a PT-QMC problem on the current CUDA device (Sec. 2: chains and temperatures

@@ -10,6 +10,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "pt.h"
@@ -40,7 +43,21 @@ struct pt_ctx {
     int64_t device_bytes;
     int64_t launches;            // kernels launched by this context
     int64_t h2d_bytes;           // bytes copied host -> device
+    int tuned_plans;             // candidate plans timed at create
 };
+
+// Plans chosen by the create-time autotuner, per problem shape, for the process.
+struct PlanKey {
+    int N, P, R, dc, n_levels, n_edges;
+    bool operator<(const PlanKey& o) const {
+        return std::tie(N, P, R, dc, n_levels, n_edges) < std::tie(o.N, o.P, o.R, o.dc, o.n_levels, o.n_edges);
+    }
+};
+struct PlanChoice {
+    int path, threads, producers;
+};
+static std::mutex g_plan_mutex;
+static std::map<PlanKey, PlanChoice> g_plan_cache;
 
 static thread_local char g_create_msg[256] = "";
 
@@ -617,6 +634,151 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         return create_fail(PT_EINVAL, "the split kernel needs all %d chains resident at once (%lld fit)", R,
                            resident);
     }
+
+    // Plan autotuning. When the path and the block size are automatic and the chains are
+    // int8 in shared memory, each candidate plan (producer-warp kernel, inline-word kernel
+    // with 256, 384 or 512 threads, split kernel) sweeps a short stretch of one continuous
+    // run, and the fastest is kept. Results do not depend on the plan; the context is then
+    // reset to its initial state. The choice is cached per problem shape for the process.
+    const bool tune = want_path == 0 && want_threads == 0 && !(opt && opt->no_autotune) && c->cooperative &&
+                      R > 1 && (path == kPathPacked || path == kPathPackedInline || path == kPathSplit);
+    if (tune) {
+        struct Cand {
+            int path, threads, producers;
+        };
+        const PlanKey key{N, P, R, packed_dc, p.n_levels, nE};
+        std::vector<Cand> cands;
+        {
+            std::lock_guard<std::mutex> lock(g_plan_mutex);
+            auto it = g_plan_cache.find(key);
+            if (it != g_plan_cache.end()) cands.push_back({it->second.path, it->second.threads, it->second.producers});
+        }
+        const bool cached = !cands.empty();
+        if (!cached) {
+            if (fits(kPathPacked)) cands.push_back({kPathPacked, 512, 128});
+            if (split_fits()) cands.push_back({kPathSplit, 512, 128});
+            if (fits(kPathPackedInline))
+                for (int th : {256, 384, 512}) cands.push_back({kPathPackedInline, th, 0});
+        }
+        // a candidate's plan, shared-memory flags and level schedule
+        auto make = [&](const Cand& cd, LaunchPlan& pl, DevProblem& pc, std::vector<uint32_t>& it_c,
+                        std::vector<int32_t>& off_c) {
+            pc = p;
+            pc.acc_in_smem = (size_t)R * kAccCount * 8 <= 16384 ? 1 : 0;
+            pc.tables_in_smem = (size_t)R * p.nL3 * 4 <= 49152 ? 1 : 0;
+            if (pc.tables_in_smem && sweep_smem_bytes(pc, cd.path, packed_dc) > (size_t)max_smem) pc.tables_in_smem = 0;
+            if (pc.acc_in_smem && sweep_smem_bytes(pc, cd.path, packed_dc) > (size_t)max_smem) pc.acc_in_smem = 0;
+            pl.path = cd.path;
+            pl.dclass = packed_dc;
+            pl.threads = cd.threads;
+            pl.n_consumer = cd.threads - cd.producers;
+            pl.smem_bytes = sweep_smem_bytes(pc, cd.path, packed_dc);
+            int cols = 1;
+            if (cd.path == kPathSplit) {
+                cols = P / 16 + 1;
+            } else {
+                while (cols < P / 8) cols <<= 1;
+            }
+            level_schedule(N, adj, it_c, off_c, std::max(1, pl.n_consumer / cols));
+            return pl.smem_bytes <= (size_t)max_smem;
+        };
+        cudaStream_t s = c->stream;
+        int best = -1, timed_plans = 0;
+        if (cands.size() == 1) {
+            best = 0;
+        } else if (cands.size() > 1) {
+            cudaEvent_t ev[2];
+            cudaEventCreate(&ev[0]);
+            cudaEventCreate(&ev[1]);
+            float best_ms = 1e30f;
+            long long t = 0, q = 0;
+            const int warm = 4, timed = std::min(24, c->max_passes);
+            for (size_t k = 0; k < cands.size(); ++k) {
+                LaunchPlan pl;
+                DevProblem pc;
+                std::vector<uint32_t> it_c;
+                std::vector<int32_t> off_c;
+                if (!make(cands[k], pl, pc, it_c, off_c)) continue;
+                long long res = 0;
+                if (prepare_sweep_kernel(pl) != cudaSuccess || sweep_resident_chains(pc, pl, &res) != cudaSuccess ||
+                    res < R) {
+                    (void)cudaGetLastError();
+                    continue;
+                }
+                cudaError_t e1 = cudaMemcpyAsync(d_items, it_c.data(), it_c.size() * 4, cudaMemcpyHostToDevice, s);
+                if (e1 == cudaSuccess)
+                    e1 = cudaMemcpyAsync(d_loff, off_c.data(), off_c.size() * 4, cudaMemcpyHostToDevice, s);
+                if (e1 == cudaSuccess) e1 = launch_sweeps(pc, pl, t, q, warm, 1, c->timeout_ns, true, s);
+                if (e1 == cudaSuccess) e1 = cudaEventRecord(ev[0], s);
+                if (e1 == cudaSuccess) e1 = launch_sweeps(pc, pl, t + warm, q + warm, timed, 1, c->timeout_ns, true, s);
+                if (e1 == cudaSuccess) e1 = cudaEventRecord(ev[1], s);
+                if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(s);
+                int status = 0;
+                if (e1 == cudaSuccess) e1 = cudaMemcpy(&status, p.status, sizeof(int), cudaMemcpyDeviceToHost);
+                if (e1 != cudaSuccess || status != 0) {
+                    cudaEventDestroy(ev[0]);
+                    cudaEventDestroy(ev[1]);
+                    free_ctx(c);
+                    return create_fail(e1 != cudaSuccess ? PT_ECUDA : status, "plan autotuning: %s",
+                                       e1 != cudaSuccess ? cudaGetErrorString(e1) : "a device wait gave up");
+                }
+                c->launches += 2;
+                t += warm + timed;
+                q += warm + timed;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[0], ev[1]);
+                ++timed_plans;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = (int)k;
+                }
+            }
+            cudaEventDestroy(ev[0]);
+            cudaEventDestroy(ev[1]);
+        }
+        if (best >= 0) {
+            LaunchPlan pl;
+            DevProblem pc;
+            if (make(cands[best], pl, pc, items, level_off)) {
+                long long res = 0;
+                if (prepare_sweep_kernel(pl) == cudaSuccess && sweep_resident_chains(pc, pl, &res) == cudaSuccess &&
+                    res >= R) {
+                    c->plan = pl;
+                    p.acc_in_smem = pc.acc_in_smem;
+                    p.tables_in_smem = pc.tables_in_smem;
+                    if (!cached) {
+                        std::lock_guard<std::mutex> lock(g_plan_mutex);
+                        g_plan_cache[key] = PlanChoice{cands[best].path, cands[best].threads, cands[best].producers};
+                    }
+                }
+                (void)cudaGetLastError();
+            }
+            c->tuned_plans = timed_plans;
+        }
+        // the chosen plan's schedule, and the initial state again
+#define TUNE_CUDA(call)                                                              \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            cudaStreamSynchronize(s);                                                \
+            free_ctx(c);                                                             \
+            return create_fail(PT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+        }                                                                            \
+    } while (0)
+        TUNE_CUDA(prepare_sweep_kernel(c->plan));
+        TUNE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s));
+        TUNE_CUDA(cudaMemcpyAsync(d_loff, level_off.data(), level_off.size() * 4, cudaMemcpyHostToDevice, s));
+        if (timed_plans > 0) {
+            TUNE_CUDA(cudaMemsetAsync(p.acc, 0, (size_t)R * kAccCount * 8, s));
+            TUNE_CUDA(cudaMemsetAsync(p.swap_stats, 0, 2 * (size_t)R * 8, s));
+            TUNE_CUDA(cudaMemsetAsync(p.mbox, 0, (size_t)max_passes * R * sizeof(Mailbox), s));
+            TUNE_CUDA(launch_init(p, s));
+            TUNE_CUDA(launch_energy(p, s));
+            c->launches += 2;
+        }
+        TUNE_CUDA(cudaStreamSynchronize(s));
+#undef TUNE_CUDA
+    }
     *out = c;
     return PT_OK;
 }
@@ -850,6 +1012,8 @@ extern "C" int pt_get_info(const pt_ctx* c, pt_info* o) {
     o->device_bytes = c->device_bytes;
     o->kernel_launches = c->launches;
     o->h2d_bytes = c->h2d_bytes;
+    o->tuned_plans = c->tuned_plans;
+    o->reserved = 0;
     return PT_OK;
 }
 
