@@ -48,7 +48,7 @@ KERNEL_NAMES = {1: "sweep_kernel (byte-wise)", 2: "sweep_packed_kernel (int8, in
 # DRAM bytes (read + write) per launch of the sweep kernel, from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum: (workload, kernel path, sweeps per launch)
 # -> bytes. Must be retaken (or removed) whenever that kernel changes.
-MEASURED_TRAFFIC = {("regular3_n256_p64_r64", 3, 1000): 1637248}
+MEASURED_TRAFFIC = {}
 # The same for the batched launch: (requests, sweeps each) -> DRAM bytes per launch.
 MEASURED_BATCH_TRAFFIC = {(512, 1000): 1297127729664 + 1345044210688}
 
@@ -61,6 +61,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="regular3_n256_p64_r64")
     ap.add_argument("--sweeps", type=int, default=0, help="override sweeps per step (profiling runs)")
+    ap.add_argument("--kernel-path", type=int, default=0,
+                    help="force the main context's kernel path (profiling runs; 0 = autotuned at create)")
+    ap.add_argument("--threads-per-block", type=int, default=0, help="force its block size (with --kernel-path)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -178,7 +181,8 @@ def run_ours(args, rank, world, local_rank):
     # a dedicated stream: the library launches on it and the CUDA events are recorded on it
     stream = torch.cuda.Stream()
     assert stream.cuda_stream != 0
-    ctx = pt.PT.from_problem(prob, stream=stream.cuda_stream)
+    ctx = pt.PT.from_problem(prob, stream=stream.cuda_stream, kernel_path=args.kernel_path,
+                             threads_per_block=args.threads_per_block)
     info = ctx.info
 
     def step():
@@ -256,7 +260,8 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed between timed steps (512 MB write outside the events)",
                    "parallelism": "one independent problem per GPU" if world > 1 else "single GPU",
                    "threads_per_block": info.threads_per_block, "levels_per_sweep": info.n_levels,
-                   "cooperative_swaps": bool(info.cooperative)},
+                   "cooperative_swaps": bool(info.cooperative), "kernel_path": int(info.kernel_path),
+                   "plans_timed_at_create": int(info.tuned_plans)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
                      "frac": achieved / peak,
                      "traffic": MEASURED_TRAFFIC.get((args.workload, int(info.kernel_path),

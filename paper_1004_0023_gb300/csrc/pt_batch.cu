@@ -731,7 +731,11 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
     std::vector<Prepared> pr(count);
     char why[200];
     for (int k = 0; k < count; ++k) {
-        const int rc = prepare_request(reqs[k], pr[k], why, sizeof(why));
+        // levels balanced for one-warp chain groups (the default and the usual autotuned
+        // width): 32 threads over the power-of-two word columns of an item
+        int cols = 1;
+        while (cols < reqs[k].P / 8) cols <<= 1;
+        const int rc = prepare_request(reqs[k], pr[k], why, sizeof(why), reqs[k].P >= 8 ? std::max(1, 32 / cols) : 0);
         if (rc) return bfail(nullptr, rc, "request %d: %s", k, why);
     }
     if (opt && (opt->cluster_size < 0 || opt->cluster_size > 16))

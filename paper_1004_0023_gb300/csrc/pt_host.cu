@@ -641,7 +641,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     // run, and the fastest is kept. Results do not depend on the plan; the context is then
     // reset to its initial state. The choice is cached per problem shape for the process.
     const bool tune = want_path == 0 && want_threads == 0 && !(opt && opt->no_autotune) && c->cooperative &&
-                      R > 1 && (path == kPathPacked || path == kPathPackedInline || path == kPathSplit);
+                      R > 1 && p.withhold_rung < 0 && !p.exact_swaps &&
+                      (path == kPathPacked || path == kPathPackedInline || path == kPathSplit);
     if (tune) {
         struct Cand {
             int path, threads, producers;
@@ -687,12 +688,15 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         if (cands.size() == 1) {
             best = 0;
         } else if (cands.size() > 1) {
-            cudaEvent_t ev[2];
+            // per-sweep cost = (time of a long launch - time of a short one) / the sweep
+            // difference, so that a kernel's per-launch setup does not count
+            cudaEvent_t ev[3];
             cudaEventCreate(&ev[0]);
             cudaEventCreate(&ev[1]);
+            cudaEventCreate(&ev[2]);
             float best_ms = 1e30f;
             long long t = 0, q = 0;
-            const int warm = 4, timed = std::min(24, c->max_passes);
+            const int warm = 4, shortn = 4, longn = std::min(36, c->max_passes);
             for (size_t k = 0; k < cands.size(); ++k) {
                 LaunchPlan pl;
                 DevProblem pc;
@@ -710,31 +714,43 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                     e1 = cudaMemcpyAsync(d_loff, off_c.data(), off_c.size() * 4, cudaMemcpyHostToDevice, s);
                 if (e1 == cudaSuccess) e1 = launch_sweeps(pc, pl, t, q, warm, 1, c->timeout_ns, true, s);
                 if (e1 == cudaSuccess) e1 = cudaEventRecord(ev[0], s);
-                if (e1 == cudaSuccess) e1 = launch_sweeps(pc, pl, t + warm, q + warm, timed, 1, c->timeout_ns, true, s);
+                if (e1 == cudaSuccess) e1 = launch_sweeps(pc, pl, t + warm, q + warm, shortn, 1, c->timeout_ns, true, s);
                 if (e1 == cudaSuccess) e1 = cudaEventRecord(ev[1], s);
+                if (e1 == cudaSuccess)
+                    e1 = launch_sweeps(pc, pl, t + warm + shortn, q + warm + shortn, longn, 1, c->timeout_ns, true, s);
+                if (e1 == cudaSuccess) e1 = cudaEventRecord(ev[2], s);
                 if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(s);
                 int status = 0;
                 if (e1 == cudaSuccess) e1 = cudaMemcpy(&status, p.status, sizeof(int), cudaMemcpyDeviceToHost);
+                c->launches += 3;
+                t += warm + shortn + longn;
+                q += warm + shortn + longn;
                 if (e1 != cudaSuccess || status != 0) {
-                    cudaEventDestroy(ev[0]);
-                    cudaEventDestroy(ev[1]);
-                    free_ctx(c);
-                    return create_fail(e1 != cudaSuccess ? PT_ECUDA : status, "plan autotuning: %s",
-                                       e1 != cudaSuccess ? cudaGetErrorString(e1) : "a device wait gave up");
+                    // a candidate that reports an error ends the tuning (the best plan timed so
+                    // far, or the fixed one, is kept; every sweep is undone below); an error that
+                    // outlives the launch ends the create
+                    (void)cudaGetLastError();
+                    if (cudaStreamSynchronize(s) != cudaSuccess ||
+                        cudaMemsetAsync(p.status, 0, sizeof(int), s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess) {
+                        for (cudaEvent_t x : ev) cudaEventDestroy(x);
+                        free_ctx(c);
+                        return create_fail(PT_ECUDA, "plan autotuning: %s", cudaGetErrorString(cudaGetLastError()));
+                    }
+                    ++timed_plans;
+                    break;
                 }
-                c->launches += 2;
-                t += warm + timed;
-                q += warm + timed;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, ev[0], ev[1]);
+                float ms_short = 0.f, ms_long = 0.f;
+                cudaEventElapsedTime(&ms_short, ev[0], ev[1]);
+                cudaEventElapsedTime(&ms_long, ev[1], ev[2]);
+                const float ms = (ms_long - ms_short) / (float)(longn - shortn);
                 ++timed_plans;
                 if (ms < best_ms) {
                     best_ms = ms;
                     best = (int)k;
                 }
             }
-            cudaEventDestroy(ev[0]);
-            cudaEventDestroy(ev[1]);
+            for (cudaEvent_t x : ev) cudaEventDestroy(x);
         }
         if (best >= 0) {
             LaunchPlan pl;

@@ -384,6 +384,7 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
 __device__ __forceinline__ void produce_words(uint4* buf, uint32_t t, const uint32_t* s_items, int n_items, int G,
                                               int lg, int gmask, int ptid, int np, uint32_t slot,
                                               const PhiloxKey& key) {
+    if (ptid < 0 || np <= 0) return;  // producer threads only
     const int total = n_items << lg;
     for (int x = ptid; x < total; x += np) {
         const int g = x & gmask;
@@ -473,7 +474,7 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     const int gmask = (1 << lg) - 1;
     const uint32_t* thr_c = thr_row(p, s_thr, rung) + 3 * p.Lmax;
     const int n_items = 2 * N;
-    const int lane = tid & 31, warp = tid >> 5;
+    const int lane = tid & 31;
     if (tid == 0) {
         s_ctl[4] = -1;  // partner rung of the pending swap pass
         s_ctl[5] = 0;   // a swap wait gave up
@@ -564,7 +565,8 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
                 side = eos_publish(p, rung, E, M, sE, sM, pass, q0, qmod0);
                 s_ctl[4] = side.active ? side.partner : -1;
             }
-        } else if (s + 1 < n_sweeps) {
+        } else if (PRE && !consumer && s + 1 < n_sweeps) {
+            // producer warps only: a consumer whose swap wait gave up skips to the barrier below
             produce_words(rbuf + (size_t)((s + 1) & 1) * n_items * G, t + 1u, s_items, n_items, G, lg, gmask,
                           tid - NC, nt - NC, (uint32_t)slot, key);
         }
@@ -766,11 +768,17 @@ __device__ __forceinline__ UnitOffsets split_offsets(int g, int W, int b) {
 }
 
 template <int DC>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 1)
 sweep_split_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
                    long long timeout_ns, int n_consumer) {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
+    // the cluster shape is compiled in; should a launch ever run without it, no CTA touches
+    // a peer's shared memory or waits at a cluster barrier
+    if (cluster.num_blocks() != 2) {
+        if (threadIdx.x == 0) atomicCAS(p.status, 0, PT_ECUDA);
+        return;
+    }
     const int h = (int)cluster.block_rank();
     const bool lead = h == 0;
     const int slot = blockIdx.x >> 1;
@@ -1171,7 +1179,8 @@ cudaError_t sweep_kernel_occupancy(const DevProblem& p, const LaunchPlan& plan, 
                                                          plan.smem_bytes);
 }
 
-// The split kernel's launch: R clusters of two CTAs; cooperative when swap passes run inside.
+// The split kernel's launch: R clusters of two CTAs (the cluster shape is compiled into the
+// kernel); cooperative when swap passes run inside.
 static cudaLaunchConfig_t split_config(const DevProblem& p, const LaunchPlan& plan, bool cooperative,
                                        cudaStream_t s, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
@@ -1179,14 +1188,10 @@ static cudaLaunchConfig_t split_config(const DevProblem& p, const LaunchPlan& pl
     cfg.blockDim = dim3(plan.threads);
     cfg.dynamicSmemBytes = plan.smem_bytes;
     cfg.stream = s;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeCooperative;
-    attr[1].val.cooperative = 1;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = cooperative ? 2 : 1;
+    cfg.numAttrs = cooperative ? 1 : 0;
     return cfg;
 }
 

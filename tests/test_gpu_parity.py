@@ -331,11 +331,14 @@ def test_invalid_arguments_are_rejected():
     g.run(10, 1)  # still usable after argument errors
 
 
-def test_partner_that_never_publishes_times_out_without_fault():
+@pytest.mark.parametrize("path", [0, 1, 2, 3, 4])
+def test_partner_that_never_publishes_times_out_without_fault(path):
     """The chain on rung 3 withholds its mailbox: its partner's bounded wait runs out, the
-    call reports PT_ETIMEDOUT, and the device stays usable for a new context."""
+    call reports PT_ETIMEDOUT, and the device stays usable for a new context. On every
+    one-CTA kernel, with sweeps left after the one whose wait gave up: the CTA that gave up
+    leaves at the next barrier without touching its random-word buffers."""
     prob = instances.workload("regular3_n16_p32_r16", 5)
-    g = pt.PT.from_problem(prob, wait_timeout_ms=200, test_withhold_rung=3, swap_mode=1)
+    g = pt.PT.from_problem(prob, wait_timeout_ms=200, test_withhold_rung=3, swap_mode=1, kernel_path=path)
     g.run(4, 1)
     with pytest.raises(pt.PTError) as e:
         g.sync()
