@@ -48,9 +48,9 @@ KERNEL_NAMES = {1: "sweep_kernel (byte-wise)", 2: "sweep_packed_kernel (int8, in
 # DRAM bytes (read + write) per launch of the sweep kernel, from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum: (workload, kernel path, sweeps per launch)
 # -> bytes. Must be retaken (or removed) whenever that kernel changes.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {("regular3_n256_p64_r64", 2, 1000): (1554944 + 1722880) // 2}
 # The same for the batched launch: (requests, sweeps each) -> DRAM bytes per launch.
-MEASURED_BATCH_TRAFFIC = {(512, 1000): 1297127729664 + 1345044210688}
+MEASURED_BATCH_TRAFFIC = {(512, 1000): 1298192722688 + 1345140493056}
 
 
 def parse_args(argv=None):
@@ -309,6 +309,7 @@ def run_batched(args, pt, instances, torch, n_sm, sm_max):
     for p in probs:
         ctxs.append(pt.PT.from_problem(p, stream=stream.cuda_stream))
     torch.cuda.synchronize()
+    launches0 = sum(int(c.get_info().kernel_launches) for c in ctxs)  # create (and plan timing) excluded
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record(stream)
     for c, p in zip(ctxs, probs):
@@ -316,7 +317,7 @@ def run_batched(args, pt, instances, torch, n_sm, sm_max):
     p1.record(stream)
     torch.cuda.synchronize()
     plain_ms = p0.elapsed_time(p1)
-    plain_launches = sum(int(c.get_info().kernel_launches) for c in ctxs)
+    plain_launches = sum(int(c.get_info().kernel_launches) for c in ctxs) - launches0
     for c in ctxs:
         c.close()
     value = attempts / (ms / 1e3)

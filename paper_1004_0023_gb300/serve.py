@@ -89,7 +89,9 @@ def replay_batched(trace, quantum_sweeps=100, max_active=512, arena_bytes=0, clu
 
 
 def replay_plain(trace, stream=None, deadline=None):
-    """One request at a time: pt_create + pt_run + read, in arrival order."""
+    """One request at a time: pt_create + pt_run + read, in arrival order. Plan timing at
+    create is off: a one-off request of 500-5000 sweeps would spend a large share of its run
+    timing candidate plans for a shape it never sees again."""
     t0 = time.perf_counter()
     lat, att, launches = [], 0, 0
     k = 0
@@ -99,7 +101,7 @@ def replay_plain(trace, stream=None, deadline=None):
             break
         if arr > now:
             time.sleep(arr - now)
-        ctx = pt.PT.from_problem(prob, stream=stream)
+        ctx = pt.PT.from_problem(prob, stream=stream, no_autotune=1)
         ctx.run(prob.n_sweeps, prob.sweeps_per_swap)
         ctx.read_state()
         ctx.obs()
