@@ -82,7 +82,8 @@ typedef struct {
                                    degree <= 7), 5 = path 3 with each chain split over a
                                    cluster of two CTAs, one half of the Trotter copies each
                                    (needs P % 16 == 0 and all R chains resident at once;
-                                   for short ladders that leave SMs idle) */
+                                   for short ladders that leave SMs idle), 6 = path 5 with
+                                   the random words computed inline (no producer warps) */
     int32_t producer_threads;   /* paths 3 and 5: threads producing random words (0 = auto) */
     int32_t test_exact_swaps;   /* test hook: 1 = skip the FP32 pre-decision of swaps and always
                                    evaluate the FP64 rule (results are identical either way) */
@@ -91,8 +92,8 @@ typedef struct {
                                    layout and keeps the fastest; results never depend on it) */
     int32_t no_autotune;        /* 0: when kernel_path and threads_per_block are automatic and
                                    the chains are int8 in shared memory, pt_create times a
-                                   short run of each candidate plan (paths 2, 3 and 5, block
-                                   sizes 256-512), keeps the fastest and resets the context
+                                   short run of each candidate plan (paths 2, 3, 5 and 6,
+                                   block sizes 256-512), keeps the fastest and resets the context
                                    to its initial state; the choice is remembered per shape
                                    for the process. Results never depend on it. 1: off. */
     int32_t reserved[3];

@@ -427,10 +427,13 @@ struct UnitOffsets {
     uint32_t own[2], opp[2], edge[2];
 };
 
-// The packed unit evaluated from precomputed row offsets (the split kernel's rows).
-template <int DC>
+// The packed unit evaluated from precomputed row offsets (the split kernel's rows). PRE: the
+// random words are read from *rbq; else word w of philox((t, i, slot, p<<24 | gg)), gg the
+// unit's 8-copy chunk in the whole chain.
+template <int DC, bool PRE>
 __device__ __forceinline__ UnitEval split_unit_eval(int8_t* sp, const uint32_t* s_sdesc, uint32_t item,
-                                                    const uint4* rbq, const UnitOffsets& o) {
+                                                    const uint4* rbq, const UnitOffsets& o, uint32_t t,
+                                                    uint32_t slot, uint32_t gg, const PhiloxKey& key) {
     UnitEval e;
     const uint32_t par = item & 1u;
     const uint32_t* desc = s_sdesc + (item >> 1) * SiteDesc<DC>::DW;
@@ -462,7 +465,7 @@ __device__ __forceinline__ UnitEval split_unit_eval(int8_t* sp, const uint32_t* 
     uint32_t a[DC];
 #pragma unroll
     for (int d = 0; d < DC; ++d) a[d] = *reinterpret_cast<const uint32_t*>(sp + nrow[d] + own_off);
-    const uint4 r4 = *rbq;
+    const uint4 r4 = PRE ? *rbq : philox(make_uint4(t, d0.y, slot, (par << 24) | gg), key);
     e.u[0] = r4.x;
     e.u[1] = r4.y;
     e.u[2] = r4.z;

@@ -402,16 +402,16 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     const int packed_dc = (dmax + 1 <= 4) ? 4 : ((dmax + 1 <= 8) ? 8 : 0);
     const bool packed_ok = (P % 8 == 0) && packed_dc > 0;
     const int want_path = opt ? opt->kernel_path : 0;
-    if (want_path < 0 || want_path > 5) {
+    if (want_path < 0 || want_path > 6) {
         free_ctx(c);
-        return create_fail(PT_EINVAL, "kernel_path must be 0..5");
+        return create_fail(PT_EINVAL, "kernel_path must be 0..6");
     }
     if ((want_path == kPathPacked || want_path == kPathPackedInline || want_path == kPathBits ||
-         want_path == kPathSplit) && !packed_ok) {
+         want_path == kPathSplit || want_path == kPathSplitInline) && !packed_ok) {
         free_ctx(c);
         return create_fail(PT_EINVAL, "the packed kernel needs P %% 8 == 0 and degree <= 7");
     }
-    if (want_path == kPathSplit && P % 16 != 0) {
+    if ((want_path == kPathSplit || want_path == kPathSplitInline) && P % 16 != 0) {
         free_ctx(c);
         return create_fail(PT_EINVAL, "the split kernel needs P %% 16 == 0");
     }
@@ -432,18 +432,18 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     };
     // the split kernel when a chain and its produced random words do not fit one CTA but do
     // fit two, and every chain's cluster can be resident at once
-    auto split_fits = [&]() {
-        if (P % 16 != 0 || !(want_threads == 0 || (want_threads >= 64 && want_threads <= 512)) || !fits(kPathSplit))
+    auto split_fits = [&](int spath = kPathSplit) {
+        if (P % 16 != 0 || !(want_threads == 0 || (want_threads >= 64 && want_threads <= 512)) || !fits(spath))
             return false;
         DevProblem q = p;
-        if (sweep_smem_bytes(q, kPathSplit, packed_dc) > (size_t)max_smem) q.tables_in_smem = 0;
-        if (sweep_smem_bytes(q, kPathSplit, packed_dc) > (size_t)max_smem) q.acc_in_smem = 0;
+        if (sweep_smem_bytes(q, spath, packed_dc) > (size_t)max_smem) q.tables_in_smem = 0;
+        if (sweep_smem_bytes(q, spath, packed_dc) > (size_t)max_smem) q.acc_in_smem = 0;
         LaunchPlan probe;
-        probe.path = kPathSplit;
+        probe.path = spath;
         probe.dclass = packed_dc;
         probe.threads = want_threads > 0 ? want_threads : 512;
-        probe.n_consumer = probe.threads - probe.threads / 4;
-        probe.smem_bytes = sweep_smem_bytes(q, kPathSplit, packed_dc);
+        probe.n_consumer = spath == kPathSplit ? probe.threads - probe.threads / 4 : probe.threads;
+        probe.smem_bytes = sweep_smem_bytes(q, spath, packed_dc);
         long long resident = 0;
         if (prepare_sweep_kernel(probe) != cudaSuccess || sweep_resident_chains(q, probe, &resident) != cudaSuccess) {
             (void)cudaGetLastError();
@@ -476,13 +476,13 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                            c->plan.smem_bytes, max_smem);
     }
     if (opt && opt->threads_per_block > 0) {
-        const int tmax = (path == kPathGeneric || path == kPathSplit) ? 512 : 1024;
+        const int tmax = (path == kPathGeneric || path == kPathSplit || path == kPathSplitInline) ? 512 : 1024;
         if (opt->threads_per_block % 32 || opt->threads_per_block > tmax) {
             free_ctx(c);
             return create_fail(PT_EINVAL, "threads_per_block must be a multiple of 32 <= %d for this kernel", tmax);
         }
         c->plan.threads = opt->threads_per_block;
-    } else if (path == kPathPacked || path == kPathSplit) {
+    } else if (path == kPathPacked || path == kPathSplit || path == kPathSplitInline) {
         c->plan.threads = 512;
     } else {
         // enough threads for the average level (units = items * padded groups per parity)
@@ -509,13 +509,17 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                                P / 16 + 1);
         }
     }
+    if (path == kPathSplitInline && c->plan.threads < P / 16 + 1) {
+        free_ctx(c);
+        return create_fail(PT_EINVAL, "the split kernel needs at least P/16 + 1 = %d threads", P / 16 + 1);
+    }
 
     // the levels, rebalanced for the items this plan's kernel takes per round: consumer
     // threads over word columns per item (a power of two for the one-CTA kernels, W + 1 for
     // the split one); the level count and the dependencies stay the same
     {
         int cols = 1;
-        if (path == kPathSplit) {
+        if (path == kPathSplit || path == kPathSplitInline) {
             cols = P / 16 + 1;
         } else {
             const int G = (path == kPathGeneric) ? ((P / 2) + 3) / 4 : P / 8;
@@ -628,7 +632,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         return create_fail(PT_EINVAL, "swap_mode 1 needs all %d chains resident at once (%lld fit on %d SMs)", R,
                            resident, n_sm);
     }
-    if (path == kPathSplit && resident < R) {
+    if ((path == kPathSplit || path == kPathSplitInline) && resident < R) {
         // the two CTAs of a chain always run together, but the swap passes need every chain
         free_ctx(c);
         return create_fail(PT_EINVAL, "the split kernel needs all %d chains resident at once (%lld fit)", R,
@@ -658,6 +662,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         if (!cached) {
             if (fits(kPathPacked)) cands.push_back({kPathPacked, 512, 128});
             if (split_fits()) cands.push_back({kPathSplit, 512, 128});
+            if (split_fits(kPathSplitInline))
+                for (int th : {384, 512}) cands.push_back({kPathSplitInline, th, 0});
             if (fits(kPathPackedInline))
                 for (int th : {256, 384, 512}) cands.push_back({kPathPackedInline, th, 0});
         }
@@ -675,7 +681,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             pl.n_consumer = cd.threads - cd.producers;
             pl.smem_bytes = sweep_smem_bytes(pc, cd.path, packed_dc);
             int cols = 1;
-            if (cd.path == kPathSplit) {
+            if (cd.path == kPathSplit || cd.path == kPathSplitInline) {
                 cols = P / 16 + 1;
             } else {
                 while (cols < P / 8) cols <<= 1;

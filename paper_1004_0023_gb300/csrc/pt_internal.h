@@ -64,7 +64,7 @@ struct DevProblem {
 // Sweep kernel variants: byte-wise (any shape), packed with Philox inline, packed with the
 // random words produced one sweep ahead by dedicated warps, bit-packed, and the produced-words
 // kernel with each chain split over a cluster of two CTAs.
-enum { kPathGeneric = 1, kPathPackedInline = 2, kPathPacked = 3, kPathBits = 4, kPathSplit = 5 };
+enum { kPathGeneric = 1, kPathPackedInline = 2, kPathPacked = 3, kPathBits = 4, kPathSplit = 5, kPathSplitInline = 6 };
 
 struct LaunchPlan {
     int path;            // kPath*

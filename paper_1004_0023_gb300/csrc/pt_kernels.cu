@@ -83,11 +83,11 @@ struct FastLayout {
     }
 };
 
-size_t split_smem_bytes(const DevProblem& p, int dclass);
+size_t split_smem_bytes(const DevProblem& p, int dclass, bool pre);
 
 size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass) {
     if (path == kPathGeneric) return GenericLayout(p).total;
-    if (path == kPathSplit) return split_smem_bytes(p, dclass);
+    if (path == kPathSplit || path == kPathSplitInline) return split_smem_bytes(p, dclass, path == kPathSplit);
     return FastLayout(p, dclass, path == kPathPacked, path == kPathBits).total;
 }
 
@@ -721,7 +721,7 @@ cudaError_t launch_multi(const MultiProblem* probs, const int2* map, int n_block
 struct SplitLayout {
     size_t spins, desc, items, loff, thr, acc, red, ctl, xch, rbuf, total;
     int W, RB, Gc;
-    __host__ __device__ SplitLayout(const DevProblem& p, int dc) {
+    __host__ __device__ SplitLayout(const DevProblem& p, int dc, bool pre) {
         const int N = p.N;
         W = p.P / 16;
         RB = 8 * W + 16;
@@ -736,12 +736,13 @@ struct SplitLayout {
         red = o;   o += 32 * 3 * 8;
         ctl = o;   o += 32;
         xch = o;   o += 64;  // written by the peer: [sweep parity][dE, dM, flips, abort], final abort
-        rbuf = o;  o += (size_t)2 * (2 * N) * Gc * 16;
+        rbuf = o;
+        if (pre) o += (size_t)2 * (2 * N) * Gc * 16;
         total = o;
     }
 };
 
-size_t split_smem_bytes(const DevProblem& p, int dclass) { return SplitLayout(p, dclass).total; }
+size_t split_smem_bytes(const DevProblem& p, int dclass, bool pre) { return SplitLayout(p, dclass, pre).total; }
 
 // Global copy held at byte c of a split row of CTA h, or -1 for padding.
 __device__ __forceinline__ int split_copy(int c, int W, int h, int P) {
@@ -767,7 +768,7 @@ __device__ __forceinline__ UnitOffsets split_offsets(int g, int W, int b) {
     return o;
 }
 
-template <int DC>
+template <int DC, bool PRE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 1)
 sweep_split_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
                    long long timeout_ns, int n_consumer) {
@@ -784,7 +785,7 @@ sweep_split_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int s
     const int slot = blockIdx.x >> 1;
     const int N = p.N, P = p.P;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const SplitLayout L(p, DC);
+    const SplitLayout L(p, DC, PRE);
     const int W = L.W, RB = L.RB, Gc = L.Gc;
     const int hs = 4 * W + 4;
     int8_t* sp = reinterpret_cast<int8_t*>(smem + L.spins);
@@ -799,7 +800,7 @@ sweep_split_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int s
     unsigned long long* s_acc = reinterpret_cast<unsigned long long*>(smem + L.acc);
     int8_t* peer_sp = cluster.map_shared_rank(sp, h ^ 1);
     int* peer_xch = cluster.map_shared_rank(s_xch, h ^ 1);
-    const int NC = n_consumer;
+    const int NC = PRE ? n_consumer : nt;
     const bool consumer = tid < NC;
     const int DW = SiteDesc<DC>::DW;
 
@@ -857,13 +858,14 @@ sweep_split_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int s
                                           min(r.w, 0xFFFFFFFEu));
         }
     };
-    if (!consumer) produce(rbuf, (uint32_t)t0);
+    if (PRE && !consumer) produce(rbuf, (uint32_t)t0);
     __syncthreads();
 
     // consumers: a fixed column g_own per thread, items q_lane, q_lane + q_step, ... of a level
     const int g_own = tid % Gc, q_lane = tid / Gc, q_step = NC / Gc;
     const bool lane_ok = consumer && q_lane < q_step;
     const bool ghost_col = g_own == W;  // the recomputed peer word: its flips are the peer's
+    const uint32_t gg_own = (uint32_t)((h * W + g_own) % (2 * W));  // its chunk in the whole chain
     // level 0 of the next sweep during the swap wait: units v, v + (NC - 32) of the level
     // (v = tid - 32), so that warp 0 is free to poll the partner's mailbox
     const int units0 = (s_loff[1] - s_loff[0]) * Gc;
@@ -900,8 +902,9 @@ sweep_split_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int s
                         for (int q = s_loff[lev] + q_lane; q < end; q += q_step) {
                             const uint32_t it = s_items[q];
                             if (ghost_col && (it & 1u)) continue;
-                            const UnitEval e = split_unit_eval<DC>(sp, s_desc, it, rb + q * Gc + g_own, off);
-                            unit_decide_commit<true>(e, thr_c, lL, lC, lF);
+                            const UnitEval e = split_unit_eval<DC, PRE>(sp, s_desc, it, rb + q * Gc + g_own, off, t,
+                                                                        (uint32_t)slot, gg_own, key);
+                            unit_decide_commit<PRE>(e, thr_c, lL, lC, lF);
                         }
                     }
                     named_barrier(1, NC);
@@ -939,7 +942,7 @@ sweep_split_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int s
                 x[2] = (int)sF;
                 x[3] = s_ctl[5];
             }
-        } else if (!dead && s + 1 < n_sweeps) {
+        } else if (PRE && !dead && s + 1 < n_sweeps) {
             produce(rbuf + (size_t)(b ^ 1) * n_items * Gc, t + 1u);
         }
         // both halves of the sweep are done, the exchanged words and sums are visible and
@@ -977,10 +980,11 @@ sweep_split_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int s
                 const uint32_t it = s_items[sq[k]];
                 valid[k] = !((it & 1u) && sg[k] == W);
                 if (valid[k]) {
-                    ev[k] = split_unit_eval<DC>(sp, s_desc, it, rb1 + sq[k] * Gc + sg[k],
-                                                split_offsets(sg[k], W, b ^ 1));
-                    Fa[k] = unit_flips<true>(ev[k], thr_c);
-                    Fb[k] = prung >= 0 ? unit_flips<true>(ev[k], thr_b) : Fa[k];
+                    ev[k] = split_unit_eval<DC, PRE>(sp, s_desc, it, rb1 + sq[k] * Gc + sg[k],
+                                                     split_offsets(sg[k], W, b ^ 1), t + 1u, (uint32_t)slot,
+                                                     (uint32_t)((h * W + sg[k]) % (2 * W)), key);
+                    Fa[k] = unit_flips<PRE>(ev[k], thr_c);
+                    Fb[k] = prung >= 0 ? unit_flips<PRE>(ev[k], thr_b) : Fa[k];
                 }
             }
         }
@@ -1144,7 +1148,9 @@ static const void* sweep_fn(const LaunchPlan& plan) {
         }
     }
     if (plan.path == kPathSplit)
-        return plan.dclass == 4 ? (const void*)sweep_split_kernel<4> : (const void*)sweep_split_kernel<8>;
+        return plan.dclass == 4 ? (const void*)sweep_split_kernel<4, true> : (const void*)sweep_split_kernel<8, true>;
+    if (plan.path == kPathSplitInline)
+        return plan.dclass == 4 ? (const void*)sweep_split_kernel<4, false> : (const void*)sweep_split_kernel<8, false>;
     if (plan.path == kPathBits) {
         if (plan.threads > 512)
             return plan.dclass == 4 ? (const void*)sweep_packed_kernel<4, false, 1024, true>
@@ -1197,7 +1203,7 @@ static cudaLaunchConfig_t split_config(const DevProblem& p, const LaunchPlan& pl
 
 cudaError_t sweep_resident_chains(const DevProblem& p, const LaunchPlan& plan, long long* chains) {
     *chains = 0;
-    if (plan.path == kPathSplit) {
+    if (plan.path == kPathSplit || plan.path == kPathSplitInline) {
         cudaLaunchAttribute attr[2];
         cudaLaunchConfig_t cfg = split_config(p, plan, false, 0, attr);
         int clusters = 0;
@@ -1220,7 +1226,7 @@ cudaError_t launch_sweeps(const DevProblem& p, const LaunchPlan& plan, long long
     int n_consumer = plan.n_consumer;
     void* args[] = {&pp, &t0, &q0, &n_sweeps, &sweeps_per_swap, &timeout_ns, &n_consumer};
     const void* fn = sweep_fn(plan);
-    if (plan.path == kPathSplit) {
+    if (plan.path == kPathSplit || plan.path == kPathSplitInline) {
         cudaLaunchAttribute attr[2];
         cudaLaunchConfig_t cfg = split_config(p, plan, cooperative, s, attr);
         const cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);

@@ -35,20 +35,22 @@ def _lib(libpt):
     return libpt
 
 
-def test_medium_workload_full_length_split():
+@pytest.mark.parametrize("path", [5, 6])
+def test_medium_workload_full_length_split(path):
     """Random 3-regular N=256, P=64, R=64, 2000 sweeps with a swap pass after each; state
-    checked every 100 sweeps."""
+    checked every 100 sweeps (random words produced ahead, path 5, or inline, path 6)."""
     prob = instances.workload("regular3_n256_p64_r64", 1)
-    g, o = both(prob, kernel_path=5)
-    assert g.info.kernel_path == 5
+    g, o = both(prob, kernel_path=path)
+    assert g.info.kernel_path == path
     for chunk in range(prob.n_sweeps // 100):
         g.run(100, 1)
         o.run(100, 1)
         assert_same(g, o, "sweep %d" % (100 * (chunk + 1)))
 
 
+@pytest.mark.parametrize("path", [5, 6])
 @pytest.mark.parametrize("P", [16, 32, 48, 128])
-def test_split_row_lengths(P):
+def test_split_row_lengths(P, path):
     """W = P/16 = 1, 2, 3 and 8 words per parity and CTA (word columns 2..9), on a degree-6
     lattice with fields (eight neighbour slots) and a degree-3 graph (four); every sweep for
     six sweeps, then 200 more with a swap pass every third sweep."""
@@ -56,7 +58,7 @@ def test_split_row_lengths(P):
     for graph, kw in (("chimera", dict(rows=2, cols=3)), ("regular", dict(n=38, degree=3))):
         prob = instances.make_problem(graph, rng, P=P, R=5, n_sweeps=0, seed=instances.philox_seed(700 + P),
                                       ladder="geometric", g0=0.1, g1=3.0, T=0.2, J=(-3, -1, 2, 4), h=(-2, 0, 1), **kw)
-        g, o = both(prob, kernel_path=5)
+        g, o = both(prob, kernel_path=path)
         for s in range(6):
             g.run(1, 1)
             o.run(1, 1)
@@ -74,7 +76,8 @@ def test_split_layouts_sweeps_and_swap_modes_give_identical_bits():
     for kw in (dict(kernel_path=3), dict(kernel_path=5), dict(kernel_path=5, producer_threads=32),
                dict(kernel_path=5, threads_per_block=256, producer_threads=64),
                dict(kernel_path=5, threads_per_block=512, producer_threads=256),
-               dict(kernel_path=5, swap_mode=2)):
+               dict(kernel_path=5, swap_mode=2), dict(kernel_path=6), dict(kernel_path=6, threads_per_block=384),
+               dict(kernel_path=6, threads_per_block=64), dict(kernel_path=6, swap_mode=2)):
         g = pt.PT.from_problem(prob, **kw)
         g.run(300, 1)
         g.sweep(13)
@@ -92,9 +95,10 @@ def test_split_rejects_unsupported_shapes():
     prob = instances.workload("regular3_n16_p32_r16", 1)
     rng = np.random.default_rng(3)
     p24 = instances.make_problem("regular", rng, n=16, degree=3, P=24, R=4, seed=5)
-    with pytest.raises(pt.PTError) as e:
-        pt.PT.from_problem(p24, kernel_path=5)
-    assert e.value.code == pt.PT_EINVAL
+    for path in (5, 6):
+        with pytest.raises(pt.PTError) as e:
+            pt.PT.from_problem(p24, kernel_path=path)
+        assert e.value.code == pt.PT_EINVAL
     # P = 512: 33 word columns, more than the 32 consumer threads asked for
     p512 = instances.make_problem("regular", rng, n=4, degree=3, P=512, R=2, seed=6)
     with pytest.raises(pt.PTError) as e:
@@ -103,18 +107,19 @@ def test_split_rejects_unsupported_shapes():
     pt.PT.from_problem(prob, kernel_path=5).close()
 
 
-def test_split_partner_that_never_publishes_times_out_without_fault():
+@pytest.mark.parametrize("path", [5, 6])
+def test_split_partner_that_never_publishes_times_out_without_fault(path):
     """A withheld mailbox makes the bounded swap wait of both CTAs of the partner chain run
     out: the call reports PT_ETIMEDOUT, every CTA leaves through the same cluster barriers,
     and the device stays usable."""
     prob = instances.workload("regular3_n16_p32_r16", 5)
-    g = pt.PT.from_problem(prob, wait_timeout_ms=200, test_withhold_rung=3, swap_mode=1, kernel_path=5)
+    g = pt.PT.from_problem(prob, wait_timeout_ms=200, test_withhold_rung=3, swap_mode=1, kernel_path=path)
     g.run(4, 1)
     with pytest.raises(pt.PTError) as e:
         g.sync()
     assert e.value.code == pt.PT_ETIMEDOUT
     g.close()
-    h, o = both(prob, kernel_path=5)
+    h, o = both(prob, kernel_path=path)
     h.run(50, 1)
     o.run(50, 1)
     assert_same(h, o, "after timeout")
@@ -122,14 +127,15 @@ def test_split_partner_that_never_publishes_times_out_without_fault():
 
 def test_auto_plan_splits_chains_that_do_not_fit_one_cta():
     """N=256, P=128, R=64: one CTA cannot hold a chain with a sweep of produced random words,
-    two can, and 64 clusters fit the GPU, so the automatic plan takes the split kernel; its
-    bits equal the oracle's and the inline-random-word kernel's."""
+    two can, and 64 clusters fit the GPU, so the automatic plan takes a split kernel (timed
+    against the one-CTA inline-word kernel); its bits equal the oracle's and the inline-word
+    kernel's."""
     spec = dict(instances.WORKLOADS["regular3_n256_p64_r64"])
     spec["P"] = 128
     rng = np.random.default_rng(9)
     prob = instances.make_problem(spec.pop("graph"), rng, seed=instances.philox_seed(9), name="p128", **spec)
     g, o = both(prob)
-    assert g.info.kernel_path == 5
+    assert g.info.kernel_path in (5, 6)
     h = pt.PT.from_problem(prob, kernel_path=2)
     for chunk in range(2):
         g.run(100, 1)
