@@ -271,6 +271,12 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchParams bp) {
             BatchInstance* W = bp.inst + bp.order[job];
             W->t0 = I.t0 + I.n_sweeps;
             if (I.sweeps_per_swap > 0) W->q0 = I.q0 + I.n_sweeps / I.sweeps_per_swap;
+            if (bp.done) {
+                // every CTA of the cluster wrote its chains back before the barrier above;
+                // the fence makes those writes visible before the flag, to the host's copies
+                __threadfence_system();
+                atomicExch(bp.done + bp.order[job], bp.done_token);
+            }
         }
     }
 }

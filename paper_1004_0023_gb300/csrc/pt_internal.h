@@ -107,6 +107,8 @@ struct BatchParams {
     int count;
     int* next_job;              // work counter, zero at launch
     int* status;
+    int* done = nullptr;        // [count] or null: done[k] = done_token once problem k is written back
+    int done_token = 1;         // nonzero, different per launch, so stale flags never match
 };
 
 // Kernel launchers (pt_kernels.cu). Each returns a cudaError_t from the launch.

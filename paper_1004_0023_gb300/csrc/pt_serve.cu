@@ -85,9 +85,16 @@ class ArenaAllocator {
 
 // Requests launched together as one persistent batched launch share a device block holding
 // their records, the work order, the work counter and a status word.
+// A backlog group: requests admitted together into one persistent batched launch. Each
+// member completes on its own (the kernel raises its flag once its chains are written back);
+// the group's block (instance records, work counter, flags) is freed once the launch ends.
 struct ServeGroup {
-    size_t off = 0, bytes = 0, status_off = 0;
-    int refs = 0;
+    size_t off = 0, bytes = 0, status_off = 0, flags_off = 0;
+    int refs = 0;                 // members not yet completed
+    int n = 0;
+    int token = 0;                // the value a member's flag takes when it is done
+    std::vector<int> flags;       // host copy of the members' done flags
+    cudaEvent_t done = nullptr;   // the launch's end
 };
 
 struct ServeReq {
@@ -102,6 +109,7 @@ struct ServeReq {
     cudaEvent_t done = nullptr;
     int stream_idx = 0;
     ServeGroup* group = nullptr;  // set while the request runs in a batched launch
+    int group_index = -1;         // its problem index (and flag) in that launch
 };
 
 // Streamed mode launches a request's sweeps in pieces of at most this many swap passes.
@@ -138,6 +146,7 @@ struct pt_server {
     std::deque<int64_t> queued;
     std::vector<int64_t> active;
     std::deque<int64_t> finished_unreported;
+    std::vector<ServeGroup*> retiring;  // groups whose members are all done, launch still running
     int64_t next_id, steps, launches;
     BatchInstance* d_inst;
     int32_t* d_order;
@@ -165,6 +174,14 @@ static void free_server(pt_server* s) {
     for (cudaStream_t st : s->pool) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
+    }
+    std::vector<ServeGroup*> groups(s->retiring);
+    for (auto& kv : s->reqs)
+        if (kv.second->group && std::find(groups.begin(), groups.end(), kv.second->group) == groups.end())
+            groups.push_back(kv.second->group);
+    for (ServeGroup* grp : groups) {
+        if (grp->done) cudaEventDestroy(grp->done);
+        delete grp;
     }
     for (auto& kv : s->reqs) {
         if (kv.second->done) cudaEventDestroy(kv.second->done);
@@ -519,7 +536,10 @@ static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
     const size_t order_off = ((size_t)n * sizeof(BatchInstance) + 255) & ~(size_t)255;
     const size_t ctr_off = order_off + (((size_t)n * sizeof(int32_t) + 255) & ~(size_t)255);
     grp->status_off = ctr_off + 16;
-    grp->bytes = ctr_off + 256;
+    grp->flags_off = ctr_off + 256;
+    grp->bytes = grp->flags_off + (((size_t)n * sizeof(int) + 255) & ~(size_t)255);
+    grp->n = n;
+    grp->flags.assign(n, 0);
     if (!s->alloc->alloc(grp->bytes, &grp->off)) {
         delete grp;
         return 1;
@@ -551,7 +571,7 @@ static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
             cudaSuccess ||
         (e = cudaMemcpyAsync(gb + order_off, order.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice,
                              st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(gb + ctr_off, 0, 256, st)) != cudaSuccess)
+        (e = cudaMemsetAsync(gb + ctr_off, 0, grp->bytes - ctr_off, st)) != cudaSuccess)
         return sfail(s, PT_ECUDA, "group upload: %s", cudaGetErrorString(e));
     BatchParams bp;
     bp.inst = (BatchInstance*)gb;
@@ -559,14 +579,23 @@ static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
     bp.count = n;
     bp.next_job = (int*)(gb + ctr_off);
     bp.status = (int*)(gb + grp->status_off);
+    bp.done = (int*)(gb + grp->flags_off);
+    // a flag left in this arena block by an earlier group carries that group's token
+    grp->token = (int)(s->group_launches % 2000000000) + 1;
+    bp.done_token = grp->token;
     if ((e = launch_batch(bp, s->cluster, std::min(s->n_clusters, n), s->threads, smem, st)) != cudaSuccess)
         return sfail(s, PT_ECUDA, "group launch: %s", cudaGetErrorString(e));
+    if ((e = cudaEventCreateWithFlags(&grp->done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventRecord(grp->done, st)) != cudaSuccess)
+        return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
     s->launches += 1;
     s->group_launches += 1;
-    for (ServeReq* q : g) {
+    for (int k = 0; k < n; ++k) {
+        ServeReq* q = g[k];
         if (!q->done && (e = cudaEventCreateWithFlags(&q->done, cudaEventDisableTiming)) != cudaSuccess)
             return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
         if ((e = cudaEventRecord(q->done, st)) != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+        q->group_index = k;
         q->stream_idx = sidx;
         q->inst.t0 += q->remaining;
         if (q->inst.sweeps_per_swap > 0) q->inst.q0 += q->remaining / q->inst.sweeps_per_swap;
@@ -578,12 +607,45 @@ static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
     return PT_OK;
 }
 
+// Frees the block of a group whose launch has ended (false: still running).
+static bool retire_group(pt_server* s, ServeGroup* grp) {
+    if (cudaEventQuery(grp->done) != cudaSuccess) return false;
+    s->alloc->release(grp->off, grp->bytes);
+    cudaEventDestroy(grp->done);
+    delete grp;
+    return true;
+}
+
 static int step_streamed(pt_server* s) {
+    // groups whose members have all completed: free their blocks once the launch has ended
+    {
+        std::vector<ServeGroup*> keep;
+        for (ServeGroup* grp : s->retiring)
+            if (!retire_group(s, grp)) keep.push_back(grp);
+        s->retiring.swap(keep);
+    }
+    // the done flags of the members of groups still running, one small copy per group
+    {
+        std::vector<ServeGroup*> polled;
+        for (int64_t id : s->active) {
+            ServeGroup* grp = s->reqs[id]->group;
+            if (!grp || std::find(polled.begin(), polled.end(), grp) != polled.end()) continue;
+            polled.push_back(grp);
+            const cudaError_t e = cudaMemcpyAsync(grp->flags.data(), s->arena + grp->off + grp->flags_off,
+                                                  (size_t)grp->n * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+            if (e != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+        }
+        if (!polled.empty()) {
+            const cudaError_t e = cudaStreamSynchronize(s->stream);
+            if (e != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
+        }
+    }
     // completions first, so their arena room can go to queued requests
     std::vector<int64_t> still;
     for (int64_t id : s->active) {
         ServeReq* q = s->reqs[id];
-        const cudaError_t e = cudaEventQuery(q->done);
+        const bool flagged = q->group && q->group->flags[q->group_index] == q->group->token;
+        const cudaError_t e = flagged ? cudaSuccess : cudaEventQuery(q->done);
         if (e == cudaErrorNotReady) {
             still.push_back(id);
             continue;
@@ -595,11 +657,9 @@ static int step_streamed(pt_server* s) {
         if (e2 != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e2));
         if (st == PT_ETIMEDOUT) return sfail(s, PT_ETIMEDOUT, "a swap wait timed out");
         if (st) return sfail(s, PT_ECUDA, "device status %d", st);
-        if (q->group && --q->group->refs == 0) {
-            s->alloc->release(q->group->off, q->group->bytes);
-            delete q->group;
-        }
+        if (q->group && --q->group->refs == 0 && !retire_group(s, q->group)) s->retiring.push_back(q->group);
         q->group = nullptr;
+        q->group_index = -1;
         s->inflight_chains -= q->prep.R;
         q->state = 2;
         s->finished_unreported.push_back(id);

@@ -2,6 +2,7 @@
 with whatever else is on the device, and each result is the same as the request run alone
 (pt_create + pt_run) and as the oracle."""
 import os
+import time
 
 import numpy as np
 import pytest
@@ -67,6 +68,7 @@ def test_results_are_the_same_alone_and_in_the_mix(arena_bytes, max_active, step
         o = Oracle.from_problem(probs[k], threads=THREADS)
         o.run(probs[k].n_sweeps, probs[k].sweeps_per_swap)
         _same(results[k][0], results[k][1], o.read_state(), o.obs(), "request %d vs oracle" % k)
+    _drain(srv)
     info = srv.info()
     assert info.active == 0 and info.queued == 0 and info.arena_used == 0
     if packed_only or not stepped:
@@ -74,6 +76,16 @@ def test_results_are_the_same_alone_and_in_the_mix(arena_bytes, max_active, step
     else:
         assert info.wide_steps > 0
     srv.close()
+
+
+def _drain(srv):
+    """A group's shared block is freed at the first step after its launch ends."""
+    for _ in range(2000):
+        if srv.info().arena_used == 0:
+            return
+        srv.step()
+        time.sleep(0.001)
+    assert srv.info().arena_used == 0
 
 
 def test_backlog_starts_as_one_batched_launch_with_the_same_bits():
@@ -89,7 +101,8 @@ def test_backlog_starts_as_one_batched_launch_with_the_same_bits():
             srv.release(rid)
     info = srv.info()
     assert info.group_launches >= 1
-    assert info.active == 0 and info.queued == 0 and info.arena_used == 0
+    assert info.active == 0 and info.queued == 0
+    _drain(srv)
     for k, p in enumerate(probs):
         alone = pt.PT.from_problem(p)
         alone.run(p.n_sweeps, p.sweeps_per_swap)
@@ -116,3 +129,34 @@ def test_poisson_replay_batched_and_plain_complete_every_request():
     for r in (b, st, p):
         assert r["completed"] == 10
         assert r["p99_s"] >= r["p50_s"] > 0
+
+
+def test_members_of_a_batched_launch_complete_on_their_own():
+    """Nine requests submitted together start in one batched launch: one long request and
+    eight short ones. The short ones complete (flagged by the kernel) while the long one is
+    still running, and every result equals the request run alone."""
+    short = _requests(8, 21, (20, 40))
+    rng = np.random.default_rng(5)
+    long_req = instances.make_problem("regular", rng, n=96, degree=3, P=32, R=12, n_sweeps=60000,
+                                      seed=instances.philox_seed(77), ladder="geometric", g0=0.1, g1=3.0, T=0.2)
+    probs = [long_req] + short
+    srv = pt.Server()
+    ids = {srv.submit(p): k for k, p in enumerate(probs)}
+    order, results = [], {}
+    while len(results) < len(probs):
+        for rid in srv.step():
+            k = ids[rid]
+            order.append((k, srv.info().active))
+            results[k] = srv.result(rid)
+            srv.release(rid)
+    assert srv.info().group_launches >= 1
+    # the eight short requests came back first, each while the long one was still active
+    assert [k for k, _ in order[:8]] != [] and 0 not in [k for k, _ in order[:8]]
+    assert all(active >= 1 for _, active in order[:8])
+    _drain(srv)
+    for k, p in enumerate(probs):
+        alone = pt.PT.from_problem(p)
+        alone.run(p.n_sweeps, p.sweeps_per_swap)
+        _same(results[k][0], results[k][1], alone.read_state(), alone.obs(), "request %d vs alone" % k)
+        alone.close()
+    srv.close()
