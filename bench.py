@@ -159,7 +159,7 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_min_mhz": min(sm) if sm else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ----------------------------------------------------------------------------- ours
@@ -247,7 +247,7 @@ def run_ours(args, rank, world, local_rank):
         batched = run_batched(args, pt, instances, torch, n_sm, sm_max)
     serving = None
     if not args.no_serving and rank == 0:
-        serving = run_serving(args, torch, batched)
+        serving = run_serving(args, torch, batched, local_rank)
     if rank != 0:
         return None
     return {
@@ -339,8 +339,11 @@ def run_batched(args, pt, instances, torch, n_sm, sm_max):
                          "traffic_unit": "DRAM bytes per launch (ncu)"}}
 
 
-def run_serving(args, torch, batched):
-    """Poisson arrivals of requests from the batched size distribution, 500..5000 sweeps each."""
+def run_serving(args, torch, batched, gpu_index=0):
+    """Poisson arrivals of requests from the batched size distribution, 500..5000 sweeps each.
+
+    The latency comparison at half capacity runs first, then the overload replay; SM clocks
+    and throttle reasons are sampled during each."""
     from paper_1004_0023_gb300 import serve
 
     out = {"workload": "Poisson arrivals, sizes as the batched workload, sweeps~U{500..5000}, swap every sweep",
@@ -349,23 +352,29 @@ def run_serving(args, torch, batched):
                      "stream of a pool with one CTA per chain; plain = one request at a time, pt_create + pt_run"}
     stream = torch.cuda.Stream()
     trace = serve.poisson_trace(args.serving_rate, args.serving_seconds, seed=2)
-    offered = sum(p.attempts_per_sweep * p.n_sweeps for _, p in trace) / max(args.serving_seconds, 1e-9)
-    res = serve.replay_batched(trace, stream=stream.cuda_stream, deadline=args.serving_seconds + 30.0)
-    res["rate_per_s"] = args.serving_rate
-    res["offered_attempts_per_s"] = offered
-    res["arrived"] = len(trace)
-    out["at_configured_rate"] = res
     # a rate the batched server sustains (half its measured batched capacity), both modes
     if batched:
         mean_work = np.mean([p.attempts_per_sweep * p.n_sweeps for _, p in trace]) if trace else 1.0
         rate = max(1.0, 0.5 * batched["value"] / mean_work)
         trace2 = serve.poisson_trace(rate, args.serving_seconds, seed=3)
+        sampler = ClockSampler(gpu_index)
+        sampler.start()
         b = serve.replay_batched(trace2, stream=stream.cuda_stream, deadline=args.serving_seconds + 30.0)
         p = serve.replay_plain(trace2, stream=stream.cuda_stream, deadline=args.serving_seconds + 30.0)
+        clocks = sampler.stop()
         for r in (b, p):
             r["rate_per_s"] = rate
             r["arrived"] = len(trace2)
-        out["at_half_capacity"] = {"server": b, "plain": p}
+        out["at_half_capacity"] = {"server": b, "plain": p, "clocks": clocks}
+    offered = sum(p.attempts_per_sweep * p.n_sweeps for _, p in trace) / max(args.serving_seconds, 1e-9)
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    res = serve.replay_batched(trace, stream=stream.cuda_stream, deadline=args.serving_seconds + 30.0)
+    res["clocks"] = sampler.stop()
+    res["rate_per_s"] = args.serving_rate
+    res["offered_attempts_per_s"] = offered
+    res["arrived"] = len(trace)
+    out["at_configured_rate"] = res
     return out
 
 
