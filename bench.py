@@ -43,7 +43,8 @@ def alg_instr_per_attempt(degree: int) -> int:
 
 KERNEL_NAMES = {1: "sweep_kernel (byte-wise)", 2: "sweep_packed_kernel (int8, inline Philox)",
                 3: "sweep_packed_kernel (int8, producer warps)", 4: "sweep_packed_kernel (bit-packed)",
-                5: "sweep_split_kernel (int8, producer warps, each chain on a 2-CTA cluster)"}
+                5: "sweep_split_kernel (int8, producer warps, each chain on a 2-CTA cluster)",
+                6: "sweep_split_kernel (int8, inline Philox, each chain on a 2-CTA cluster)"}
 
 # DRAM bytes (read + write) per launch of the sweep kernel, from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum: (workload, kernel path, sweeps per launch)
