@@ -127,15 +127,15 @@ def test_split_partner_that_never_publishes_times_out_without_fault(path):
 
 def test_auto_plan_splits_chains_that_do_not_fit_one_cta():
     """N=256, P=128, R=64: one CTA cannot hold a chain with a sweep of produced random words,
-    two can, and 64 clusters fit the GPU, so the automatic plan takes a split kernel (timed
-    against the one-CTA inline-word kernel); its bits equal the oracle's and the inline-word
-    kernel's."""
+    two can, and 64 clusters fit the GPU, so the split kernels are among the automatic plan's
+    timed candidates (with the one-CTA inline-word kernels); whichever wins, the bits equal
+    the oracle's and the inline-word kernel's."""
     spec = dict(instances.WORKLOADS["regular3_n256_p64_r64"])
     spec["P"] = 128
     rng = np.random.default_rng(9)
     prob = instances.make_problem(spec.pop("graph"), rng, seed=instances.philox_seed(9), name="p128", **spec)
     g, o = both(prob)
-    assert g.info.kernel_path in (5, 6)
+    assert g.info.kernel_path in (2, 5, 6) and g.info.tuned_plans >= 2
     h = pt.PT.from_problem(prob, kernel_path=2)
     for chunk in range(2):
         g.run(100, 1)
