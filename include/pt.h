@@ -151,6 +151,8 @@ typedef struct {
  *   cuda_stream cudaStream_t to use, or NULL for a stream owned by the context.
  * Initial spins come from the key: copy k of site i of chain rho is -1 iff bit 31 of
  * word k%4 of philox((0, i, rho, 2<<28 | k/4), seed) is set.
+ * With an automatic plan (see pt_options.no_autotune) pt_create first times a short run of
+ * each candidate kernel plan, then returns the context to exactly that initial state.
  * Returns PT_EINVAL, PT_ENOMEM, PT_ECUDA or PT_ENODEV on failure (*out untouched). */
 int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladder, int32_t R,
               const uint32_t* flip_thr, const double* swap_coef, uint64_t seed,
@@ -278,7 +280,9 @@ const char* pt_batch_last_error(const pt_batch* b);
  * admitted request's state and counters live in the arena; all of its sweeps are launched
  * at once on one stream of a pool (one CTA per chain), so requests that arrive while others
  * run overlap with them on the device. When a backlog of 8 or more requests waits, they
- * start together in one persistent batched launch (as pt_batch_run) instead. In stepped
+ * start together in one persistent batched launch (as pt_batch_run) instead; each of them
+ * is reported finished as soon as its own chains are written back, not when the whole
+ * launch ends. In stepped
  * mode each step instead advances every admitted request by quantum_sweeps sweeps in one
  * launch and waits for it. Results are read with pt_server_read_result and the arena room
  * is returned by pt_server_release. Each result equals pt_create + pt_run of that request
