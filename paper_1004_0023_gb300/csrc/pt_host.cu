@@ -435,6 +435,11 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     auto split_fits = [&](int spath = kPathSplit) {
         if (P % 16 != 0 || !(want_threads == 0 || (want_threads >= 64 && want_threads <= 512)) || !fits(spath))
             return false;
+        // every one of the P/16 + 1 word columns needs a consumer (and, with producer warps,
+        // a producer) thread
+        const int th = want_threads > 0 ? want_threads : 512;
+        const int cols = P / 16 + 1;
+        if (spath == kPathSplit ? (th / 4 < cols || th - th / 4 < cols) : th < cols) return false;
         DevProblem q = p;
         if (sweep_smem_bytes(q, spath, packed_dc) > (size_t)max_smem) q.tables_in_smem = 0;
         if (sweep_smem_bytes(q, spath, packed_dc) > (size_t)max_smem) q.acc_in_smem = 0;
@@ -663,7 +668,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             if (fits(kPathPacked)) cands.push_back({kPathPacked, 512, 128});
             if (split_fits()) cands.push_back({kPathSplit, 512, 128});
             if (split_fits(kPathSplitInline))
-                for (int th : {384, 512}) cands.push_back({kPathSplitInline, th, 0});
+                for (int th : {384, 512})
+                    if (th >= P / 16 + 1) cands.push_back({kPathSplitInline, th, 0});
             if (fits(kPathPackedInline))
                 for (int th : {256, 384, 512}) cands.push_back({kPathPackedInline, th, 0});
         }

@@ -350,3 +350,42 @@ def test_partner_that_never_publishes_times_out_without_fault(path):
     h.run(50, 1)
     o.run(50, 1)
     assert_same(h, o, "after timeout")
+
+
+def test_largest_trotter_stack_and_largest_resident_chain():
+    """P = 4096, the largest P accepted: 512 words per parity, more word columns than a CTA
+    has threads, so the level loop runs in its flat unit order. And N = 4096 sites at P = 16
+    (64 KiB of int8 chain per replica). Both bit-exact with the oracle."""
+    rng = np.random.default_rng(4096)
+    big_p = instances.make_problem("regular", rng, n=6, degree=3, P=4096, R=3, n_sweeps=0,
+                                   seed=instances.philox_seed(4096), ladder="geometric", g0=0.1, g1=3.0, T=0.2)
+    g, o = both(big_p)
+    for s in range(3):
+        g.run(1, 1)
+        o.run(1, 1)
+        assert_same(g, o, "P=4096 sweep %d" % (s + 1))
+    g.run(40, 2)
+    o.run(40, 2)
+    assert_same(g, o, "P=4096 after 40 more")
+    big_n = instances.make_problem("regular", rng, n=4096, degree=3, P=16, R=4, n_sweeps=0,
+                                   seed=instances.philox_seed(4097), ladder="geometric", g0=0.1, g1=3.0, T=0.2)
+    g, o = both(big_n)
+    g.run(30, 1)
+    o.run(30, 1)
+    assert_same(g, o, "N=4096")
+
+
+def test_chain_too_large_for_any_layout_is_rejected():
+    """A chain no layout can hold in one SM's shared memory is refused at create with
+    PT_EINVAL (nothing is launched), and the device stays usable."""
+    rng = np.random.default_rng(5)
+    huge = instances.make_problem("regular", rng, n=60000, degree=3, P=64, R=2, n_sweeps=0,
+                                  seed=instances.philox_seed(5), ladder="geometric", g0=0.1, g1=3.0, T=0.2)
+    with pytest.raises(pt.PTError) as e:
+        pt.PT.from_problem(huge)
+    assert e.value.code == pt.PT_EINVAL
+    prob = instances.workload("regular3_n16_p32_r16", 1)
+    g, o = both(prob)
+    g.run(20, 1)
+    o.run(20, 1)
+    assert_same(g, o, "after a refused create")
