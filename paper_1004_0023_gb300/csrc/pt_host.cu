@@ -649,7 +649,9 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     // with 256, 384 or 512 threads, split kernel) sweeps a short stretch of one continuous
     // run, and the fastest is kept. Results do not depend on the plan; the context is then
     // reset to its initial state. The choice is cached per problem shape for the process.
-    const bool tune = want_path == 0 && want_threads == 0 && !(opt && opt->no_autotune) && c->cooperative &&
+    // (also when the fixed plan cannot hold every chain at once: a candidate that can runs the
+    // swap passes inside its launch; every candidate timed is one whose chains are all resident)
+    const bool tune = want_path == 0 && want_threads == 0 && !(opt && opt->no_autotune) && coop_ok && mode != 2 &&
                       R > 1 && p.withhold_rung < 0 && !p.exact_swaps &&
                       (path == kPathPacked || path == kPathPackedInline || path == kPathSplit);
     if (tune) {
@@ -772,6 +774,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                 if (prepare_sweep_kernel(pl) == cudaSuccess && sweep_resident_chains(pc, pl, &res) == cudaSuccess &&
                     res >= R) {
                     c->plan = pl;
+                    c->cooperative = true;  // resident (checked above), cooperative launch available
                     p.acc_in_smem = pc.acc_in_smem;
                     p.tables_in_smem = pc.tables_in_smem;
                     if (!cached) {

@@ -389,3 +389,23 @@ def test_chain_too_large_for_any_layout_is_rejected():
     g.run(20, 1)
     o.run(20, 1)
     assert_same(g, o, "after a refused create")
+
+
+def test_more_chains_than_fit_at_once():
+    """R = 200 chains of the N=256, P=64 workload. With the producer-warp kernel one chain
+    fills an SM, so not every chain can be resident, and swap passes run as separate launches
+    between sweep launches. The automatic plan times only candidates whose chains all fit
+    (the inline-word kernel: several CTAs per SM) and so swaps inside one launch. Both give
+    the oracle's bits."""
+    spec = dict(instances.WORKLOADS["regular3_n256_p64_r64"])
+    spec["R"] = 200
+    rng = np.random.default_rng(200)
+    prob = instances.make_problem(spec.pop("graph"), rng, seed=instances.philox_seed(200), name="r200", **spec)
+    o = Oracle.from_problem(prob, threads=THREADS)
+    o.run(20, 1)
+    for kw in (dict(kernel_path=3), dict()):
+        g = pt.PT.from_problem(prob, **kw)
+        assert bool(g.info.cooperative) == (not kw)
+        g.run(20, 1)
+        assert_same(g, o, "R=200 %s" % kw)
+        g.close()
