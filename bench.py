@@ -33,7 +33,7 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "spin-flip attempts/s"
-# Algorithmic integer lane-instructions per attempt ("Roofline"):
+# Algorithmic integer lane-instructions per attempt, the work the method itself needs:
 # 1/4 of a Philox4x32-10 call (10 rounds x (2 wide multiplies + 2 three-input XORs)) = 10,
 # local field d multiply-adds, L = s*f (1), m = s*(s- + s+) (2), table index (2),
 # acceptance compare (2), flip select (1), E/M/count updates (3).
