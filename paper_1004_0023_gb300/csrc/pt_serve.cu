@@ -95,6 +95,8 @@ struct ServeGroup {
     int token = 0;                // the value a member's flag takes when it is done
     std::vector<int> flags;       // host copy of the members' done flags
     cudaEvent_t done = nullptr;   // the launch's end
+    int stream_idx = 0;           // the pool stream it runs on
+    int ctas = 0;                 // CTAs launched (each holds an SM until the launch ends)
 };
 
 struct ServeReq {
@@ -118,9 +120,11 @@ constexpr int kStreamedPasses = 256;
 // Streamed mode under backlog: once this many requests wait, they start together in one
 // persistent batched launch (chains packed onto thread-block clusters), which sustains a
 // higher rate than one launch per request. Below it, a request starts on its own launch
-// while the chains already in flight number less than kChainBudgetPerSm per SM.
+// while the SMs it needs are free: a request launched alone is one cooperative launch whose
+// chains wait for one another's swap mailboxes, so every one of its CTAs must be resident
+// together. Each in-flight chain is counted as one SM (a CTA of the streamed kernel can
+// need a whole SM's shared memory), and a running group launch as its CTAs until it ends.
 constexpr int kGroupMin = 8;
-constexpr int kChainBudgetPerSm = 2;
 
 }  // namespace
 
@@ -138,8 +142,9 @@ struct pt_server {
     int64_t wide_steps;
     bool streamed;
     std::vector<cudaStream_t> pool;
+    std::vector<int> stream_load;  // requests launched alone plus groups still running, per stream
     int next_stream;
-    long long inflight_chains;  // streamed mode: chains of the requests on the device
+    long long inflight_sms;  // streamed mode: SMs held by requests launched alone and by group launches
     int64_t group_launches;
     size_t smem_cap;
     std::map<int64_t, ServeReq*> reqs;
@@ -215,7 +220,7 @@ extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream,
     s->streamed = !(opt && (opt->reserved[1] == 1 || opt->reserved[0] == 1));  // reserved[1] == 1: stepped
     s->next_stream = 0;
     s->wide_steps = 0;
-    s->inflight_chains = 0;
+    s->inflight_sms = 0;
     s->group_launches = 0;
     if (s->cluster > 16 || s->max_active > 65536) {
         delete s;
@@ -414,10 +419,24 @@ static int upload_request(pt_server* s, ServeReq* q, cudaStream_t st) {
     return PT_OK;
 }
 
+// The pool stream with the least work still running (first such stream from a rotating
+// start), so that a new launch never waits in stream order behind a long request or group.
+static int pick_stream(pt_server* s) {
+    const int n = (int)s->pool.size();
+    if ((int)s->stream_load.size() != n) s->stream_load.assign(n, 0);
+    int best = s->next_stream;
+    for (int k = 0; k < n; ++k) {
+        const int i = (s->next_stream + k) % n;
+        if (s->stream_load[i] < s->stream_load[best]) best = i;
+    }
+    s->next_stream = (best + 1) % n;
+    s->stream_load[best] += 1;
+    return best;
+}
+
 static int launch_streamed(pt_server* s, ServeReq* q) {
-    cudaStream_t st = s->pool[s->next_stream];
-    q->stream_idx = s->next_stream;
-    s->next_stream = (s->next_stream + 1) % (int)s->pool.size();
+    q->stream_idx = pick_stream(s);
+    cudaStream_t st = s->pool[q->stream_idx];
     int rc = upload_request(s, q, st);
     if (rc) return rc;
     unsigned char* base = s->arena + q->block_off;
@@ -544,9 +563,9 @@ static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
         delete grp;
         return 1;
     }
-    cudaStream_t st = s->pool[s->next_stream];
-    const int sidx = s->next_stream;
-    s->next_stream = (s->next_stream + 1) % (int)s->pool.size();
+    const int sidx = pick_stream(s);
+    cudaStream_t st = s->pool[sidx];
+    grp->stream_idx = sidx;
     std::vector<BatchInstance> insts(n);
     size_t smem = 0;
     for (int k = 0; k < n; ++k) {
@@ -585,6 +604,8 @@ static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
     bp.done_token = grp->token;
     if ((e = launch_batch(bp, s->cluster, std::min(s->n_clusters, n), s->threads, smem, st)) != cudaSuccess)
         return sfail(s, PT_ECUDA, "group launch: %s", cudaGetErrorString(e));
+    grp->ctas = std::min(s->n_clusters, n) * s->cluster;
+    s->inflight_sms += grp->ctas;
     if ((e = cudaEventCreateWithFlags(&grp->done, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventRecord(grp->done, st)) != cudaSuccess)
         return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e));
@@ -610,6 +631,8 @@ static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
 // Frees the block of a group whose launch has ended (false: still running).
 static bool retire_group(pt_server* s, ServeGroup* grp) {
     if (cudaEventQuery(grp->done) != cudaSuccess) return false;
+    s->stream_load[grp->stream_idx] -= 1;
+    s->inflight_sms -= grp->ctas;
     s->alloc->release(grp->off, grp->bytes);
     cudaEventDestroy(grp->done);
     delete grp;
@@ -657,15 +680,16 @@ static int step_streamed(pt_server* s) {
         if (e2 != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(e2));
         if (st == PT_ETIMEDOUT) return sfail(s, PT_ETIMEDOUT, "a swap wait timed out");
         if (st) return sfail(s, PT_ECUDA, "device status %d", st);
+        if (!q->group) s->stream_load[q->stream_idx] -= 1;  // its own launch has ended
         if (q->group && --q->group->refs == 0 && !retire_group(s, q->group)) s->retiring.push_back(q->group);
+        if (!q->group) s->inflight_sms -= q->prep.R;
         q->group = nullptr;
         q->group_index = -1;
-        s->inflight_chains -= q->prep.R;
         q->state = 2;
         s->finished_unreported.push_back(id);
     }
     s->active.swap(still);
-    const long long budget = (long long)kChainBudgetPerSm * s->n_sm;
+    const long long budget = s->n_sm;
     if ((int)s->queued.size() >= kGroupMin) {
         // backlog: every queued request that gets a slot and arena room starts in one launch
         std::vector<ServeReq*> g;
@@ -676,7 +700,6 @@ static int step_streamed(pt_server* s) {
             q->block_off = off;
             s->queued.pop_front();
             s->active.push_back(q->id);
-            s->inflight_chains += q->prep.R;
             g.push_back(q);
         }
         if (!g.empty()) {
@@ -685,6 +708,7 @@ static int step_streamed(pt_server* s) {
                 for (ServeReq* q : g) {  // no room for the group's block: one launch each
                     const int rc2 = launch_streamed(s, q);
                     if (rc2) return rc2;
+                    s->inflight_sms += q->prep.R;
                 }
             } else if (rc) {
                 return rc;
@@ -693,7 +717,7 @@ static int step_streamed(pt_server* s) {
     } else {
         while (!s->queued.empty() && (int)s->active.size() < s->max_active) {
             ServeReq* q = s->reqs[s->queued.front()];
-            if (!s->active.empty() && s->inflight_chains + q->prep.R > budget) break;
+            if (!s->active.empty() && s->inflight_sms + q->prep.R > budget) break;
             size_t off = 0;
             if (!s->alloc->alloc(q->block_bytes, &off)) break;
             q->block_off = off;
@@ -701,7 +725,7 @@ static int step_streamed(pt_server* s) {
             const int rc = launch_streamed(s, q);
             if (rc) return rc;
             s->active.push_back(q->id);
-            s->inflight_chains += q->prep.R;
+            s->inflight_sms += q->prep.R;
         }
     }
     s->steps += 1;
