@@ -246,17 +246,26 @@ void ptq::build_site_desc(int N, int P, int dclass, const std::vector<std::vecto
     }
 }
 
-template <typename T>
-static cudaError_t dev_alloc(pt_ctx* c, T** ptr, size_t count) {
-    void* p = nullptr;
-    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) return e;
-    c->allocs.push_back(p);
-    c->device_bytes += (int64_t)bytes;
-    *ptr = (T*)p;
-    return cudaSuccess;
-}
+// All of a context's device buffers are carved out of one allocation, so a create costs one
+// cudaMalloc: first every buffer is placed (256-byte aligned), then the pointers are set.
+struct DevCarve {
+    size_t total = 0;
+    std::vector<std::pair<void**, size_t>> slots;  // where to store each buffer's address
+    template <typename T>
+    void add(T** ptr, size_t count) {
+        slots.push_back({reinterpret_cast<void**>(ptr), total});
+        total += (std::max<size_t>(count * sizeof(T), 16) + 255) & ~(size_t)255;
+    }
+    cudaError_t allocate(pt_ctx* c) {
+        void* base = nullptr;
+        const cudaError_t e = cudaMalloc(&base, total);
+        if (e != cudaSuccess) return e;
+        c->allocs.push_back(base);
+        c->device_bytes += (int64_t)total;
+        for (auto& sl : slots) *sl.first = static_cast<unsigned char*>(base) + sl.second;
+        return cudaSuccess;
+    }
+};
 
 static void free_ctx(pt_ctx* c) {
     for (void* p : c->allocs) cudaFree(p);
@@ -565,22 +574,25 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     double* d_coef;
     const int max_passes = 1024;
     c->max_passes = max_passes;
-    if ((e = dev_alloc(c, &d_nbr, nbr.size())) != cudaSuccess ||
-        (e = dev_alloc(c, &d_h, (size_t)N)) != cudaSuccess ||
-        (e = dev_alloc(c, &d_items, items.size())) != cudaSuccess ||
-        (e = dev_alloc(c, &d_loff, level_off.size())) != cudaSuccess ||
-        (e = dev_alloc(c, &d_thr, c->thr.size())) != cudaSuccess ||
-        (e = dev_alloc(c, &d_desc, desc.size())) != cudaSuccess ||
-        (e = dev_alloc(c, &d_coef, c->coef.size())) != cudaSuccess ||
-        (e = dev_alloc(c, &p.spins, (size_t)R * p.slot_stride)) != cudaSuccess ||
-        (e = dev_alloc(c, &p.E, (size_t)R)) != cudaSuccess || (e = dev_alloc(c, &p.M, (size_t)R)) != cudaSuccess ||
-        (e = dev_alloc(c, &p.rung_of_slot, (size_t)R)) != cudaSuccess ||
-        (e = dev_alloc(c, &p.slot_of_rung, (size_t)R)) != cudaSuccess ||
-        (e = dev_alloc(c, &p.acc, (size_t)R * kAccCount)) != cudaSuccess ||
-        (e = dev_alloc(c, &p.swap_stats, 2 * (size_t)R)) != cudaSuccess ||
-        (e = dev_alloc(c, &p.mbox, (size_t)max_passes * R)) != cudaSuccess ||
-        (e = dev_alloc(c, &p.status, (size_t)4)) != cudaSuccess ||
-        (e = dev_alloc(c, &c->staging, (size_t)R * N * P)) != cudaSuccess) {
+    DevCarve carve;
+    carve.add(&d_nbr, nbr.size());
+    carve.add(&d_h, (size_t)N);
+    carve.add(&d_items, items.size());
+    carve.add(&d_loff, level_off.size());
+    carve.add(&d_thr, c->thr.size());
+    carve.add(&d_desc, desc.size());
+    carve.add(&d_coef, c->coef.size());
+    carve.add(&p.spins, (size_t)R * p.slot_stride);
+    carve.add(&p.E, (size_t)R);
+    carve.add(&p.M, (size_t)R);
+    carve.add(&p.rung_of_slot, (size_t)R);
+    carve.add(&p.slot_of_rung, (size_t)R);
+    carve.add(&p.acc, (size_t)R * kAccCount);
+    carve.add(&p.swap_stats, 2 * (size_t)R);
+    carve.add(&p.mbox, (size_t)max_passes * R);
+    carve.add(&p.status, (size_t)4);
+    carve.add(&c->staging, (size_t)R * N * P);
+    if ((e = carve.allocate(c)) != cudaSuccess) {
         free_ctx(c);
         return create_fail(e == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA, "cudaMalloc: %s",
                            cudaGetErrorString(e));
