@@ -1164,6 +1164,10 @@ static const void* sweep_fn(const LaunchPlan& plan) {
             return pre ? (const void*)sweep_packed_kernel<4, true, 1024> : (const void*)sweep_packed_kernel<4, false, 1024>;
         return pre ? (const void*)sweep_packed_kernel<8, true, 1024> : (const void*)sweep_packed_kernel<8, false, 1024>;
     }
+    if (!pre && plan.threads <= 384)
+        // blocks of at most 384 threads may use up to 168 registers per thread
+        return plan.dclass == 4 ? (const void*)sweep_packed_kernel<4, false, 384>
+                                : (const void*)sweep_packed_kernel<8, false, 384>;
     if (plan.dclass == 4)
         return pre ? (const void*)sweep_packed_kernel<4, true, 512> : (const void*)sweep_packed_kernel<4, false, 512>;
     return pre ? (const void*)sweep_packed_kernel<8, true, 512> : (const void*)sweep_packed_kernel<8, false, 512>;
