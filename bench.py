@@ -49,7 +49,7 @@ KERNEL_NAMES = {1: "sweep_kernel (byte-wise)", 2: "sweep_packed_kernel (int8, in
 # DRAM bytes (read + write) per launch of the sweep kernel, from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum: (workload, kernel path, sweeps per launch)
 # -> bytes. Must be retaken (or removed) whenever that kernel changes.
-MEASURED_TRAFFIC = {("regular3_n256_p64_r64", 2, 1000): (1554944 + 1722880) // 2,
+MEASURED_TRAFFIC = {("regular3_n256_p64_r64", 2, 1000): (1648384 + 1893632) // 2,
                     ("chimera16_n2048_p128_r96", 4, 500): (26632448 + 11264 + 27145472) // 2}
 # The same for the batched launch: (requests, sweeps each) -> DRAM bytes per launch.
 MEASURED_BATCH_TRAFFIC = {(512, 1000): 1298192722688 + 1345140493056}
