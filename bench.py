@@ -9,8 +9,10 @@ P=64 Trotter copies, R=64 rungs (geometric Gamma 0.05..4.0 at T=0.02), 2000 swee
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
 Under torchrun each rank runs its own independent problem (different seed) on its own GPU:
-the work partitions into independent problems, so there is no data-path collective; the
-only collective is the max-over-ranks of the timed region.
+the work partitions into independent problems, so there is no data-path collective. The
+only collectives are the barriers around each timed region and the max over ranks of its
+time (with the sum of the units): the device-timed value, the end-to-end value and the
+batched values are all whole-job figures. The serving replay runs on rank 0 alone.
 
 --impl reference times the CPU oracle (the plain C implementation the tests compare against)
 on this machine's host cores, on a bounded sample of the same workload.
@@ -237,7 +239,7 @@ def run_ours(args, rank, world, local_rank):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, prob, pt, torch)
+        e2e = run_e2e(args, prob, pt, torch, world, torch.device("cuda", local_rank))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -246,7 +248,8 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
     batched = None
     if not args.no_batched:
-        batched = run_batched(args, pt, instances, torch, n_sm, sm_max)
+        batched = run_batched(args, pt, instances, torch, n_sm, sm_max, rank, world,
+                              torch.device("cuda", local_rank))
     serving = None
     if not args.no_serving and rank == 0:
         serving = run_serving(args, torch, batched, local_rank)
@@ -283,12 +286,14 @@ def run_ours(args, rank, world, local_rank):
     }
 
 
-def run_batched(args, pt, instances, torch, n_sm, sm_max):
+def run_batched(args, pt, instances, torch, n_sm, sm_max, rank=0, world=1, device=None):
     """Many independent requests in one persistent launch vs one pt_run per request.
 
     Workload: `batch_count` requests, N ~ U{32..1024} (3-regular or K4,4 cells), P ~ U{32,64,128},
-    R ~ U{16..128}, `batch_sweeps` sweeps each, a swap pass after every sweep."""
-    probs = instances.batch_problems(count=args.batch_count, index=1, n_sweeps=args.batch_sweeps)
+    R ~ U{16..128}, `batch_sweeps` sweeps each, a swap pass after every sweep. With several
+    ranks each runs its own request set; both values are the attempts of all ranks over the
+    slowest rank's device time."""
+    probs = instances.batch_problems(count=args.batch_count, index=1 + rank, n_sweeps=args.batch_sweeps)
     attempts = sum(p.attempts_per_sweep * p.n_sweeps for p in probs)
     stream = torch.cuda.Stream()
     t_create = time.perf_counter()
@@ -297,13 +302,18 @@ def run_batched(args, pt, instances, torch, n_sm, sm_max):
     info = b.info()
     b.run()
     b.sync()
+    torch.cuda.synchronize()
+    barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     b.run()
     e1.record(stream)
     b.sync()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    barrier(world)
+    local_ms = e0.elapsed_time(e1)
+    max_s, all_attempts = reduce_timing(local_ms / 1e3, float(attempts), world, device=device)
+    ms = max_s * 1e3
     b_graph = b.info().graph
     b.close()
     # plain path: every request through its own pt_create + pt_run, one after another
@@ -311,6 +321,7 @@ def run_batched(args, pt, instances, torch, n_sm, sm_max):
     for p in probs:
         ctxs.append(pt.PT.from_problem(p, stream=stream.cuda_stream))
     torch.cuda.synchronize()
+    barrier(world)
     launches0 = sum(int(c.get_info().kernel_launches) for c in ctxs)  # create (and plan timing) excluded
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record(stream)
@@ -318,25 +329,27 @@ def run_batched(args, pt, instances, torch, n_sm, sm_max):
         c.run(p.n_sweeps, p.sweeps_per_swap)
     p1.record(stream)
     torch.cuda.synchronize()
-    plain_ms = p0.elapsed_time(p1)
+    barrier(world)
+    plain_ms = reduce_timing(p0.elapsed_time(p1) / 1e3, float(attempts), world, device=device)[0] * 1e3
     plain_launches = sum(int(c.get_info().kernel_launches) for c in ctxs) - launches0
     for c in ctxs:
         c.close()
-    value = attempts / (ms / 1e3)
+    value = all_attempts / (ms / 1e3)
+    local_value = attempts / (local_ms / 1e3)  # this GPU's rate, against this GPU's peak
     deg = [max(np.bincount(np.concatenate([p.ei, p.ej]), minlength=p.n)) for p in probs]
     ialg = float(np.average([alg_instr_per_attempt(int(d)) for d in deg],
                             weights=[p.attempts_per_sweep * p.n_sweeps for p in probs]))
     peak = n_sm * 128 * sm_max * 1e6 / 1e12
     return {"workload": "%d requests, N~U{32..1024} 3-regular or K4,4 cells, P~U{32,64,128}, R~U{16..128}, "
                         "%d sweeps, swap pass after every sweep" % (args.batch_count, args.batch_sweeps),
-            "value": value, "unit": "attempts/s", "ms": ms, "attempts": attempts,
-            "plain_value": attempts / (plain_ms / 1e3), "plain_ms": plain_ms,
+            "value": value, "unit": "attempts/s", "ms": ms, "attempts": all_attempts,
+            "plain_value": all_attempts / (plain_ms / 1e3), "plain_ms": plain_ms,
             "speedup_vs_plain": plain_ms / ms, "gpu_launches": 1, "plain_gpu_launches": plain_launches,
             "cluster": info.cluster, "n_clusters": info.n_clusters, "smem_bytes": int(info.smem_bytes),
             "group_widen": info.group_widen, "autotuned_layouts": info.tuned_layouts,
             "create_and_autotune_s": create_s, "graph_replay": bool(b_graph),
-            "roofline": {"bound": "alu", "achieved": ialg * value / 1e12, "peak": peak, "unit": "Tinstr/s",
-                         "frac": ialg * value / 1e12 / peak, "kernel": "batch_kernel",
+            "roofline": {"bound": "alu", "achieved": ialg * local_value / 1e12, "peak": peak, "unit": "Tinstr/s",
+                         "frac": ialg * local_value / 1e12 / peak, "kernel": "batch_kernel",
                          "traffic": MEASURED_BATCH_TRAFFIC.get((args.batch_count, args.batch_sweeps)),
                          "traffic_unit": "DRAM bytes per launch (ncu)"}}
 
@@ -380,8 +393,11 @@ def run_serving(args, torch, batched, gpu_index=0):
     return out
 
 
-def run_e2e(args, prob, pt, torch):
-    """Create from pinned host arrays, run, read state and statistics back, destroy."""
+def run_e2e(args, prob, pt, torch, world=1, device=None):
+    """Create from pinned host arrays, run, read state and statistics back, destroy.
+
+    With several ranks each runs its own problem; the value is the units of all ranks over the
+    slowest rank's time, like the device-timed value."""
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
     ei, ej, J, h = pin(prob.ei), pin(prob.ej), pin(prob.J), pin(prob.h)
     out = torch.empty((prob.R, prob.n, prob.P), dtype=torch.int8).pin_memory().numpy()
@@ -399,13 +415,18 @@ def run_e2e(args, prob, pt, torch):
     for _ in range(max(1, min(args.warmup, 2))):
         once()
     torch.cuda.synchronize()
+    barrier(world)
     t0 = time.perf_counter()
     n = max(1, min(args.steps, 5))
     for _ in range(n):
         once()
-    dt = (time.perf_counter() - t0) / n
+    torch.cuda.synchronize()
+    local_s = time.perf_counter() - t0
+    barrier(world)
+    max_s, units = reduce_timing(local_s, float(prob.attempts_per_sweep * prob.n_sweeps * n), world, device=device)
+    dt = max_s / n
     d2h = prob.R * prob.n * prob.P + prob.R * 8 * 8 + 2 * (prob.R - 1) * 8 + prob.R * 4
-    return {"value": prob.attempts_per_sweep * prob.n_sweeps / dt, "unit": "attempts/s",
+    return {"value": units / max_s, "unit": "attempts/s",
             "h2d_bytes_per_step": int(res["h2d"]), "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
             "what": "pt_create from pinned host arrays + pt_run + pt_read_state + pt_read_observables + pt_destroy"}
 
