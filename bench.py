@@ -443,14 +443,15 @@ def cpu_baseline(prob, budget_s=12.0, threads=None):
     t0 = time.perf_counter()
     o.run(2, prob.sweeps_per_swap)
     probe = max(time.perf_counter() - t0, 1e-6) / 2
-    n = int(max(2, min(prob.n_sweeps, budget_s / probe)))
+    # the chain continues past one step's sweeps until the time budget is spent
+    n = int(max(2, min(100 * max(prob.n_sweeps, 1), budget_s / probe)))
     t0 = time.perf_counter()
     o.run(n, prob.sweeps_per_swap)
     dt = time.perf_counter() - t0
     o.close()
     return {"value": prob.attempts_per_sweep * n / dt, "unit": "attempts/s", "cores": threads, "kind": "oracle",
-            "sample": "%d of %d sweeps (+ swap passes) of the same problem, OpenMP over chains, %.1f s"
-                      % (n, prob.n_sweeps, dt)}
+            "sample": "%d sweeps (+ swap passes; %.2f steps of %d sweeps) of the same problem, one continuous "
+                      "chain run, OpenMP over chains, %.1f s" % (n, n / max(prob.n_sweeps, 1), prob.n_sweeps, dt)}
 
 
 def run_reference(args, rank, world):
