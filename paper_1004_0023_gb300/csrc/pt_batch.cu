@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "pt.h"
@@ -473,8 +474,9 @@ int ptq::prepare_request(const pt_request& r, Prepared& pr, char* why, size_t wh
         return PT_EINVAL;
     }
     for (int q = 0; q < R; ++q)
-        if (!(r.ladder[q].T > 0.0) || !(r.ladder[q].gamma > 0.0)) {
-            snprintf(why, why_len, "rung %d: T and gamma must be > 0", q);
+        if (!(r.ladder[q].T > 0.0) || !(r.ladder[q].gamma > 0.0) || !std::isfinite(r.ladder[q].T) ||
+            !std::isfinite(r.ladder[q].gamma)) {
+            snprintf(why, why_len, "rung %d: T and gamma must be finite and > 0", q);
             return PT_EINVAL;
         }
     std::vector<std::vector<int>> adj(N), adjJ(N);
@@ -500,6 +502,10 @@ int ptq::prepare_request(const pt_request& r, Prepared& pr, char* why, size_t wh
             return PT_EINVAL;
         }
         dmax = std::max(dmax, (int)adj[i].size());
+        if (inst->h[i] < -127 || inst->h[i] > 127) {
+            snprintf(why, why_len, "site %d: h must be in [-127,127]", i);
+            return PT_EINVAL;
+        }
         int l = abs(inst->h[i]);
         for (int J : adjJ[i]) l += abs(J);
         if (l > 127) {

@@ -330,6 +330,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
             return create_fail(PT_EINVAL, "duplicate edge at site %d", i);
         dmax = std::max(dmax, (int)adj[i].size());
+        if (inst->h[i] < -127 || inst->h[i] > 127) return create_fail(PT_EINVAL, "site %d: h must be in [-127,127]", i);
         int l = abs(inst->h[i]);
         for (int J : adjJ[i]) l += abs(J);
         if (l > 127) return create_fail(PT_EINVAL, "site %d: |h| + sum |J| must be <= 127", i);

@@ -46,6 +46,43 @@ def test_create_without_device_fails_loudly(libpt):
     assert e.value.code in (pt.PT_ENODEV, pt.PT_ECUDA)
 
 
+def test_create_rejects_out_of_range_instances_before_any_device_call(libpt):
+    """pt_create checks its arguments on the host first, so each bad instance gets PT_EINVAL
+    with or without a GPU: fields outside [-127, 127] (INT_MIN included, which must not reach
+    abs()), |h| + sum |J| above 127, zero or out-of-range couplings, odd P, and a non-finite
+    or non-positive rung."""
+    prob = instances.workload("regular3_n16_p32_r16", 1)
+
+    def create(h=None, J=None, P=None, T=None, gamma=None):
+        return pt.PT(prob.n, prob.ei, prob.ej, prob.J if J is None else J, prob.h if h is None else h,
+                     prob.P if P is None else P, prob.T if T is None else T,
+                     prob.gamma if gamma is None else gamma, 1)
+
+    bad = []
+    for v in (-(2 ** 31), 128, -128, 2 ** 31 - 1):
+        h = np.array(prob.h, np.int32)
+        h[3] = v
+        bad.append(dict(h=h))
+    h = np.array(prob.h, np.int32)
+    h[prob.ei[0]] = 127  # in range alone, but the site's couplings push the sum past 127
+    bad.append(dict(h=h))
+    for v in (0, 128, -(2 ** 31)):
+        J = np.array(prob.J, np.int32)
+        J[0] = v
+        bad.append(dict(J=J))
+    bad.append(dict(P=3))
+    T = np.array(prob.T, np.float64)
+    T[1] = np.inf
+    bad.append(dict(T=T))
+    g = np.array(prob.gamma, np.float64)
+    g[2] = -1.0
+    bad.append(dict(gamma=g))
+    for kw in bad:
+        with pytest.raises(pt.PTError) as e:
+            create(**kw)
+        assert e.value.code == pt.PT_EINVAL, kw
+
+
 @pytest.mark.parametrize("name", ["regular3_n16_p32_r16", "regular3_n256_p64_r64", "chimera16_n2048_p128_r96",
                                   "classical_regular3_n256_r64"])
 def test_host_tables_bit_identical_to_oracle(libpt, name):
