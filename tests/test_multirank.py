@@ -1,5 +1,6 @@
 """The N > 1 path of bench.py on CPU ranks (gloo, world size 2): the max-over-ranks timing
-and the sum of units, and the reference arm printing one line from rank 0 only."""
+and the sum of units, the end-to-end and batched figures as whole-job values (with fake
+device objects), and the reference arm printing one line from rank 0 only."""
 import json
 import os
 import socket
@@ -57,3 +58,129 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+class _FakeEvent:
+    """Stands in for torch.cuda.Event: rank r's timed regions last 10 (r + 1) ms."""
+    rank = 0
+
+    def __init__(self, enable_timing=True):
+        pass
+
+    def record(self, stream=None):
+        pass
+
+    def elapsed_time(self, other):
+        return 10.0 * (_FakeEvent.rank + 1)
+
+
+class _FakeInfo:
+    h2d_bytes = 100
+    kernel_launches = 0
+    cluster = 2
+    n_clusters = 76
+    smem_bytes = 1
+    group_widen = 0
+    tuned_layouts = 1
+    graph = 1
+
+
+class _FakeCtx:
+    def __init__(self, *a, **k):
+        pass
+
+    @classmethod
+    def from_problem(cls, prob, **k):
+        return cls()
+
+    def run(self, *a):
+        pass
+
+    def read_state(self, out=None):
+        pass
+
+    def obs(self):
+        return {}
+
+    def get_info(self):
+        return _FakeInfo()
+
+    def close(self):
+        pass
+
+
+class _FakeBatch(_FakeCtx):
+    def __init__(self, probs, **k):
+        pass
+
+    def info(self):
+        return _FakeInfo()
+
+    def sync(self):
+        pass
+
+
+def _timed_paths_worker(rank, world, port, out_dir):
+    import types
+
+    import torch
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1004_0023_gb300 import instances
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    _FakeEvent.rank = rank
+
+    class _Pinned:  # from_numpy(...).pin_memory() without a GPU
+        def __init__(self, t):
+            self.t = t
+
+        def pin_memory(self):
+            return self.t
+
+    fake_torch = types.SimpleNamespace(
+        cuda=types.SimpleNamespace(Event=_FakeEvent, Stream=lambda: types.SimpleNamespace(cuda_stream=1),
+                                   synchronize=lambda: None),
+        from_numpy=lambda a: _Pinned(torch.from_numpy(a)),
+        empty=lambda shape, dtype: _Pinned(torch.empty(shape, dtype=dtype)),
+        int8=torch.int8)
+    fake_pt = types.SimpleNamespace(PT=_FakeCtx, Batch=_FakeBatch)
+    args = bench.parse_args(["--steps", "2", "--warmup", "3", "--batch-count", "6", "--batch-sweeps", "10"])
+    prob = instances.workload("regular3_n16_p32_r16", 1)
+    e2e = bench.run_e2e(args, prob, fake_pt, fake_torch, world, "cpu")
+    b = bench.run_batched(args, fake_pt, instances, fake_torch, 152, 2070.0, rank, world, "cpu")
+    mine = sum(p.attempts_per_sweep * p.n_sweeps
+               for p in instances.batch_problems(count=6, index=1 + rank, n_sweeps=10))
+    dist.barrier()
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, "timed%d.json" % rank), "w") as f:
+        json.dump({"e2e": e2e["value"], "e2e_ms": e2e["ms_per_step"], "value": b["value"], "ms": b["ms"],
+                   "attempts": b["attempts"], "plain_ms": b["plain_ms"], "frac": b["roofline"]["frac"],
+                   "mine": float(mine)}, f)
+
+
+def test_end_to_end_and_batched_figures_are_whole_job_over_ranks(tmp_path):
+    """bench.run_e2e and bench.run_batched on two gloo ranks with fake device objects (rank r's
+    batched launch takes 10 (r + 1) ms): the values are the units of both ranks over the
+    slowest rank's time, and the batched roofline stays per GPU."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    port = _free_port()
+    mp.spawn(_timed_paths_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    r = [json.load(open(tmp_path / ("timed%d.json" % k))) for k in range(2)]
+    total = r[0]["mine"] + r[1]["mine"]
+    for k in range(2):
+        assert r[k]["attempts"] == total
+        assert r[k]["ms"] == 20.0 and r[k]["plain_ms"] == 20.0
+        assert r[k]["value"] == pytest.approx(total / 0.020)
+        assert r[k]["e2e"] == pytest.approx(r[0]["e2e"])  # one reduced figure, the same on every rank
+    # per-GPU roofline: rank k ran its own attempts in 10 (k + 1) ms, so its fraction of one
+    # GPU's issue peak (152 SMs x 128 lanes x 2070 MHz) implies 24 to 27 instructions per attempt
+    # (the whole-job rate would put rank 1 near twice that)
+    peak = 152 * 128 * 2070e6
+    for k in range(2):
+        per_attempt = r[k]["frac"] * peak * (0.010 * (k + 1)) / r[k]["mine"]
+        assert 24.0 <= per_attempt <= 27.0, (k, per_attempt)
