@@ -276,10 +276,13 @@ const char* pt_batch_last_error(const pt_batch* b);
 /* ---- Serving: continuous batching ----------------------------------------------------
  * A request (pt_request) is copied and queued by pt_server_submit. pt_server_step never
  * blocks: it reports the requests that have finished, then admits queued requests in
- * arrival order while a slot (max_active) and room in the device arena are free. An
+ * arrival order while a slot (max_active) and room in the device arena are free, and while
+ * the chains in flight (one CTA each, a batched launch's CTAs until it ends) plus the
+ * request's own R stay within the device's SM count, so that every admitted request is
+ * resident at once (a request larger than that is admitted when nothing else runs). An
  * admitted request's state and counters live in the arena; all of its sweeps are launched
- * at once on one stream of a pool (one CTA per chain), so requests that arrive while others
- * run overlap with them on the device. When a backlog of 8 or more requests waits, they
+ * at once on the least-loaded stream of a pool (one CTA per chain), so requests that arrive
+ * while others run overlap with them on the device. When a backlog of 8 or more requests waits, they
  * start together in one persistent batched launch (as pt_batch_run) instead; each of them
  * is reported finished as soon as its own chains are written back, not when the whole
  * launch ends. In stepped
