@@ -196,10 +196,25 @@ void ptq::level_schedule(int N, const std::vector<std::vector<int>>& adj, std::v
             ready.erase(ready.begin(), ready.begin() + take);
             ready.insert(ready.end(), next.begin(), next.end());
         }
+        // keep the as-early-as-possible levels where the fill takes more rounds than they do
+        // (it can, by one, on long chains with small rounds)
+        std::vector<int> ca(nlev, 0), cb(nlev, 0);
         for (int i = 0; i < N; ++i) {
-            l0[i] = level[2 * i];
-            l1[i] = level[2 * i + 1];
+            ca[l0[i]]++;
+            ca[l1[i]]++;
+            cb[level[2 * i]]++;
+            cb[level[2 * i + 1]]++;
         }
+        long long ra = 0, rb = 0;
+        for (int l = 0; l < nlev; ++l) {
+            ra += (ca[l] + per_round - 1) / per_round;
+            rb += (cb[l] + per_round - 1) / per_round;
+        }
+        if (rb <= ra)
+            for (int i = 0; i < N; ++i) {
+                l0[i] = level[2 * i];
+                l1[i] = level[2 * i + 1];
+            }
     }
     std::vector<int> count(nlev + 1, 0);
     for (int i = 0; i < N; ++i) {

@@ -228,3 +228,52 @@ def test_ctypes_structs_match_the_c_header(tmp_path):
         assert int(out[name]) == ctypes.sizeof(cls), name
         for f in cls._fields_:
             assert int(out["%s.%s" % (name, f[0])]) == getattr(cls, f[0]).offset, (name, f[0])
+
+
+def _random_graph(kind, n, rng):
+    if kind == "sparse":
+        p = rng.uniform(0.0, min(1.0, 8.0 / n))
+        return [(i, j) for i in range(n) for j in range(i + 1, n) if rng.random() < p]
+    if kind == "tree":
+        return [(int(rng.integers(0, i)), i) for i in range(1, n)]
+    if kind == "star":
+        return [(0, i) for i in range(1, n)]
+    if kind == "path":  # a path through the sites in random order: long dependency chains
+        perm = rng.permutation(n)
+        return [(int(perm[i]), int(perm[i + 1])) for i in range(n - 1)]
+    ei, ej = instances.random_regular_graph(n, 3, rng)
+    return list(zip(ei.tolist(), ej.tolist()))
+
+
+@pytest.mark.parametrize("kind", ["sparse", "tree", "star", "path", "regular3"])
+def test_balanced_schedule_on_random_graphs(kind):
+    """Over random graphs of each family and round sizes from 1 to 1000: the balanced
+    schedule is a permutation of the updates, keeps every dependency strictly earlier, has
+    the as-early-as-possible level count, and never takes more kernel rounds than the
+    as-early-as-possible schedule (on long chains with small rounds the fill alone can take
+    one more; the as-early-as-possible levels are kept there)."""
+    rng = np.random.default_rng({"sparse": 1, "tree": 2, "star": 3, "path": 4, "regular3": 5}[kind])
+    for _ in range(24):
+        n = int(rng.integers(2, 200))
+        if kind == "regular3":
+            n += n % 2
+            n = max(n, 4)
+        pairs = _random_graph(kind, n, rng)
+        ei = np.array([a for a, _ in pairs], np.int32)
+        ej = np.array([b for _, b in pairs], np.int32)
+        _, off0 = pt.make_schedule(n, ei, ej)
+        adj = [set() for _ in range(n)]
+        for a, b in pairs:
+            adj[a].add(b)
+            adj[b].add(a)
+        for k in (1, 2, 3, 4, 7, 8, 16, 32, 48, 96, 1000):
+            items, off = pt.make_schedule(n, ei, ej, items_per_round=k)
+            assert sorted(items.tolist()) == list(range(2 * n))
+            assert off.size == off0.size
+            level = _levels(items, off)
+            for i in range(n):
+                assert level[2 * i] < level[2 * i + 1]
+                for j in adj[i]:
+                    if j < i:
+                        assert level[2 * j] < level[2 * i] and level[2 * j + 1] < level[2 * i + 1]
+            assert _rounds(off, k) <= _rounds(off0, k), (kind, n, k)
