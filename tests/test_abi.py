@@ -93,6 +93,27 @@ def test_host_tables_bit_identical_to_oracle(libpt, name):
     assert np.array_equal(coef.view(np.uint64), o.swap_coef().view(np.uint64))
 
 
+def test_host_tables_bit_identical_to_oracle_on_random_ladders(libpt):
+    """The FP64 tables pt_create builds equal the oracle's bit for bit on random ladders:
+    T and Gamma spread over four decades (so thresholds run from "always" through the
+    exponential range down to 0), P from 1 (classical, Gamma = 0) to 4096, Lmax up to 127.
+    A one-site instance with h = Lmax gives the oracle the same table size."""
+    rng = np.random.default_rng(11)
+    for _ in range(40):
+        P = int(rng.choice([1, 2, 4, 8, 16, 32, 64, 128, 512, 4096]))
+        R = int(rng.integers(1, 12))
+        lmax = int(rng.integers(1, 128))
+        T = 10.0 ** rng.uniform(-2.0, 2.0, R)
+        gamma = np.zeros(R) if P == 1 else 10.0 ** rng.uniform(-2.0, 2.0, R)
+        prob = instances.tiny_problem(1, [], [], [lmax], P, T, gamma)
+        o = Oracle.from_problem(prob)
+        assert o.lmax == lmax
+        thr, coef = pt.make_tables(P, T, gamma, lmax)
+        assert np.array_equal(thr, o.flip_table()), (P, R, lmax)
+        assert np.array_equal(coef.view(np.uint64), o.swap_coef().view(np.uint64)), (P, R, lmax)
+        o.close()
+
+
 def test_host_tables_reject_bad_ladder(libpt):
     with pytest.raises(pt.PTError):
         pt.make_tables(4, [1.0, 0.0], [1.0, 1.0], 3)
