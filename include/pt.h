@@ -78,7 +78,7 @@ typedef struct {
     int32_t kernel_path;        /* 0 = auto, 1 = byte-wise, 2 = packed with inline random
                                    words, 3 = packed with random words produced one sweep
                                    ahead by dedicated warps, 4 = packed with one bit per
-                                   copy in shared memory (paths 2-5 need P % 8 == 0 and
+                                   copy in shared memory (paths 2-6 need P % 8 == 0 and
                                    degree <= 7), 5 = path 3 with each chain split over a
                                    cluster of two CTAs, one half of the Trotter copies each
                                    (needs P % 16 == 0 and all R chains resident at once;
