@@ -171,10 +171,12 @@ int pt_sweep(pt_ctx* ctx, int64_t n);
 int pt_swap(pt_ctx* ctx);
 
 /* Fig. 4's loop: n_sweeps sweeps with a swap pass after every sweeps_per_swap-th sweep
- * (0 = no swaps). Bit-identical to the equivalent sequence of pt_sweep / pt_swap calls. */
+ * (0 = no swaps, at most 2^30). Bit-identical to the equivalent sequence of pt_sweep /
+ * pt_swap calls. */
 int pt_run(pt_ctx* ctx, int64_t n_sweeps, int32_t sweeps_per_swap);
 
-/* Copy the state, rung-ordered int8 (+1/-1), into out (bytes >= R*N*P). Synchronises. */
+/* Copy the state, rung-ordered int8 (+1/-1), into out (bytes >= R*N*P). Synchronises.
+ * (Fig. 6's copy of the chains back to the host, here only when the caller asks.) */
 int pt_read_state(pt_ctx* ctx, int8_t* out, size_t bytes);
 
 /* Overwrite the state (rung-ordered int8 +1/-1, bytes = R*N*P) and recompute E and M
@@ -296,7 +298,10 @@ typedef struct {
     int64_t arena_bytes;    /* device memory for admitted requests (0 = half of the free memory) */
     int32_t max_active;     /* requests on the device at once (0 = 512) */
     int32_t quantum_sweeps; /* sweeps per request per step (0 = 100) */
-    int32_t cluster_size;   /* CTAs per cluster (0 = 2) */
+    int32_t cluster_size;   /* CTAs per cluster of batched launches (1..16), or 0: 2 in
+                               stepped mode; a backlog launch in streamed mode takes the
+                               largest of 2, 4, 8, 16 whose clusters (one per request) fit the
+                               SMs no other launch holds */
     int32_t reserved[3];    /* reserved[1] = 1: stepped mode (a quantum of sweeps per launch);
                                reserved[0] = 1: stepped mode with chains packed on clusters only */
 } pt_server_options;
@@ -327,21 +332,23 @@ const char* pt_server_last_error(const pt_server* s);
 
 /* ---- Running on caller-owned device memory, without allocating ----------------------
  * The paper has no counterpart to this entry point. It is for callers that cannot allocate
- * device memory, neither themselves nor through this library: work recorded into a CUDA
- * graph by stream capture (allocations are not captured), latency-critical loops that must
- * not enter the allocator, and embedding runtimes that hand out device memory only from
- * their own pool. pt_create allocates; such a caller instead builds the problem with
- * pt_make_tables and pt_make_schedule, copies it into device memory it owns, and calls
- * pt_run_noalloc, which allocates nothing (no cudaMalloc, no cudaFree, no library routine
- * that allocates).
+ * device memory, neither themselves nor through this library: latency-critical loops that
+ * must not enter the allocator (cudaMalloc / cudaFree can synchronise the device and take
+ * locks other threads hold), and embedding runtimes or frameworks that hand out device
+ * memory only from their own accounted pool, or fix the process's device memory at start-up.
+ * pt_create allocates; such a caller instead builds the problem with pt_make_tables and
+ * pt_make_schedule, copies it into device memory it owns, and calls pt_run_noalloc, which
+ * allocates nothing (no cudaMalloc, no cudaFree, no library routine that allocates).
  *
  * The only scratch memory the kernel needs, the swap mailboxes, is one fixed array of
  * PT_NOALLOC_MAILBOXES 16-byte entries (256 KiB) that every GPU loading this library holds
  * until the process exits. All calls share it and it keeps the last call's contents; each
  * launch clears the entries it uses. Calls that overlap on the GPU (other streams, other
  * threads) race on it: serialise them. The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture. */
+ * device address (cudaGetSymbolAddress, with that device current) and caches it for the
+ * process; make that first call before any stream capture. cuda_stream must belong to the
+ * current device, and a device reset (cudaDeviceReset) makes the cached address stale: do
+ * not call this on a device after its reset. */
 #define PT_NOALLOC_MAILBOXES 16384  /* swap passes x rungs one launch can hold */
 
 typedef struct {
@@ -372,9 +379,11 @@ typedef struct {
 
 /* Same arithmetic and bits as pt_run(n_sweeps, sweeps_per_swap) on a context in the same
  * state, launched on cuda_stream (asynchronous). All pointers are device pointers owned by
- * the caller. Returns PT_EINVAL (message in pt_noalloc_last_error) for sizes beyond the
- * fixed mailbox array or the shared memory of one CTA, PT_EOVERFLOW for counters past
- * 2^32 - 1, PT_ECUDA if a launch fails. */
+ * the caller. A call whose swap passes x R exceed PT_NOALLOC_MAILBOXES runs as several
+ * launches of whole swap intervals, each clearing the mailboxes it uses first. Returns
+ * PT_EINVAL (message in pt_noalloc_last_error) for R beyond the fixed mailbox array, a chain
+ * beyond the shared memory of one CTA, or sweeps_per_swap > 2^30; PT_EOVERFLOW for counters
+ * past 2^32 - 1; PT_ECUDA if a launch fails. */
 int pt_run_noalloc(const pt_device_problem* prob, int64_t n_sweeps, int32_t sweeps_per_swap,
                    int32_t wait_timeout_ms, void* cuda_stream);
 const char* pt_noalloc_last_error(void);
@@ -382,10 +391,13 @@ const char* pt_noalloc_last_error(void);
 /* Wait for all queued work of the context. */
 int pt_sync(pt_ctx* ctx);
 
-/* Free the context (synchronises first). NULL is a no-op. */
+/* Free the context (synchronises first). NULL is a no-op. (Fig. 6: the device's copy of
+ * the problem is released once the run ends.) */
 int pt_destroy(pt_ctx* ctx);
 
-/* One-line message of the last error on ctx (or of the last failed create if ctx is NULL). */
+/* One-line message of the last error on ctx (or of the last failed create if ctx is NULL).
+ * The paper's kernel launches can fail and are retried by the host (Fig. 7); here a failure
+ * is reported once, with its reason, and stays (sticky) on the context. */
 const char* pt_last_error(const pt_ctx* ctx);
 
 #ifdef __cplusplus

@@ -852,9 +852,15 @@ static int enqueue_sweeps(pt_ctx* c, long long n, int sps) {
     // chunks of at most max_passes swap passes (mailbox capacity), aligned to the swap interval
     long long done = 0;
     while (done < n) {
+        // with swaps, whole intervals only (n is a multiple of sps), so every launch starts on
+        // an interval boundary
         long long chunk = n - done;
-        if (sps > 0) chunk = std::min<long long>(chunk, (long long)c->max_passes * sps);
-        chunk = std::min<long long>(chunk, 1ll << 30);
+        if (sps > 0) {
+            chunk = std::min<long long>(chunk, (long long)c->max_passes * sps);
+            chunk = std::min<long long>(chunk, ((1ll << 30) / sps) * sps);
+        } else {
+            chunk = std::min<long long>(chunk, 1ll << 30);
+        }
         const int passes = sps > 0 ? (int)(chunk / sps) : 0;
         if (passes > 0 && c->q + passes - c->mbox_clear_q >= kTagPeriod - 1) {
             // a mailbox tag is q mod (2^24 - 1) + 1: clear before any tag value could repeat
@@ -893,7 +899,8 @@ extern "C" int pt_swap(pt_ctx* c) {
 extern "C" int pt_run(pt_ctx* c, int64_t n_sweeps, int32_t sps) {
     int g = guard(c);
     if (g) return g;
-    if (n_sweeps < 0 || sps < 0) return ctx_fail(c, PT_EINVAL, "n_sweeps and sweeps_per_swap must be >= 0");
+    if (n_sweeps < 0 || sps < 0 || sps > (1 << 30))
+        return ctx_fail(c, PT_EINVAL, "need n_sweeps >= 0 and 0 <= sweeps_per_swap <= 2^30");
     if (c->t + n_sweeps > c->sweep_limit)
         return ctx_fail(c, PT_EOVERFLOW, "sweep count would exceed %lld", c->sweep_limit);
     if (sps == 0 || c->dp.R == 1) {

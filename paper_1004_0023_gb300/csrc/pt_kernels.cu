@@ -174,7 +174,11 @@ __device__ int eos_decide(const DevProblem& p, const SwapSide& w, int rung, long
     const Mailbox* mb = p.mbox + (size_t)w.pass * R;
     long long pE, pM;
     const unsigned long long start = globaltimer_ns();
-    for (;;) {
+    // the first polls spin (the partner usually publishes within an L2 round trip); later
+    // ones back off with __nanosleep, doubling up to 256 ns, so that a CTA waiting on a slow
+    // partner leaves its issue slots and the L2 to the CTAs sharing its SM
+    unsigned int nap = 0;
+    for (int polls = 0;; ++polls) {
         const unsigned long long wa = ld_relaxed_u64(&mb[w.partner].a);
         const unsigned long long wb = ld_relaxed_u64(&mb[w.partner].b);
         if ((wa & 0xFFFFFFull) == w.tag && (wb & 0xFFFFFFull) == w.tag) {
@@ -186,6 +190,10 @@ __device__ int eos_decide(const DevProblem& p, const SwapSide& w, int rung, long
             atomicCAS(p.status, 0, PT_ETIMEDOUT);
             *abort = 1;
             return rung;
+        }
+        if (polls >= 32) {
+            nap = nap ? min(2u * nap, 256u) : 16u;
+            __nanosleep(nap);
         }
     }
     const int rl = w.rl;

@@ -2,11 +2,12 @@
 // device buffers the caller owns, with no allocation of any kind.
 //
 // Who needs this: callers that cannot allocate device memory, neither themselves nor
-// through this library. Work recorded into a CUDA graph by stream capture cannot call
-// cudaMalloc (allocations are not captured, and some drivers reject them during capture);
-// latency-critical loops must not enter the allocator; and embedding runtimes often hand
-// out device memory only from their own pool. pt_create allocates, so such callers prepare
-// the problem with the host-only helpers, copy it into memory they own, and call this.
+// through this library. Latency-critical loops must not enter the allocator (cudaMalloc
+// and cudaFree can synchronise the device and take locks shared with other threads);
+// embedding runtimes and frameworks often hand out device memory only from their own pool
+// and account for every byte; and some deployments fix the process's device memory at
+// start-up. pt_create allocates, so such callers prepare the problem with the host-only
+// helpers, copy it into memory they own, and call this.
 //
 // The one piece of scratch memory the kernel needs, the swap mailboxes, is the file-scope
 // array below: PT_NOALLOC_MAILBOXES entries of 16 bytes (256 KiB), which every GPU that
@@ -28,6 +29,8 @@ static __device__ __align__(256) Mailbox g_noalloc_mailboxes[PT_NOALLOC_MAILBOXE
 
 // In host code `g_noalloc_mailboxes` only names a host-side stand-in for the symbol; the
 // device address is looked up once per device (with that device current) and cached here.
+// A device reset (cudaDeviceReset) makes a cached address stale, so the entry point must not
+// be called on a device after its reset.
 static std::mutex g_setup_lock;
 static void* g_mailbox_addr[256];
 static bool g_mailbox_ready[256];
@@ -70,7 +73,8 @@ extern "C" int pt_run_noalloc(const pt_device_problem* q, int64_t n_sweeps, int3
         !q->rung_of_slot || !q->slot_of_rung || !q->stats || !q->swap_stats || !q->status)
         return fail(PT_EINVAL, "a device pointer is null");
     if (((uintptr_t)q->spins & 15) != 0) return fail(PT_EINVAL, "spins must be 16-byte aligned");
-    if (n_sweeps < 0 || sweeps_per_swap < 0) return fail(PT_EINVAL, "n_sweeps and sweeps_per_swap must be >= 0");
+    if (n_sweeps < 0 || sweeps_per_swap < 0 || sweeps_per_swap > (1 << 30))
+        return fail(PT_EINVAL, "need n_sweeps >= 0 and 0 <= sweeps_per_swap <= 2^30");
     if (q->t0 < 0 || q->q0 < 0 || q->t0 + n_sweeps > 0xFFFFFFFFll ||
         (sweeps_per_swap > 0 && q->q0 + n_sweeps / sweeps_per_swap > 0xFFFFFFFFll))
         return fail(PT_EOVERFLOW, "sweep or swap-pass counter would exceed 2^32 - 1");
@@ -150,8 +154,12 @@ extern "C" int pt_run_noalloc(const pt_device_problem* q, int64_t n_sweeps, int3
         long long chunk, passes = 0;
         int sps = 0;
         if (done < full) {
+            // whole swap intervals only, so that every launch starts on an interval boundary
+            // and the passes fall on the same sweeps as in one long run
             chunk = full - done;
             if (chunk > max_passes * sweeps_per_swap) chunk = max_passes * sweeps_per_swap;
+            const long long cap = ((1ll << 30) / sweeps_per_swap) * sweeps_per_swap;
+            if (chunk > cap) chunk = cap;
             passes = chunk / sweeps_per_swap;
             sps = sweeps_per_swap;
             // every call shares the array; a mailbox left by an earlier call could carry a
@@ -160,8 +168,8 @@ extern "C" int pt_run_noalloc(const pt_device_problem* q, int64_t n_sweeps, int3
                 return fail(PT_ECUDA, "clearing the mailboxes failed");
         } else {
             chunk = n_sweeps - done;
+            if (chunk > (1ll << 30)) chunk = 1ll << 30;
         }
-        if (chunk > (1ll << 30)) chunk = 1ll << 30;
         if (launch_sweeps(p, plan, t, qq, (int)chunk, sps, timeout_ns, sps > 0, s) != cudaSuccess)
             return fail(PT_ECUDA, "sweep launch failed");
         t += chunk;

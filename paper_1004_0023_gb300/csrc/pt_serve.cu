@@ -134,6 +134,8 @@ struct pt_server {
     unsigned char* arena;
     ArenaAllocator* alloc;
     int max_active, quantum, cluster, threads, n_clusters;
+    bool adaptive_cluster;   // backlog launches pick their cluster size from the free SMs
+    int ncl_by_log2[5];      // clusters of 1, 2, 4, 8, 16 CTAs that fit at once (0: none)
     int wide_threads, n_sm;
     bool wide;
     MultiProblem* d_multi;
@@ -214,6 +216,7 @@ extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream,
     s->max_active = (opt && opt->max_active > 0) ? opt->max_active : 512;
     s->quantum = (opt && opt->quantum_sweeps > 0) ? opt->quantum_sweeps : 100;
     s->cluster = (opt && opt->cluster_size > 0) ? opt->cluster_size : 2;
+    s->adaptive_cluster = !(opt && opt->cluster_size > 0);
     s->threads = 512;
     s->wide_threads = 256;
     s->wide = !(opt && opt->reserved[0] == 1);    // reserved[0] == 1: stepped, packed launches only
@@ -275,6 +278,14 @@ extern "C" int pt_server_create(const pt_server_options* opt, void* cuda_stream,
         return sfail(nullptr, PT_EINVAL, "no cluster of %d CTAs fits (%s)", s->cluster, cudaGetErrorString(e));
     }
     s->n_clusters = ncl;
+    for (int l = 0; l < 5; ++l) {
+        int n = 0;
+        if (batch_max_clusters(1 << l, s->threads, s->smem_cap, &n) != cudaSuccess) {
+            (void)cudaGetLastError();
+            n = 0;
+        }
+        s->ncl_by_log2[l] = n;
+    }
     if (s->streamed) {
         for (int k = 0; k < 16; ++k) {
             cudaStream_t st;
@@ -551,6 +562,32 @@ static int launch_streamed(pt_server* s, ServeReq* q) {
 // Returns 1 (nothing launched) when the arena has no room for the group's block.
 static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
     const int n = (int)g.size();
+    // Cluster size: the given one, or the largest of 2..16 CTAs for which the group's
+    // clusters (one per member at most) still fit the SMs no other launch holds. A member
+    // runs on one cluster, so a small backlog on an idle GPU gets wide clusters (each
+    // request's chains over many SMs, low latency) and a long one gets narrow clusters
+    // (many requests at once, the highest throughput).
+    int K = s->cluster, ncl = s->n_clusters;
+    if (s->adaptive_cluster) {
+        const long long free_sms = std::max<long long>(0, s->n_sm - s->inflight_sms);
+        int l = 1;
+        while (l < 4 && s->ncl_by_log2[l + 1] > 0 && (long long)std::min(n, s->ncl_by_log2[l + 1]) * (2 << l) <= free_sms)
+            ++l;
+        // every member must fit a CTA of that cluster size (narrower clusters hold more chains
+        // per CTA but never need more room than streaming one chain per group)
+        for (; l > 1; --l) {
+            bool ok = true;
+            for (ServeReq* q : g) {
+                BatchInstance I = q->inst;
+                choose_groups(I, 1 << l, s->threads, s->smem_cap);
+                if (batch_smem_bytes(I, 1 << l, s->threads) > s->smem_cap) ok = false;
+            }
+            if (ok) break;
+        }
+        K = 1 << l;
+        ncl = s->ncl_by_log2[l] > 0 ? s->ncl_by_log2[l] : s->n_clusters;
+        if (s->ncl_by_log2[l] <= 0) K = s->cluster;
+    }
     ServeGroup* grp = new ServeGroup();
     const size_t order_off = ((size_t)n * sizeof(BatchInstance) + 255) & ~(size_t)255;
     const size_t ctr_off = order_off + (((size_t)n * sizeof(int32_t) + 255) & ~(size_t)255);
@@ -573,8 +610,8 @@ static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
         int rc = upload_request(s, q, st);
         if (rc) return rc;
         q->inst.n_sweeps = (int)q->remaining;
-        choose_groups(q->inst, s->cluster, s->threads, s->smem_cap);
-        smem = std::max(smem, batch_smem_bytes(q->inst, s->cluster, s->threads));
+        choose_groups(q->inst, K, s->threads, s->smem_cap);
+        smem = std::max(smem, batch_smem_bytes(q->inst, K, s->threads));
         insts[k] = q->inst;
     }
     std::vector<int32_t> order(n);
@@ -602,9 +639,9 @@ static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
     // a flag left in this arena block by an earlier group carries that group's token
     grp->token = (int)(s->group_launches % 2000000000) + 1;
     bp.done_token = grp->token;
-    if ((e = launch_batch(bp, s->cluster, std::min(s->n_clusters, n), s->threads, smem, st)) != cudaSuccess)
+    if ((e = launch_batch(bp, K, std::min(ncl, n), s->threads, smem, st)) != cudaSuccess)
         return sfail(s, PT_ECUDA, "group launch: %s", cudaGetErrorString(e));
-    grp->ctas = std::min(s->n_clusters, n) * s->cluster;
+    grp->ctas = std::min(ncl, n) * K;
     s->inflight_sms += grp->ctas;
     if ((e = cudaEventCreateWithFlags(&grp->done, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventRecord(grp->done, st)) != cudaSuccess)

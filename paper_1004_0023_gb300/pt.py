@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(HERE, "libpt.so")
 
 PT_OK, PT_EINVAL, PT_ENOMEM, PT_ECUDA, PT_EOVERFLOW, PT_ETIMEDOUT, PT_EBUSY, PT_ENODEV = (
     0, -1, -2, -3, -4, -5, -6, -7)
+# fixed swap-mailbox entries of pt_run_noalloc (PT_NOALLOC_MAILBOXES in include/pt.h)
+PT_NOALLOC_MAILBOXES = 16384
 _NAMES = {0: "PT_OK", -1: "PT_EINVAL", -2: "PT_ENOMEM", -3: "PT_ECUDA", -4: "PT_EOVERFLOW",
           -5: "PT_ETIMEDOUT", -6: "PT_EBUSY", -7: "PT_ENODEV"}
 

@@ -1,13 +1,19 @@
 """Serving driver: replays a Poisson arrival trace of PT-QMC requests.
 
 Two modes on the same trace:
-  batched -- the continuous-batching server of the C library (pt_server_*): requests are
-             admitted as slots and arena room free up and advance together in one launch
-             per step;
+  batched -- the continuous-batching server of the C library (pt_server_*). In its default
+             (streamed) mode each request is admitted as soon as a slot, arena room and the
+             SMs its chains need are free, and launched at once with all of its sweeps on a
+             stream of a pool, so requests that arrive while others run overlap with them on
+             the device; a backlog starts together in one persistent batched launch, whose
+             members complete on their own. (Stepped mode instead advances every admitted
+             request by a quantum of sweeps per launch.)
   plain   -- one request at a time, first come first served, each with its own
              pt_create + pt_run + read (one problem per launch).
-Latency = completion time - arrival time (host wall clock); throughput = spin-flip attempts
-of the completed requests / wall time from the first arrival to the last completion.
+Latency = completion time - arrival time (host wall clock), where a request completes once
+its final state and statistics have been read back to the host in both modes; throughput =
+spin-flip attempts of the completed requests / wall time from the first arrival to the last
+completion.
 """
 from __future__ import annotations
 
@@ -72,6 +78,7 @@ def replay_batched(trace, quantum_sweeps=100, max_active=512, arena_bytes=0, clu
         max_mix = max(max_mix, info.active)
         finished = srv.step()
         for rid in finished:
+            srv.result(rid)  # the final state and statistics, read as the plain arm reads them
             done_t[rid] = time.perf_counter() - t0
             srv.release(rid)
         if not finished and not stepped:
@@ -105,9 +112,9 @@ def replay_plain(trace, stream=None, deadline=None):
         ctx.run(prob.n_sweeps, prob.sweeps_per_swap)
         ctx.read_state()
         ctx.obs()
+        lat.append(time.perf_counter() - t0 - arr)  # the result is on the host; teardown follows
         launches += int(ctx.get_info().kernel_launches)
         ctx.close()
-        lat.append(time.perf_counter() - t0 - arr)
         att += prob.attempts_per_sweep * prob.n_sweeps
         k += 1
     wall = (time.perf_counter() - t0) - (trace[0][0] if trace else 0.0)

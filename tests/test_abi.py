@@ -238,6 +238,7 @@ def test_ctypes_structs_match_the_c_header(tmp_path):
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
         for f in cls._fields_:
             lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines.append('printf("PT_NOALLOC_MAILBOXES %d\\n", PT_NOALLOC_MAILBOXES);')
     lines.append("return 0; }")
     src = tmp_path / "abi.c"
     src.write_text("\n".join(lines))
@@ -245,6 +246,7 @@ def test_ctypes_structs_match_the_c_header(tmp_path):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
                                                        check=True).stdout.splitlines())
+    assert int(out["PT_NOALLOC_MAILBOXES"]) == pt.PT_NOALLOC_MAILBOXES
     for name, cls in structs.items():
         assert int(out[name]) == ctypes.sizeof(cls), name
         for f in cls._fields_:

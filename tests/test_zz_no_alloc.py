@@ -1,10 +1,13 @@
-"""pt_run_noalloc against pt_run: same bits on two calls in a row.
+"""pt_run_noalloc against pt_run and the CPU oracle: same bits on two calls in a row.
 
-pt_run_noalloc serves callers that cannot allocate device memory (stream capture into a
-CUDA graph, allocator-free latency loops, runtimes with their own memory pool). Here the
-test itself owns the device buffers (torch tensors) and fills them from the host-only
-helpers; the entry point must leave exactly the state pt_run leaves on a context. The
-tolerance is the one every parity test here uses: zero.
+pt_run_noalloc serves callers that cannot allocate device memory (allocator-free latency
+loops, runtimes and frameworks that hand out device memory only from their own pool). Here
+the test itself owns the device buffers (torch tensors) and fills them from the host-only
+helpers; the entry point must leave exactly the state pt_run leaves on a context, and the
+state the oracle reaches. The tolerance is the one every parity test here uses: zero.
+The cases cover one launch per call, calls that need several launches (more swap passes x
+rungs than the fixed mailbox array holds, so the mailboxes are cleared between launches on
+one stream), and calls whose sweep count is not a multiple of the swap interval.
 """
 import ctypes
 
@@ -84,27 +87,68 @@ def _state_of(torch, t, prob):
     }
 
 
-@pytest.mark.parametrize("name,calls", [("regular3_n16_p32_r16", (300, 211)), ("regular3_n256_p64_r64", (120, 80))])
-def test_noalloc_entry_point_matches_pt_run_on_two_calls_in_a_row(libpt, name, calls):
-    torch = pytest.importorskip("torch")
+_KEYS = ("E", "M", "n_meas", "sum_E", "sum_E2", "sum_M", "sum_M2", "flip_acc", "swap_att", "swap_acc",
+         "replica_at")
+
+
+def _run_and_compare(torch, name, calls, sps, with_oracle=False):
     prob = instances.workload(name, 6)
     ref = pt.PT.from_problem(prob)
+    orc = None
+    if with_oracle:
+        from oracle import Oracle
+
+        orc = Oracle.from_problem(prob, threads=4)
     dp, bufs = _device_problem(torch, prob, ref, None)
     stream = torch.cuda.Stream()
     for n_sweeps in calls:
-        pt.run_noalloc(dp, n_sweeps, 1, 0, stream.cuda_stream)
+        pt.run_noalloc(dp, n_sweeps, sps, 0, stream.cuda_stream)
         dp.t0 += n_sweeps
-        dp.q0 += n_sweeps
-        ref.run(n_sweeps, 1)
+        dp.q0 += n_sweeps // sps
+        ref.run(n_sweeps, sps)
         stream.synchronize()
         got = _state_of(torch, bufs, prob)
-        want = ref.obs()
         assert got["status"] == 0
-        assert np.array_equal(got["state"], ref.read_state())
-        for k in ("E", "M", "n_meas", "sum_E", "sum_E2", "sum_M", "sum_M2", "flip_acc", "swap_att",
-                  "swap_acc", "replica_at"):
-            assert np.array_equal(np.asarray(got[k]), np.asarray(want[k])), (name, n_sweeps, k)
+        wants = [("pt_run", ref.read_state(), ref.obs())]
+        if orc is not None:
+            orc.run(n_sweeps, sps)
+            wants.append(("oracle", orc.read_state(), orc.obs()))
+        for who, state, want in wants:
+            assert np.array_equal(got["state"], state), (name, n_sweeps, who)
+            for k in _KEYS:
+                assert np.array_equal(np.asarray(got[k]), np.asarray(want[k])), (name, n_sweeps, who, k)
+        assert int(ref.obs()["t"]) == dp.t0 and int(ref.obs()["q"]) == dp.q0
     ref.close()
+    if orc is not None:
+        orc.close()
+
+
+@pytest.mark.parametrize("name,calls", [("regular3_n16_p32_r16", (300, 211)), ("regular3_n256_p64_r64", (120, 80))])
+def test_noalloc_entry_point_matches_pt_run_on_two_calls_in_a_row(libpt, name, calls):
+    torch = pytest.importorskip("torch")
+    _run_and_compare(torch, name, calls, 1)
+
+
+def test_noalloc_entry_point_matches_the_oracle_on_two_calls_in_a_row(libpt):
+    torch = pytest.importorskip("torch")
+    _run_and_compare(torch, "regular3_n16_p32_r16", (257, 190), 1, with_oracle=True)
+
+
+def test_noalloc_calls_that_need_several_launches(libpt):
+    # R = 64 rungs leave room for 16384 / 64 = 256 swap passes per launch: 600 sweeps with a
+    # swap after each run as three launches (256, 256, 88 passes), 300 as two, each clearing
+    # the shared mailboxes it uses after the previous launch on the same stream
+    torch = pytest.importorskip("torch")
+    assert 600 * 64 > pt.PT_NOALLOC_MAILBOXES and 300 * 64 > pt.PT_NOALLOC_MAILBOXES
+    _run_and_compare(torch, "regular3_n256_p64_r64", (600, 300), 1)
+
+
+def test_noalloc_sweep_counts_that_are_not_a_multiple_of_the_swap_interval(libpt):
+    # 301 = 100 intervals of 3 sweeps + 1 sweep without a pass; the second call starts on an
+    # interval boundary of its own, as pt_run does; the second case also spans two launches
+    torch = pytest.importorskip("torch")
+    _run_and_compare(torch, "regular3_n16_p32_r16", (301, 152), 3, with_oracle=True)
+    _run_and_compare(torch, "regular3_n256_p64_r64", (1003, 257), 2)
 
 
 def test_noalloc_entry_point_rejects_sizes_beyond_its_fixed_scratch(libpt):
