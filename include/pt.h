@@ -89,7 +89,9 @@ typedef struct {
                                    evaluate the FP64 rule (results are identical either way) */
     int32_t cluster_size;       /* batched launches: CTAs per thread-block cluster (1..16), or
                                    0 = autotune (pt_batch_create times a short run of each
-                                   layout and keeps the fastest; results never depend on it) */
+                                   layout and keeps the fastest, remembered per batch shape --
+                                   every request's N, P, R, degree class, levels and sweeps --
+                                   for the process; results never depend on it) */
     int32_t no_autotune;        /* 0: when kernel_path and threads_per_block are automatic and
                                    the chains are int8 in shared memory, pt_create times a
                                    short run of each candidate plan (paths 2, 3, 5 and 6,
@@ -250,7 +252,8 @@ typedef struct {
     int64_t device_bytes;
     int64_t kernel_launches;
     int64_t h2d_bytes;
-    int32_t tuned_layouts;      /* layouts the autotuner timed (0 = layout given) */
+    int32_t tuned_layouts;      /* layouts the autotuner timed (0 = layout given, or reused:
+                                   the choice is remembered per batch shape for the process) */
     int32_t group_widen;        /* threads per chain: doublings (> 0) or halvings (< 0) of the
                                    width that gives about one update unit per thread in an
                                    average level; fixed layouts use -4 (narrowest that fits) */

@@ -21,6 +21,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "pt.h"
@@ -426,6 +428,31 @@ struct pt_batch {
 };
 
 static thread_local char g_batch_create_msg[256] = "";
+
+// Layouts chosen by the autotuner, per batch shape (every request's sizes, level count and
+// sweeps), for the process: a create of a batch of the same shapes reuses the choice and
+// times nothing. The layout never changes a result, so reuse is always safe.
+struct BatchLayoutChoice {
+    int cluster, widen;
+};
+static std::mutex g_layout_mutex;
+static std::map<std::vector<long long>, BatchLayoutChoice> g_layout_cache;
+
+static std::vector<long long> batch_shape_key(const std::vector<BatchInstance>& insts, int threads) {
+    std::vector<long long> key;
+    key.reserve(insts.size() * 7 + 1);
+    key.push_back(threads);
+    for (const BatchInstance& I : insts) {
+        key.push_back(I.N);
+        key.push_back(I.P);
+        key.push_back(I.R);
+        key.push_back(I.dc);
+        key.push_back(I.n_levels);
+        key.push_back(I.n_sweeps);
+        key.push_back(I.sweeps_per_swap);
+    }
+    return key;
+}
 
 static int bfail(pt_batch* b, int code, const char* fmt, ...) {
     va_list ap;
@@ -894,7 +921,22 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
     }
     b->h2d_bytes += (int64_t)(const_bytes + sizeof(int32_t) * count + map.size() * sizeof(int2));
     if (!fixed_cluster) {
+        const std::vector<long long> key = batch_shape_key(b->h_inst, b->threads);
+        BatchLayoutChoice cached{0, 0};
+        {
+            std::lock_guard<std::mutex> lock(g_layout_mutex);
+            auto it = g_layout_cache.find(key);
+            if (it != g_layout_cache.end()) cached = it->second;
+        }
+        if (cached.cluster > 0 && plan_layout(b, cached.cluster, cached.widen, why, sizeof(why)) == PT_OK) {
+            *out = b;
+            return PT_OK;
+        }
         const int rc = autotune(b);
+        if (rc == PT_OK) {
+            std::lock_guard<std::mutex> lock(g_layout_mutex);
+            g_layout_cache[key] = BatchLayoutChoice{b->cluster, b->widen};
+        }
         if (rc != PT_OK) {
             snprintf(g_batch_create_msg, sizeof(g_batch_create_msg), "%s", b->msg);
             free_batch(b);

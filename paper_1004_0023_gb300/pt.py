@@ -367,9 +367,10 @@ class Batch:
     def sync(self):
         self._check(self.lib.pt_batch_sync(self.handle))
 
-    def read_state(self, k):
+    def read_state(self, k, out=None):
         prob = self.problems[k]
-        out = np.empty((prob.R, prob.n, prob.P), np.int8)
+        if out is None:
+            out = np.empty((prob.R, prob.n, prob.P), np.int8)
         self._check(self.lib.pt_batch_read_state(self.handle, int(k), _ptr(out), out.nbytes))
         return out
 
