@@ -83,7 +83,14 @@ typedef struct {
                                    cluster of two CTAs, one half of the Trotter copies each
                                    (needs P % 16 == 0 and all R chains resident at once;
                                    for short ladders that leave SMs idle), 6 = path 5 with
-                                   the random words computed inline (no producer warps) */
+                                   the random words computed inline (no producer warps),
+                                   7 = every chain of the problem resident on the CTAs of one
+                                   thread-block cluster (cluster_size CTAs, 0 = the fewest
+                                   that hold them), each chain swept by a group of
+                                   group_threads threads, swap passes decided in shared memory
+                                   (needs what paths 2-6 need; for problems too small to fill
+                                   the GPU, whose sweeps would otherwise wait on the swap
+                                   mailboxes between SMs) */
     int32_t producer_threads;   /* paths 3 and 5: threads producing random words (0 = auto) */
     int32_t test_exact_swaps;   /* test hook: 1 = skip the FP32 pre-decision of swaps and always
                                    evaluate the FP64 rule (results are identical either way) */
@@ -94,11 +101,14 @@ typedef struct {
                                    for the process; results never depend on it) */
     int32_t no_autotune;        /* 0: when kernel_path and threads_per_block are automatic and
                                    the chains are int8 in shared memory, pt_create times a
-                                   short run of each candidate plan (paths 2, 3, 5 and 6,
-                                   block sizes 256-512), keeps the fastest and resets the context
-                                   to its initial state; the choice is remembered per shape
-                                   for the process. Results never depend on it. 1: off. */
-    int32_t reserved[3];
+                                   short run of each candidate plan (paths 2, 3, 5, 6 and 7,
+                                   block sizes 256-512, clusters of 1-8 CTAs), keeps the fastest
+                                   and resets the context to its initial state; the choice is
+                                   remembered per shape for the process. Results never depend
+                                   on it. 1: off. */
+    int32_t group_threads;      /* kernel_path 7: threads sweeping one chain (32, 64, ..., 512),
+                                   0 = the narrowest that keeps every chain resident */
+    int32_t reserved[2];
 } pt_options;
 
 /* Statistics (Fig. 4 "gather statistics"; Sec. 5 accumulates in high precision).

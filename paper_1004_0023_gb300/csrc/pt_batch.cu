@@ -53,7 +53,7 @@ struct BatchLayout {
         E = o;      o += up16((size_t)C * 8);
         M = o;      o += up16((size_t)C * 8);
         pub = o;    o += (size_t)2 * C * 16;
-        thr = o;    o += (size_t)ngroups * thr_words * 4;
+        thr = o;    o += (size_t)(I.thr_resident ? I.R : ngroups) * thr_words * 4;
         red = o;    o += up16((size_t)ngroups * (I.group_threads / 32) * 3 * 8);
         chains = o; o += (size_t)nbufs * chain_stride;
         total = o;
@@ -112,6 +112,11 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
             s_E[x] = I.E[c_begin + x];
             s_M[x] = I.M[c_begin + x];
         }
+        if (I.thr_resident)  // every rung's row, so a chain never reloads one after a swap
+            for (int x = tid; x < I.R * L.thr_words; x += nt) {
+                const int r = x / L.thr_words, c = x - r * L.thr_words;
+                s_thr[x] = c < I.nL3 ? I.thr[(size_t)r * I.nL3 + c] : 0u;
+            }
         for (int b = 0; b < L.nbufs; ++b) {
             int8_t* ones = reinterpret_cast<int8_t*>(s_chains + (size_t)b * L.chain_stride + I.slot_stride);
             for (int x = tid; x < P; x += nt) ones[x] = 1;
@@ -146,9 +151,15 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
             int8_t* buf = reinterpret_cast<int8_t*>(s_chains + (size_t)(I.resident ? lc : grp) * L.chain_stride);
             if (!I.resident) load_split(buf, I.spins + (size_t)rho * I.slot_stride, N, P, G, ginv, gtid, gsize);
             const int rung = s_rung[rho];
-            for (int x = gtid; x < I.nL3; x += gsize) thr_g[x] = I.thr[(size_t)rung * I.nL3 + x];
-            group_sync(bar, gsize);
-            const uint32_t* thr_c = thr_g + 3 * I.Lmax;
+            const uint32_t* thr_c;
+            if (I.thr_resident) {
+                thr_c = s_thr + (size_t)rung * L.thr_words + 3 * I.Lmax;
+                if (!I.resident) group_sync(bar, gsize);  // the streamed chain is in place
+            } else {
+                for (int x = gtid; x < I.nL3; x += gsize) thr_g[x] = I.thr[(size_t)rung * I.nL3 + x];
+                group_sync(bar, gsize);
+                thr_c = thr_g + 3 * I.Lmax;
+            }
             int sumL = 0, sumC = 0, nf = 0;  // sumC and nf count twice (see unit_commit)
             for (int lev = 0; lev < I.n_levels; ++lev) {
                 const int base = s_loff[lev];
@@ -208,11 +219,14 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
             const long long q = I.q0 + pass;
             const int pb = pass & 1;
             for (int lc = tid; lc < c_count; lc += nt) s_pub[pb * C + lc] = make_longlong2(s_E[lc], s_M[lc]);
-            cluster.sync();
+            if (K == 1)
+                __syncthreads();
+            else
+                cluster.sync();
             for (int rl = (int)(q & 1) + 2 * tid; rl + 1 < R; rl += 2 * nt) {
                 const int X = s_slot[rl], Y = s_slot[rl + 1];
-                const longlong2 px = cluster.map_shared_rank(s_pub, X / C)[pb * C + X % C];
-                const longlong2 py = cluster.map_shared_rank(s_pub, Y / C)[pb * C + Y % C];
+                const longlong2 px = K == 1 ? s_pub[pb * C + X] : cluster.map_shared_rank(s_pub, X / C)[pb * C + X % C];
+                const longlong2 py = K == 1 ? s_pub[pb * C + Y] : cluster.map_shared_rank(s_pub, Y / C)[pb * C + Y % C];
                 const bool acc = swap_accept_fast(px.x, py.x, px.y, py.y, I.coef[rl], I.coef[(R - 1) + rl],
                                                   (uint32_t)q, (uint32_t)rl, key, false);
                 if (rank == 0) {
@@ -256,6 +270,15 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(BatchParams bp) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int K = (int)cluster.num_blocks();
+    if (bp.single) {
+        // one problem on this one cluster; the host keeps its counters
+        if (bp.one.dc == 4)
+            run_problem<4>(bp.one, smem, s_keys, cluster, rank, K);
+        else
+            run_problem<8>(bp.one, smem, s_keys, cluster, rank, K);
+        if (K > 1) cluster.sync();  // peers are done reading this CTA's published (E, M)
+        return;
+    }
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) s_job = atomicAdd(bp.next_job, 1);
         cluster.sync();
@@ -388,6 +411,26 @@ cudaError_t batch_max_clusters(int cluster, int threads, size_t smem, int* n_clu
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaOccupancyMaxActiveClusters(n_clusters, (void*)batch_kernel, &cfg);
+}
+
+size_t batch_smem_cap() {
+    int dev = 0, max_smem = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    return (size_t)max_smem - 1024;  // room for the kernel's static shared memory
+}
+
+cudaError_t launch_batch_single(const BatchInstance& I, int cluster, int threads, size_t smem, cudaStream_t s) {
+    BatchParams bp;
+    bp.inst = nullptr;
+    bp.order = nullptr;
+    bp.count = 1;
+    bp.next_job = nullptr;
+    bp.status = nullptr;
+    bp.single = 1;
+    bp.one = I;
+    return launch_batch(bp, cluster, 1, threads, smem, s);
 }
 
 cudaError_t launch_batch_init(const BatchInstance* inst, const int2* map, int n_chains, cudaStream_t s) {
@@ -638,11 +681,21 @@ void ptq::choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_
     for (int w = 0; w < widen && g < 512 && g < threads; ++w) g <<= 1;
     for (int w = 0; w < -widen && g > 32; ++w) g >>= 1;  // down to one warp per chain
     while (g < threads && threads / g > C) g <<= 1;      // still no more groups than chains
+    // every rung's threshold row in shared memory when the rows take at most 48 KB and the
+    // chains still fit; resident chains come first
+    const int thr_words = (int)(up16((size_t)I.nL3 * 4) / 4);
+    const int thr_ok = (size_t)I.R * thr_words * 4 <= 49152 ? 1 : 0;
     for (;;) {
         I.group_threads = g;
         I.resident = 1;
+        I.thr_resident = thr_ok;
+        if (batch_smem_bytes(I, cluster, threads) <= smem_cap) break;
+        I.thr_resident = 0;
         if (batch_smem_bytes(I, cluster, threads) <= smem_cap) break;
         I.resident = 0;
+        I.thr_resident = thr_ok;
+        if (batch_smem_bytes(I, cluster, threads) <= smem_cap) break;
+        I.thr_resident = 0;
         if (batch_smem_bytes(I, cluster, threads) <= smem_cap || g >= 512 || g >= threads) break;
         g <<= 1;  // one streaming buffer per group: fewer, larger groups
     }

@@ -55,6 +55,7 @@ struct PlanKey {
 };
 struct PlanChoice {
     int path, threads, producers;
+    int cluster, group_threads, thr_resident;  // path 7
 };
 static std::mutex g_plan_mutex;
 static std::map<PlanKey, PlanChoice> g_plan_cache;
@@ -305,6 +306,89 @@ static int check_status(pt_ctx* c) {
         if (e_ != cudaSuccess) return ctx_fail((c), PT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+// Path 7: the context's problem as the batched kernel's one request, for one launch of
+// n sweeps starting at counters (t0, q0).
+static BatchInstance chains_instance(const DevProblem& p, const LaunchPlan& plan, long long t0, long long q0, int n,
+                                     int sps) {
+    BatchInstance I;
+    memset(&I, 0, sizeof(I));
+    I.sdesc = p.desc;
+    I.items = p.items;
+    I.level_off = p.level_off;
+    I.thr = p.thr;
+    I.coef = p.coef;
+    I.spins = p.spins;
+    I.E = p.E;
+    I.M = p.M;
+    I.rung_of_slot = p.rung_of_slot;
+    I.slot_of_rung = p.slot_of_rung;
+    I.acc = p.acc;
+    I.swap_stats = p.swap_stats;
+    I.N = p.N;
+    I.P = p.P;
+    I.R = p.R;
+    I.Lmax = p.Lmax;
+    I.nL3 = p.nL3;
+    I.n_levels = p.n_levels;
+    I.dc = plan.dclass;
+    I.slot_stride = p.slot_stride;
+    I.group_threads = plan.group_threads;
+    I.resident = 1;
+    I.thr_resident = plan.thr_resident;
+    I.key0 = p.key0;
+    I.key1 = p.key1;
+    I.t0 = t0;
+    I.q0 = q0;
+    I.n_sweeps = n;
+    I.sweeps_per_swap = sps;
+    return I;
+}
+
+// n sweeps (a swap pass after every sps-th) of any plan, starting at counters (t0, q0).
+static cudaError_t launch_plan_sweeps(const DevProblem& p, const LaunchPlan& plan, long long t0, long long q0, int n,
+                                      int sps, long long timeout_ns, bool cooperative, cudaStream_t s) {
+    if (plan.path == kPathPackedChains)
+        return launch_batch_single(chains_instance(p, plan, t0, q0, n, sps), plan.cluster, plan.threads,
+                                   plan.smem_bytes, s);
+    return launch_sweeps(p, plan, t0, q0, n, sps, timeout_ns, cooperative, s);
+}
+
+// Path 7 for a problem: the narrowest chain groups (widen < 0 halves the size-based width,
+// down to one warp) with every chain resident on one cluster of `cluster` CTAs. Returns
+// false when the chains do not all fit or no such cluster can run.
+static bool chains_plan(const DevProblem& p, int dclass, int cluster, int widen, LaunchPlan& pl,
+                        int force_group = 0) {
+    BatchInstance I = chains_instance(p, pl, 0, 0, 0, 0);
+    I.dc = dclass;
+    const size_t cap = batch_smem_cap();
+    choose_groups(I, cluster, 512, cap, widen);
+    if (force_group > 0) {
+        // the given width, with every rung's threshold row resident if that still fits
+        I.group_threads = force_group;
+        I.resident = 1;
+        I.thr_resident = 1;
+        if (batch_smem_bytes(I, cluster, 512) > cap || (size_t)I.R * ((I.nL3 * 4 + 15) / 16 * 16) > 49152)
+            I.thr_resident = 0;
+    }
+    if (!I.resident) return false;
+    const size_t smem = batch_smem_bytes(I, cluster, 512);
+    if (smem > cap) return false;
+    int ncl = 0;
+    if (batch_max_clusters(cluster, 512, smem, &ncl) != cudaSuccess || ncl < 1) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    pl.path = kPathPackedChains;
+    pl.dclass = dclass;
+    pl.threads = 512;
+    pl.n_consumer = 512;
+    pl.smem_bytes = smem;
+    pl.cluster = cluster;
+    pl.group_threads = I.group_threads;
+    pl.thr_resident = I.thr_resident;
+    return true;
+}
+
 extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladder, int32_t R,
                          const uint32_t* flip_thr, const double* swap_coef, uint64_t seed,
                          const pt_options* opt, void* cuda_stream, pt_ctx** out) {
@@ -427,12 +511,12 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     const int packed_dc = (dmax + 1 <= 4) ? 4 : ((dmax + 1 <= 8) ? 8 : 0);
     const bool packed_ok = (P % 8 == 0) && packed_dc > 0;
     const int want_path = opt ? opt->kernel_path : 0;
-    if (want_path < 0 || want_path > 6) {
+    if (want_path < 0 || want_path > 7) {
         free_ctx(c);
-        return create_fail(PT_EINVAL, "kernel_path must be 0..6");
+        return create_fail(PT_EINVAL, "kernel_path must be 0..7");
     }
     if ((want_path == kPathPacked || want_path == kPathPackedInline || want_path == kPathBits ||
-         want_path == kPathSplit || want_path == kPathSplitInline) && !packed_ok) {
+         want_path == kPathSplit || want_path == kPathSplitInline || want_path == kPathPackedChains) && !packed_ok) {
         free_ctx(c);
         return create_fail(PT_EINVAL, "the packed kernel needs P %% 8 == 0 and degree <= 7");
     }
@@ -444,7 +528,19 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     // shared memory when they take at most 48 KB and the chosen layout still fits
     p.acc_in_smem = (size_t)R * kAccCount * 8 <= 16384 ? 1 : 0;
     p.tables_in_smem = (size_t)R * p.nL3 * 4 <= 49152 ? 1 : 0;
-    int path = want_path;
+    // path 7 is set up on the inline-word plan's data (int8 rows, site descriptors) and
+    // switched to the packed-chains launch once the device state exists
+    const bool want_chains = want_path == kPathPackedChains;
+    if (want_chains && ((opt->threads_per_block != 0) || p.withhold_rung >= 0 || p.exact_swaps ||
+                        opt->cluster_size < 0 || opt->cluster_size > 16 ||
+                        (opt->group_threads != 0 && (opt->group_threads < 32 || opt->group_threads > 512 ||
+                                                     (opt->group_threads & (opt->group_threads - 1)))))) {
+        free_ctx(c);
+        return create_fail(PT_EINVAL,
+                           "kernel_path 7 takes cluster_size (0..16) and group_threads (0 or 32..512, a power of "
+                           "two), no threads_per_block and no test hooks");
+    }
+    int path = want_chains ? kPathPackedInline : want_path;
     const int want_threads = opt ? opt->threads_per_block : 0;
     // a layout fits if it does with the threshold rows and / or the statistics moved out
     auto fits = [&](int pth) {
@@ -672,6 +768,36 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                            resident);
     }
 
+    if (want_chains) {
+        // the packed-chains plan: the given cluster size, or the smallest that holds every
+        // chain; the given chain-group width, or the narrowest that fits
+        LaunchPlan pl;
+        bool ok = false;
+        for (int K = opt->cluster_size > 0 ? opt->cluster_size : 1; K <= 16 && !ok; K *= 2) {
+            ok = chains_plan(p, packed_dc, K, kGroupWidenDefault, pl, opt->group_threads);
+            if (opt->cluster_size > 0) break;
+        }
+        if (!ok) {
+            free_ctx(c);
+            return create_fail(PT_EINVAL, "kernel_path 7: the chains do not all fit the cluster's shared memory");
+        }
+        int cols = 1;
+        while (cols < P / 8) cols <<= 1;
+        level_schedule(N, adj, items, level_off, std::max(1, pl.group_threads / cols));
+        cudaStream_t s = c->stream;
+        if ((e = cudaMemcpyAsync(d_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(d_loff, level_off.data(), level_off.size() * 4, cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+            free_ctx(c);
+            return create_fail(PT_ECUDA, "schedule upload: %s", cudaGetErrorString(e));
+        }
+        p.n_levels = (int)level_off.size() - 1;
+        c->plan = pl;
+        c->cooperative = true;
+    }
+
     // Plan autotuning. When the path and the block size are automatic and the chains are
     // int8 in shared memory, each candidate plan (producer-warp kernel, inline-word kernel
     // with 256, 384 or 512 threads, split kernel) sweeps a short stretch of one continuous
@@ -685,13 +811,16 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     if (tune) {
         struct Cand {
             int path, threads, producers;
+            int cluster = 1, group_threads = 0;  // path 7
         };
         const PlanKey key{N, P, R, packed_dc, p.n_levels, nE};
         std::vector<Cand> cands;
         {
             std::lock_guard<std::mutex> lock(g_plan_mutex);
             auto it = g_plan_cache.find(key);
-            if (it != g_plan_cache.end()) cands.push_back({it->second.path, it->second.threads, it->second.producers});
+            if (it != g_plan_cache.end())
+                cands.push_back({it->second.path, it->second.threads, it->second.producers, it->second.cluster,
+                                 it->second.group_threads});
         }
         const bool cached = !cands.empty();
         if (!cached) {
@@ -702,11 +831,29 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                     if (th >= P / 16 + 1) cands.push_back({kPathSplitInline, th, 0});
             if (fits(kPathPackedInline))
                 for (int th : {256, 384, 512}) cands.push_back({kPathPackedInline, th, 0});
+            // every chain resident on one cluster (small problems: swaps never leave the
+            // cluster), at the narrowest chain groups that fit and two wider ones
+            for (int K : {1, 2, 4, 8})
+                for (int widen : {kGroupWidenDefault, -2, 0}) {
+                    LaunchPlan pl;
+                    if (!chains_plan(p, packed_dc, K, widen, pl)) continue;
+                    bool dup = false;
+                    for (const Cand& cd : cands)
+                        dup = dup || (cd.path == kPathPackedChains && cd.cluster == K && cd.group_threads == pl.group_threads);
+                    if (!dup) cands.push_back({kPathPackedChains, 512, 0, K, pl.group_threads});
+                }
         }
         // a candidate's plan, shared-memory flags and level schedule
         auto make = [&](const Cand& cd, LaunchPlan& pl, DevProblem& pc, std::vector<uint32_t>& it_c,
                         std::vector<int32_t>& off_c) {
             pc = p;
+            if (cd.path == kPathPackedChains) {
+                if (!chains_plan(pc, packed_dc, cd.cluster, kGroupWidenDefault, pl, cd.group_threads)) return false;
+                int cols = 1;
+                while (cols < P / 8) cols <<= 1;
+                level_schedule(N, adj, it_c, off_c, std::max(1, pl.group_threads / cols));
+                return true;
+            }
             pc.acc_in_smem = (size_t)R * kAccCount * 8 <= 16384 ? 1 : 0;
             pc.tables_in_smem = (size_t)R * p.nL3 * 4 <= 49152 ? 1 : 0;
             if (pc.tables_in_smem && sweep_smem_bytes(pc, cd.path, packed_dc) > (size_t)max_smem) pc.tables_in_smem = 0;
@@ -746,20 +893,23 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                 std::vector<int32_t> off_c;
                 if (!make(cands[k], pl, pc, it_c, off_c)) continue;
                 long long res = 0;
-                if (prepare_sweep_kernel(pl) != cudaSuccess || sweep_resident_chains(pc, pl, &res) != cudaSuccess ||
-                    res < R) {
+                if (pl.path != kPathPackedChains &&
+                    (prepare_sweep_kernel(pl) != cudaSuccess || sweep_resident_chains(pc, pl, &res) != cudaSuccess ||
+                     res < R)) {
                     (void)cudaGetLastError();
                     continue;
                 }
                 cudaError_t e1 = cudaMemcpyAsync(d_items, it_c.data(), it_c.size() * 4, cudaMemcpyHostToDevice, s);
                 if (e1 == cudaSuccess)
                     e1 = cudaMemcpyAsync(d_loff, off_c.data(), off_c.size() * 4, cudaMemcpyHostToDevice, s);
-                if (e1 == cudaSuccess) e1 = launch_sweeps(pc, pl, t, q, warm, 1, c->timeout_ns, true, s);
+                if (e1 == cudaSuccess) e1 = launch_plan_sweeps(pc, pl, t, q, warm, 1, c->timeout_ns, true, s);
                 if (e1 == cudaSuccess) e1 = cudaEventRecord(ev[0], s);
-                if (e1 == cudaSuccess) e1 = launch_sweeps(pc, pl, t + warm, q + warm, shortn, 1, c->timeout_ns, true, s);
+                if (e1 == cudaSuccess)
+                    e1 = launch_plan_sweeps(pc, pl, t + warm, q + warm, shortn, 1, c->timeout_ns, true, s);
                 if (e1 == cudaSuccess) e1 = cudaEventRecord(ev[1], s);
                 if (e1 == cudaSuccess)
-                    e1 = launch_sweeps(pc, pl, t + warm + shortn, q + warm + shortn, longn, 1, c->timeout_ns, true, s);
+                    e1 = launch_plan_sweeps(pc, pl, t + warm + shortn, q + warm + shortn, longn, 1, c->timeout_ns,
+                                            true, s);
                 if (e1 == cudaSuccess) e1 = cudaEventRecord(ev[2], s);
                 if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(s);
                 int status = 0;
@@ -799,15 +949,18 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             DevProblem pc;
             if (make(cands[best], pl, pc, items, level_off)) {
                 long long res = 0;
-                if (prepare_sweep_kernel(pl) == cudaSuccess && sweep_resident_chains(pc, pl, &res) == cudaSuccess &&
-                    res >= R) {
+                if (pl.path == kPathPackedChains ||
+                    (prepare_sweep_kernel(pl) == cudaSuccess && sweep_resident_chains(pc, pl, &res) == cudaSuccess &&
+                     res >= R)) {
                     c->plan = pl;
                     c->cooperative = true;  // resident (checked above), cooperative launch available
                     p.acc_in_smem = pc.acc_in_smem;
                     p.tables_in_smem = pc.tables_in_smem;
                     if (!cached) {
                         std::lock_guard<std::mutex> lock(g_plan_mutex);
-                        g_plan_cache[key] = PlanChoice{cands[best].path, cands[best].threads, cands[best].producers};
+                        const Cand& cb = cands[best];
+                        g_plan_cache[key] = PlanChoice{cb.path, cb.threads, cb.producers, cb.cluster, cb.group_threads,
+                                                       pl.thr_resident};
                     }
                 }
                 (void)cudaGetLastError();
@@ -824,7 +977,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             return create_fail(PT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
         }                                                                            \
     } while (0)
-        TUNE_CUDA(prepare_sweep_kernel(c->plan));
+        if (c->plan.path != kPathPackedChains) TUNE_CUDA(prepare_sweep_kernel(c->plan));
         TUNE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s));
         TUNE_CUDA(cudaMemcpyAsync(d_loff, level_off.data(), level_off.size() * 4, cudaMemcpyHostToDevice, s));
         if (timed_plans > 0) {
@@ -849,6 +1002,21 @@ static int guard(pt_ctx* c) {
 }
 
 static int enqueue_sweeps(pt_ctx* c, long long n, int sps) {
+    if (c->plan.path == kPathPackedChains) {
+        // swaps in shared memory: no mailboxes, so only the sweep counter bounds a launch
+        long long done = 0;
+        while (done < n) {
+            long long chunk = n - done;
+            chunk = std::min<long long>(chunk, sps > 0 ? ((1ll << 30) / sps) * sps : (1ll << 30));
+            CUDA_OR_FAIL(c, launch_batch_single(chains_instance(c->dp, c->plan, c->t, c->q, (int)chunk, sps),
+                                                c->plan.cluster, c->plan.threads, c->plan.smem_bytes, c->stream));
+            c->launches += 1;
+            c->t += chunk;
+            if (sps > 0) c->q += chunk / sps;
+            done += chunk;
+        }
+        return PT_OK;
+    }
     // chunks of at most max_passes swap passes (mailbox capacity), aligned to the swap interval
     long long done = 0;
     while (done < n) {

@@ -64,7 +64,17 @@ struct DevProblem {
 // Sweep kernel variants: byte-wise (any shape), packed with Philox inline, packed with the
 // random words produced one sweep ahead by dedicated warps, bit-packed, and the produced-words
 // kernel with each chain split over a cluster of two CTAs.
-enum { kPathGeneric = 1, kPathPackedInline = 2, kPathPacked = 3, kPathBits = 4, kPathSplit = 5, kPathSplitInline = 6 };
+// Path 7 runs the batched kernel on the one problem: all chains packed on the CTAs of one
+// cluster (thread groups per chain), resident in shared memory, swaps in shared memory.
+enum {
+    kPathGeneric = 1,
+    kPathPackedInline = 2,
+    kPathPacked = 3,
+    kPathBits = 4,
+    kPathSplit = 5,
+    kPathSplitInline = 6,
+    kPathPackedChains = 7
+};
 
 struct LaunchPlan {
     int path;            // kPath*
@@ -72,6 +82,9 @@ struct LaunchPlan {
     int n_consumer;      // threads running the levels (the rest produce random words)
     int dclass;          // padded neighbour slots the kernel is built for
     size_t smem_bytes;   // dynamic shared memory per CTA
+    int cluster = 1;     // path 7: CTAs in the one cluster
+    int group_threads = 0;  // path 7: threads sweeping one chain
+    int thr_resident = 0;   // path 7: every rung's threshold row in shared memory
 };
 
 // Sizes of the dynamic shared-memory carve-up of the sweep kernel for a path.
@@ -96,6 +109,7 @@ struct BatchInstance {
     int N, P, R, Lmax, nL3, n_levels, dc, slot_stride;
     int group_threads;         // threads sweeping one chain (a divisor of the CTA size)
     int resident;              // 1: a CTA keeps all its chains in shared memory for the run
+    int thr_resident;          // 1: every rung's threshold row stays in shared memory for the run
     uint32_t key0, key1;
     long long t0, q0;          // counters before this run
     int n_sweeps, sweeps_per_swap;
@@ -109,6 +123,9 @@ struct BatchParams {
     int* status;
     int* done = nullptr;        // [count] or null: done[k] = done_token once problem k is written back
     int done_token = 1;         // nonzero, different per launch, so stale flags never match
+    int single = 0;             // 1: one cluster runs `one` (passed by value) once; inst, order,
+                                // next_job and done are unused and the counters stay on the host
+    BatchInstance one;
 };
 
 // Kernel launchers (pt_kernels.cu). Each returns a cudaError_t from the launch.
@@ -172,5 +189,10 @@ cudaError_t launch_batch(const BatchParams& bp, int cluster, int n_clusters, int
                          cudaStream_t s);
 cudaError_t batch_max_clusters(int cluster, int threads, size_t smem, int* n_clusters);
 cudaError_t launch_batch_init(const BatchInstance* inst, const int2* map, int n_chains, cudaStream_t s);
+// One problem on one cluster of `cluster` CTAs (path 7); I carries t0, q0, n_sweeps, sweeps_per_swap.
+cudaError_t launch_batch_single(const BatchInstance& I, int cluster, int threads, size_t smem, cudaStream_t s);
+// The largest shared-memory need of the batched kernel: the device's opt-in maximum less
+// the kernel's static shared memory.
+size_t batch_smem_cap();
 
 }  // namespace ptq

@@ -357,10 +357,11 @@ static int admit(pt_server* s) {
         q->block_off = off;
         unsigned char* base = s->arena + off;
         const Prepared& p = q->prep;
-        const int gthreads = q->inst.group_threads, resident = q->inst.resident;
+        const int gthreads = q->inst.group_threads, resident = q->inst.resident, thr_res = q->inst.thr_resident;
         fill_instance(q->inst, p, base, q->req);
         q->inst.group_threads = gthreads;
         q->inst.resident = resident;
+        q->inst.thr_resident = thr_res;
         std::vector<unsigned char> host(p.off_spins, 0);
         memcpy(&host[p.off_sdesc], p.sdesc.data(), p.sdesc.size() * 4);
         memcpy(&host[p.off_items], p.items.data(), p.items.size() * 4);
@@ -404,10 +405,11 @@ static int admit(pt_server* s) {
 static int upload_request(pt_server* s, ServeReq* q, cudaStream_t st) {
     unsigned char* base = s->arena + q->block_off;
     const Prepared& pr = q->prep;
-    const int gthreads = q->inst.group_threads, resident = q->inst.resident;
+    const int gthreads = q->inst.group_threads, resident = q->inst.resident, thr_res = q->inst.thr_resident;
     fill_instance(q->inst, pr, base, q->req);
     q->inst.group_threads = gthreads;
     q->inst.resident = resident;
+    q->inst.thr_resident = thr_res;
     std::vector<unsigned char> host(pr.off_spins, 0);
     memcpy(&host[pr.off_sdesc], pr.sdesc.data(), pr.sdesc.size() * 4);
     memcpy(&host[pr.off_items], pr.items.data(), pr.items.size() * 4);

@@ -38,7 +38,8 @@ class pt_rung(ctypes.Structure):
 class pt_options(ctypes.Structure):
     _fields_ = [("threads_per_block", _i32), ("wait_timeout_ms", _i32), ("swap_mode", _i32),
                 ("test_withhold_rung", _i32), ("kernel_path", _i32), ("producer_threads", _i32),
-                ("test_exact_swaps", _i32), ("cluster_size", _i32), ("no_autotune", _i32), ("reserved", _i32 * 3)]
+                ("test_exact_swaps", _i32), ("cluster_size", _i32), ("no_autotune", _i32), ("group_threads", _i32),
+                ("reserved", _i32 * 2)]
 
 
 class pt_observables(ctypes.Structure):
@@ -214,7 +215,8 @@ class PT:
 
     def __init__(self, n, ei, ej, J, h, P, T, gamma, seed, flip_thr=None, swap_coef=None,
                  threads_per_block=0, wait_timeout_ms=0, swap_mode=0, stream=None,
-                 test_withhold_rung=-1, kernel_path=0, producer_threads=0, test_exact_swaps=0, no_autotune=0):
+                 test_withhold_rung=-1, kernel_path=0, producer_threads=0, test_exact_swaps=0, no_autotune=0,
+                 cluster_size=0, group_threads=0):
         self.lib = load()
         self._arrays = [np.ascontiguousarray(a, np.int32) for a in (ei, ej, J, h)]
         inst = pt_instance(int(n), int(self._arrays[0].size),
@@ -227,7 +229,7 @@ class PT:
         coef = None if swap_coef is None else np.ascontiguousarray(swap_coef, np.float64)
         opt = pt_options(int(threads_per_block), int(wait_timeout_ms), int(swap_mode),
                          int(test_withhold_rung) + 1, int(kernel_path), int(producer_threads),
-                         int(test_exact_swaps), 0, int(no_autotune))
+                         int(test_exact_swaps), int(cluster_size), int(no_autotune), int(group_threads))
         h_out = _vp()
         rc = self.lib.pt_create(ctypes.byref(inst), self.P, ladder, self.R,
                                 None if thr is None else _ptr(thr), None if coef is None else _ptr(coef),

@@ -40,12 +40,23 @@ def poisson_trace(rate: float, duration: float, seed: int = 1, sweep_range=(500,
     return list(zip(times, probs))
 
 
-def _summary(lat, attempts, wall, extra):
+def _summary(lat, attempts, wall, extra, arrived=None):
+    """Latency percentiles over the completed requests, and over every arrival with the
+    requests still unfinished at the deadline counted as infinitely late (None when the
+    percentile falls on one of them)."""
     lat = np.asarray(lat, np.float64)
     d = {"completed": int(lat.size), "attempts_per_s": attempts / wall if wall > 0 else 0.0, "wall_s": wall}
     if lat.size:
         d.update(p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
                  mean_s=float(lat.mean()), max_s=float(lat.max()))
+    if arrived is not None:
+        unfinished = max(0, int(arrived) - int(lat.size))
+        d["unfinished"] = unfinished
+        if arrived:
+            allv = np.concatenate([lat, np.full(unfinished, np.inf)])
+            for q, key in ((50, "p50_all_s"), (99, "p99_all_s")):
+                v = float(np.percentile(allv, q, method="higher"))
+                d[key] = v if np.isfinite(v) else None
     d.update(extra)
     return d
 
@@ -87,10 +98,10 @@ def replay_batched(trace, quantum_sweeps=100, max_active=512, arena_bytes=0, clu
     lat = [done_t[r] - arrival[r] for r in done_t]
     info = srv.info()
     out = _summary(lat, sum(attempts[r] for r in done_t), wall,
-                   {"mode": "stepped" if stepped else "streamed", "submitted": k, "max_active_seen": max_mix, "steps": int(info.steps),
-                    "wide_steps": int(info.wide_steps), "group_launches": int(info.group_launches),
-                    "kernel_launches": int(info.kernel_launches),
-                    "quantum_sweeps": quantum_sweeps})
+                   {"mode": "stepped" if stepped else "streamed", "submitted": k, "max_active_seen": max_mix,
+                    "steps": int(info.steps), "wide_steps": int(info.wide_steps),
+                    "group_launches": int(info.group_launches), "kernel_launches": int(info.kernel_launches),
+                    "quantum_sweeps": quantum_sweeps}, arrived=len(trace))
     srv.close()
     return out
 
@@ -118,4 +129,5 @@ def replay_plain(trace, stream=None, deadline=None):
         att += prob.attempts_per_sweep * prob.n_sweeps
         k += 1
     wall = (time.perf_counter() - t0) - (trace[0][0] if trace else 0.0)
-    return _summary(lat, att, wall, {"mode": "plain", "submitted": k, "kernel_launches": launches})
+    return _summary(lat, att, wall, {"mode": "plain", "submitted": k, "kernel_launches": launches},
+                    arrived=len(trace))
