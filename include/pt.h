@@ -313,8 +313,8 @@ typedef struct {
     int32_t quantum_sweeps; /* sweeps per request per step (0 = 100) */
     int32_t cluster_size;   /* CTAs per cluster of batched launches (1..16), or 0: 2 in
                                stepped mode; a backlog launch in streamed mode takes the
-                               largest of 2, 4, 8, 16 whose clusters (one per request) fit the
-                               SMs no other launch holds */
+                               largest of 8, 4 and 2 at which every request of the backlog
+                               gets a cluster of its own at once (else 2) */
     int32_t reserved[3];    /* reserved[1] = 1: stepped mode (a quantum of sweeps per launch);
                                reserved[0] = 1: stepped mode with chains packed on clusters only */
 } pt_server_options;

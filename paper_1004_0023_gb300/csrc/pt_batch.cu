@@ -130,8 +130,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
     }
     __syncthreads();
 
-    const PhiloxKey key = philox_schedule(I.key0, I.key1);  // swap decisions
-    const PhiloxKeyShared skey{s_keys};                     // update units: round keys in shared memory
+    const PhiloxKeyShared skey{s_keys};  // update units and swap decisions: round keys in shared memory
     const int G = P >> 3;
     const uint32_t ginv = chunk_ginv(G);
     int lg = 0;
@@ -146,7 +145,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
 
     for (int s = 0; s < I.n_sweeps; ++s) {
         const uint32_t t = (uint32_t)(I.t0 + s);
-        for (int lc = grp; lc < c_count; lc += ngroups) {
+        for (int lc = grp < ngroups ? grp : c_count; lc < c_count; lc += ngroups) {  // threads past the last group idle
             const int rho = c_begin + lc;
             int8_t* buf = reinterpret_cast<int8_t*>(s_chains + (size_t)(I.resident ? lc : grp) * L.chain_stride);
             if (!I.resident) load_split(buf, I.spins + (size_t)rho * I.slot_stride, N, P, G, ginv, gtid, gsize);
@@ -228,7 +227,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
                 const longlong2 px = K == 1 ? s_pub[pb * C + X] : cluster.map_shared_rank(s_pub, X / C)[pb * C + X % C];
                 const longlong2 py = K == 1 ? s_pub[pb * C + Y] : cluster.map_shared_rank(s_pub, Y / C)[pb * C + Y % C];
                 const bool acc = swap_accept_fast(px.x, py.x, px.y, py.y, I.coef[rl], I.coef[(R - 1) + rl],
-                                                  (uint32_t)q, (uint32_t)rl, key, false);
+                                                  (uint32_t)q, (uint32_t)rl, skey, false);
                 if (rank == 0) {
                     atomicAdd(I.swap_stats + 2 * rl, 1ull);
                     if (acc) atomicAdd(I.swap_stats + 2 * rl + 1, 1ull);
@@ -675,12 +674,18 @@ void ptq::choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_
     const long long units = 2ll * I.N * (I.P / 8);
     const long long avg = (units + I.n_levels - 1) / I.n_levels;
     const int C = (I.R + cluster - 1) / cluster;
+    // widths are powers of two that divide the CTA, so every thread is in a group
+    auto up_ok = [&](int x) {
+        const int y = 2 * x;
+        return y <= threads && threads % y == 0;
+    };
     int g = 64;
-    while (g < 512 && g < avg) g <<= 1;
-    while (g < 512 && threads / g > C) g <<= 1;
-    for (int w = 0; w < widen && g < 512 && g < threads; ++w) g <<= 1;
+    while (up_ok(g) && g < avg) g <<= 1;
+    while (up_ok(g) && threads / g > C) g <<= 1;
+    for (int w = 0; w < widen && up_ok(g); ++w) g <<= 1;
     for (int w = 0; w < -widen && g > 32; ++w) g >>= 1;  // down to one warp per chain
-    while (g < threads && threads / g > C) g <<= 1;      // still no more groups than chains
+    while (up_ok(g) && threads / g > C) g <<= 1;         // still no more groups than chains
+    while (g > 32 && up_ok(g) && threads / g > 15) g <<= 1;  // named barriers 1..15 (0: the CTA's)
     // every rung's threshold row in shared memory when the rows take at most 48 KB and the
     // chains still fit; resident chains come first
     const int thr_words = (int)(up16((size_t)I.nL3 * 4) / 4);
@@ -696,8 +701,9 @@ void ptq::choose_groups(BatchInstance& I, int cluster, int threads, size_t smem_
         I.thr_resident = thr_ok;
         if (batch_smem_bytes(I, cluster, threads) <= smem_cap) break;
         I.thr_resident = 0;
-        if (batch_smem_bytes(I, cluster, threads) <= smem_cap || g >= 512 || g >= threads) break;
+        if (batch_smem_bytes(I, cluster, threads) <= smem_cap || !up_ok(g)) break;
         g <<= 1;  // one streaming buffer per group: fewer, larger groups
+        while (up_ok(g) && threads / g > 15) g <<= 1;
     }
 }
 

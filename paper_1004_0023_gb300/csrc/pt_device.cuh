@@ -75,9 +75,10 @@ __device__ __forceinline__ double det_exp(double x) {
 }
 
 // Swap decision for X on rung rl and Y on rung rl + 1 at pass q.
+template <typename Key = PhiloxKey>
 __device__ __forceinline__ bool swap_accept(long long EX, long long EY, long long MX, long long MY,
                                             double a, double c, uint32_t q, uint32_t rl,
-                                            const PhiloxKey& key) {
+                                            const Key& key) {
     const double dE = __ll2double_rn(EX - EY);
     const double dM = __ll2double_rn(MX - MY);
     const double delta = __dadd_rn(__dmul_rn(a, dE), __dmul_rn(c, dM));
@@ -98,9 +99,10 @@ __device__ __forceinline__ bool swap_accept(long long EX, long long EY, long lon
 // The estimate decides only when u is farther than that margin (plus float rounding of u)
 // from the threshold, or Delta's sign and the -23 cut are certain; otherwise swap_accept
 // decides. Either way the result equals swap_accept's.
+template <typename Key = PhiloxKey>
 __device__ __forceinline__ bool swap_accept_fast(long long EX, long long EY, long long MX, long long MY,
                                                  double a, double c, uint32_t q, uint32_t rl,
-                                                 const PhiloxKey& key, bool exact_only) {
+                                                 const Key& key, bool exact_only) {
     if (!exact_only) {
         const float pa = (float)a * (float)(EX - EY);
         const float pc = (float)c * (float)(MX - MY);
@@ -119,7 +121,7 @@ __device__ __forceinline__ bool swap_accept_fast(long long EX, long long EY, lon
             }
         }
     }
-    return swap_accept(EX, EY, MX, MY, a, c, q, rl, key);
+    return swap_accept<Key>(EX, EY, MX, MY, a, c, q, rl, key);
 }
 
 // ------------------------------------------------------------------------- PTX helpers

@@ -564,17 +564,16 @@ static int launch_streamed(pt_server* s, ServeReq* q) {
 // Returns 1 (nothing launched) when the arena has no room for the group's block.
 static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
     const int n = (int)g.size();
-    // Cluster size: the given one, or the largest of 2..16 CTAs for which the group's
-    // clusters (one per member at most) still fit the SMs no other launch holds. A member
-    // runs on one cluster, so a small backlog on an idle GPU gets wide clusters (each
-    // request's chains over many SMs, low latency) and a long one gets narrow clusters
-    // (many requests at once, the highest throughput).
+    // Cluster size: the given one, or the largest of 8, 4 and 2 CTAs at which every member
+    // gets a cluster of its own at once (2 when even that is too many). A member runs on one
+    // cluster, so a short backlog gets wide clusters (each request's chains over more SMs,
+    // lower latency) and a long one narrow clusters (the most requests at once: on this GPU
+    // clusters of 2 also sweep the most attempts per second). 16 is not used: fewer of them
+    // fit the GPU's SMs, and they lost to 8 on latency as well in measured replays.
     int K = s->cluster, ncl = s->n_clusters;
     if (s->adaptive_cluster) {
-        const long long free_sms = std::max<long long>(0, s->n_sm - s->inflight_sms);
-        int l = 1;
-        while (l < 4 && s->ncl_by_log2[l + 1] > 0 && (long long)std::min(n, s->ncl_by_log2[l + 1]) * (2 << l) <= free_sms)
-            ++l;
+        int l = 3;
+        while (l > 1 && s->ncl_by_log2[l] < n) --l;
         // every member must fit a CTA of that cluster size (narrower clusters hold more chains
         // per CTA but never need more room than streaming one chain per group)
         for (; l > 1; --l) {
