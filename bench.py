@@ -321,9 +321,10 @@ def batched_headline(args, pt, instances, torch, n_sm, rank, world, local_rank, 
     e2e = None
     if not args.no_e2e:
         e2e = batched_e2e(args, probs, attempts, pt, torch, stream, world, device)
-    cpu = None
+    cpu = cpu_mt = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_batch_sample(probs, budget_s=16.0)
+        cpu_mt = cpu_batch_sample(probs, budget_s=8.0, kind="paper_mt")
     workload = ("%d requests, N~U{32..1024} random 3-regular or K4,4 cell lattice, P~U{32,64,128}, R~U{16..128}, "
                 "J in {-2,-1,1,2}, h in {-1,0,1}, geometric Gamma 0.05..4.0 at T=0.02, %d sweeps each, swap pass "
                 "after every sweep" % (args.batch_count, probs[0].n_sweeps))
@@ -344,6 +345,7 @@ def batched_headline(args, pt, instances, torch, n_sm, rank, world, local_rank, 
         "step_ms": {"min": float(np.min(step_ms)), "median": float(np.median(step_ms)), "max": float(np.max(step_ms))},
         "roofline": rf,
         "cpu_baseline": cpu,
+        "cpu_paper_mt": cpu_mt,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
@@ -477,9 +479,10 @@ def plain_record(name, args, pt, instances, torch, n_sm, sm_mhz, rank, world, de
                   n_sm, mhz, KERNEL_NAMES.get(int(info.kernel_path), "sweep kernel"),
                   "%s_%d" % (name, prob.n_sweeps))
     ctx.close()
-    cpu = None
+    cpu = cpu_mt = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob, budget_s=4.0 if not clocks else 12.0)
+        cpu_mt = cpu_baseline(prob, budget_s=3.0, kind="paper_mt")
     return {"workload": name, "value": units / max_s, "unit": "attempts/s", "ms_per_step": float(np.mean(step_ms)),
             "steps": steps, "gpu_launches": launches, "clocks": ck,
             "config": {"workload": name, "n": prob.n, "P": prob.P, "R": prob.R, "degree": d,
@@ -488,7 +491,7 @@ def plain_record(name, args, pt, instances, torch, n_sm, sm_mhz, rank, world, de
                        "threads_per_block": int(info.threads_per_block), "levels_per_sweep": int(info.n_levels),
                        "cooperative_swaps": bool(info.cooperative), "plans_timed_at_create": int(info.tuned_plans),
                        "l2": "flushed between timed steps (512 MB write outside the events)"},
-            "roofline": rf, "cpu_baseline": cpu}
+            "roofline": rf, "cpu_baseline": cpu, "cpu_paper_mt": cpu_mt}
 
 
 def plain_e2e(args, prob, pt, torch, world=1, device=None):
@@ -569,14 +572,20 @@ def run_serving(args, torch, capacity, gpu_index=0):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_baseline(prob, budget_s=12.0, threads=None):
-    """The CPU oracle as it stands, on the host cores, over a bounded sample of sweeps."""
-    from oracle import Oracle
-    from oracle import oracle as orc
-
-    orc.build()
+def cpu_baseline(prob, budget_s=12.0, threads=None, kind="oracle"):
+    """A CPU implementation on the host cores over a bounded sample of sweeps: the oracle as it
+    stands (kind "oracle"), or the paper's multi-threaded design (kind "paper_mt")."""
     threads = threads or os.cpu_count() or 1
-    o = Oracle.from_problem(prob, threads=threads)
+    if kind == "oracle":
+        from oracle import Oracle
+        from oracle import oracle as orc
+
+        orc.build()
+        o = Oracle.from_problem(prob, threads=threads)
+    else:
+        from cpu_pt import CpuPT
+
+        o = CpuPT.from_problem(prob, threads=threads)
     t0 = time.perf_counter()
     o.run(2, prob.sweeps_per_swap)
     probe = max(time.perf_counter() - t0, 1e-6) / 2
@@ -586,24 +595,33 @@ def cpu_baseline(prob, budget_s=12.0, threads=None):
     o.run(n, prob.sweeps_per_swap)
     dt = time.perf_counter() - t0
     o.close()
-    return {"value": prob.attempts_per_sweep * n / dt, "unit": "attempts/s", "cores": threads, "kind": "oracle",
+    how = "OpenMP over chains" if kind == "oracle" else "persistent threads, work pool hardest chain first"
+    return {"value": prob.attempts_per_sweep * n / dt, "unit": "attempts/s", "cores": threads, "kind": kind,
             "sample": "%d sweeps (+ swap passes; %.2f steps of %d sweeps) of the same problem, one continuous "
-                      "chain run, OpenMP over chains, %.1f s" % (n, n / max(prob.n_sweeps, 1), prob.n_sweeps, dt)}
+                      "chain run, %s, %.1f s" % (n, n / max(prob.n_sweeps, 1), prob.n_sweeps, how, dt)}
 
 
-def cpu_batch_sample(probs, budget_s=16.0, threads=None, picks=8):
-    """The CPU oracle on a seeded sample of the batched mix: `picks` requests spread evenly over
-    the mix (indices 0, count/picks, ...), each run for an equal share of the time budget."""
-    from oracle import Oracle
-    from oracle import oracle as orc
-
-    orc.build()
+def cpu_batch_sample(probs, budget_s=16.0, threads=None, picks=8, kind="oracle"):
+    """A CPU implementation on a seeded sample of the batched mix: `picks` requests spread
+    evenly over the mix (indices 0, count/picks, ...), each run for an equal share of the time
+    budget. kind "oracle": the plain oracle (OpenMP over chains); "paper_mt": the paper's
+    multi-threaded design (persistent threads, work pool hardest chain first, Sec. 4)."""
     threads = threads or os.cpu_count() or 1
+    if kind == "oracle":
+        from oracle import Oracle
+        from oracle import oracle as orc
+
+        orc.build()
+        make = lambda p: Oracle.from_problem(p, threads=threads)  # noqa: E731
+    else:
+        from cpu_pt import CpuPT
+
+        make = lambda p: CpuPT.from_problem(p, threads=threads)  # noqa: E731
     idx = [int(k * len(probs) / picks) for k in range(min(picks, len(probs)))]
     att, secs, sweeps = 0.0, 0.0, []
     for k in idx:
         p = probs[k]
-        o = Oracle.from_problem(p, threads=threads)
+        o = make(p)
         t0 = time.perf_counter()
         o.run(1, p.sweeps_per_swap)
         probe = max(time.perf_counter() - t0, 1e-6)
@@ -614,9 +632,10 @@ def cpu_batch_sample(probs, budget_s=16.0, threads=None, picks=8):
         att += float(p.attempts_per_sweep) * n
         sweeps.append(n)
         o.close()
-    return {"value": att / secs, "unit": "attempts/s", "cores": threads, "kind": "oracle",
-            "sample": "requests %s of the %d-request mix, %s sweeps each (+ swap passes), OpenMP over chains, "
-                      "%.1f s of oracle time" % (idx, len(probs), sweeps, secs)}
+    how = "OpenMP over chains" if kind == "oracle" else "persistent threads, work pool hardest chain first"
+    return {"value": att / secs, "unit": "attempts/s", "cores": threads, "kind": kind,
+            "sample": "requests %s of the %d-request mix, %s sweeps each (+ swap passes), %s, %.1f s of CPU time"
+                      % (idx, len(probs), sweeps, how, secs)}
 
 
 def run_reference(args, rank, world):
