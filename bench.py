@@ -85,7 +85,12 @@ def kernel_source_hash() -> str:
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
 # kernel, from one ncu capture: (kernel, workload key) -> (kernel_source_hash() of the build
 # captured, bytes). A figure whose hash no longer matches the sources is reported as null.
-MEASURED_TRAFFIC: dict = {}
+MEASURED_TRAFFIC: dict = {
+    # one 1000-sweep launch of the N=256, P=64, R=64 plan (path 2, 384 threads): 1.60 MB read, 0 written
+    ("sweep_packed_kernel (int8, inline Philox)", "regular3_n256_p64_r64_2000"): ("526b0deafa5eb2d6", 1595904),
+    # one 500-sweep launch of the K4,4 lattice, bit-packed (path 4, 512 threads)
+    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("526b0deafa5eb2d6", 26657024 + 5120),
+}
 
 
 def measured_traffic(kernel: str, key: str):
