@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <deque>
 #include <map>
 #include <vector>
@@ -95,6 +96,7 @@ struct ServeGroup {
     int token = 0;                // the value a member's flag takes when it is done
     std::vector<int> flags;       // host copy of the members' done flags
     cudaEvent_t done = nullptr;   // the launch's end
+    cudaEvent_t zeroed = nullptr; // the block's counter, status and flags are zero (before the launch)
     int stream_idx = 0;           // the pool stream it runs on
     int ctas = 0;                 // CTAs launched (each holds an SM until the launch ends)
 };
@@ -188,6 +190,7 @@ static void free_server(pt_server* s) {
             groups.push_back(kv.second->group);
     for (ServeGroup* grp : groups) {
         if (grp->done) cudaEventDestroy(grp->done);
+        if (grp->zeroed) cudaEventDestroy(grp->zeroed);
         delete grp;
     }
     for (auto& kv : s->reqs) {
@@ -628,7 +631,9 @@ static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
             cudaSuccess ||
         (e = cudaMemcpyAsync(gb + order_off, order.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice,
                              st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(gb + ctr_off, 0, grp->bytes - ctr_off, st)) != cudaSuccess)
+        (e = cudaMemsetAsync(gb + ctr_off, 0, grp->bytes - ctr_off, st)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&grp->zeroed, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventRecord(grp->zeroed, st)) != cudaSuccess)
         return sfail(s, PT_ECUDA, "group upload: %s", cudaGetErrorString(e));
     BatchParams bp;
     bp.inst = (BatchInstance*)gb;
@@ -637,8 +642,11 @@ static int launch_group(pt_server* s, const std::vector<ServeReq*>& g) {
     bp.next_job = (int*)(gb + ctr_off);
     bp.status = (int*)(gb + grp->status_off);
     bp.done = (int*)(gb + grp->flags_off);
-    // a flag left in this arena block by an earlier group carries that group's token
-    grp->token = (int)(s->group_launches % 2000000000) + 1;
+    // a flag left in this arena block by an earlier group (of this server, or of an earlier
+    // user of the same device memory) must never match: tokens are unique in the process,
+    // and the host reads a group's flags only once the memset above has run (grp->zeroed)
+    static std::atomic<unsigned> g_next_token{0};
+    grp->token = (int)(g_next_token.fetch_add(1) % 2000000000u) + 1;
     bp.done_token = grp->token;
     if ((e = launch_batch(bp, K, std::min(ncl, n), s->threads, smem, st)) != cudaSuccess)
         return sfail(s, PT_ECUDA, "group launch: %s", cudaGetErrorString(e));
@@ -673,6 +681,7 @@ static bool retire_group(pt_server* s, ServeGroup* grp) {
     s->inflight_sms -= grp->ctas;
     s->alloc->release(grp->off, grp->bytes);
     cudaEventDestroy(grp->done);
+    cudaEventDestroy(grp->zeroed);
     delete grp;
     return true;
 }
@@ -691,6 +700,12 @@ static int step_streamed(pt_server* s) {
         for (int64_t id : s->active) {
             ServeGroup* grp = s->reqs[id]->group;
             if (!grp || std::find(polled.begin(), polled.end(), grp) != polled.end()) continue;
+            // the flags are copied on the server's stream, which is not ordered after the
+            // group's stream: until the memset that zeroes them has run, the block still holds
+            // whatever the memory held before, so they are not read yet
+            const cudaError_t z = cudaEventQuery(grp->zeroed);
+            if (z == cudaErrorNotReady) continue;
+            if (z != cudaSuccess) return sfail(s, PT_ECUDA, "%s", cudaGetErrorString(z));
             polled.push_back(grp);
             const cudaError_t e = cudaMemcpyAsync(grp->flags.data(), s->arena + grp->off + grp->flags_off,
                                                   (size_t)grp->n * sizeof(int), cudaMemcpyDeviceToHost, s->stream);

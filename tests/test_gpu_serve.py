@@ -160,3 +160,44 @@ def test_members_of_a_batched_launch_complete_on_their_own():
         _same(results[k][0], results[k][1], alone.read_state(), alone.obs(), "request %d vs alone" % k)
         alone.close()
     srv.close()
+
+
+def test_backlog_on_device_memory_that_held_other_data():
+    """A server's arena is fresh device memory that may hold anything an earlier user left
+    (here: small integers, like the completion tokens of an earlier server's batched
+    launches). Long requests first occupy every stream of the server's pool, so that the
+    backlog launched next waits behind one of them, zeroing of its flags included. Each
+    member must still complete only once the kernel has written it back: the flags are read
+    only after the launch's own zeroing has run, and tokens never repeat in a process. Every
+    result equals the request run alone."""
+    torch = pytest.importorskip("torch")
+    arena = 256 << 20
+    for round_ in range(2):
+        junk = (torch.arange(arena // 4, dtype=torch.int32, device="cuda") % 64) + 1
+        torch.cuda.synchronize()
+        del junk
+        torch.cuda.empty_cache()  # give the memory back, so the arena below can reuse it
+        busy = _requests(16, 50 + round_, (20000, 30000))
+        backlog = _requests(20, 40 + round_, (30, 120))
+        probs = busy + backlog
+        srv = pt.Server(arena_bytes=arena)
+        ids, results = {}, {}
+        for k, p in enumerate(busy):  # one at a time: each starts on its own launch and stream
+            ids[srv.submit(p)] = k
+            for rid in srv.step():
+                results[ids[rid]] = srv.result(rid)
+                srv.release(rid)
+        for k, p in enumerate(backlog):
+            ids[srv.submit(p)] = len(busy) + k
+        while len(results) < len(probs):
+            for rid in srv.step():
+                results[ids[rid]] = srv.result(rid)
+                srv.release(rid)
+        assert srv.info().group_launches >= 1
+        _drain(srv)
+        srv.close()
+        for k, p in enumerate(probs):
+            alone = pt.PT.from_problem(p)
+            alone.run(p.n_sweeps, p.sweeps_per_swap)
+            _same(results[k][0], results[k][1], alone.read_state(), alone.obs(), "round %d request %d" % (round_, k))
+            alone.close()
