@@ -71,25 +71,33 @@ KERNEL_NAMES = {1: "sweep_kernel (byte-wise)", 2: "sweep_packed_kernel (int8, in
                 7: "batch_kernel (all chains of the problem packed on one cluster, swaps in shared memory)"}
 
 
-def kernel_source_hash() -> str:
-    """First 16 hex digits of a SHA-256 over the CUDA sources: DRAM traffic figures below
-    are reported only for the build they were measured on."""
+# The sources each kernel is compiled from (its own file and the headers it includes).
+KERNEL_SOURCES = {"sweep": ("pt_kernels.cu", "pt_device.cuh", "pt_internal.h"),
+                  "batch": ("pt_batch.cu", "pt_device.cuh", "pt_internal.h")}
+
+
+def kernel_source_hash(which: str) -> str:
+    """First 16 hex digits of a SHA-256 over one kernel's sources (and include/pt.h): DRAM
+    traffic figures below are reported only for the build they were measured on."""
     d = os.path.join(ROOT, "paper_1004_0023_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode() + b"\0" + fh.read())
+    for path in [os.path.join(d, f) for f in KERNEL_SOURCES[which]] + [os.path.join(ROOT, "include", "pt.h")]:
+        with open(path, "rb") as fh:
+            h.update(os.path.basename(path).encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
-# kernel, from one ncu capture: (kernel, workload key) -> (kernel_source_hash() of the build
-# captured, bytes). A figure whose hash no longer matches the sources is reported as null.
+# kernel, from one ncu capture: (kernel, workload key) -> (source set, kernel_source_hash()
+# of the build captured, bytes). A figure whose hash no longer matches is reported as null.
 MEASURED_TRAFFIC: dict = {
     # one 1000-sweep launch of the N=256, P=64, R=64 plan (path 2, 384 threads): 1.60 MB read, 0 written
-    ("sweep_packed_kernel (int8, inline Philox)", "regular3_n256_p64_r64_2000"): ("526b0deafa5eb2d6", 1595904),
+    ("sweep_packed_kernel (int8, inline Philox)", "regular3_n256_p64_r64_2000"): ("sweep", "97048c22377e0ae3", 1595904),
     # one 500-sweep launch of the K4,4 lattice, bit-packed (path 4, 512 threads)
-    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("526b0deafa5eb2d6", 26657024 + 5120),
+    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("sweep", "97048c22377e0ae3", 26657024 + 5120),
+    # one graph-replayed launch of the 512-request mix, 1000 sweeps each (clusters of 2, one
+    # warp per chain): 1.288 TB read + 1.343 TB written, 1.85 B per attempt
+    ("batch_kernel", "batched_512x1000"): ("batch", "ebc14daccf9f3072", 1287723221504 + 1343270942720),
 }
 
 
@@ -97,8 +105,8 @@ def measured_traffic(kernel: str, key: str):
     ent = MEASURED_TRAFFIC.get((kernel, key))
     if ent is None:
         return None, "no ncu capture recorded for this kernel and workload"
-    src, nbytes = ent
-    if src != kernel_source_hash():
+    which, src, nbytes = ent
+    if src != kernel_source_hash(which):
         return None, "stale: the kernel sources changed since the ncu capture (%s)" % src
     return nbytes, "ncu dram__bytes_read.sum + dram__bytes_write.sum, per launch"
 
