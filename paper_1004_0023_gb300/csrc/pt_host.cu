@@ -511,12 +511,13 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     const int packed_dc = (dmax + 1 <= 4) ? 4 : ((dmax + 1 <= 8) ? 8 : 0);
     const bool packed_ok = (P % 8 == 0) && packed_dc > 0;
     const int want_path = opt ? opt->kernel_path : 0;
-    if (want_path < 0 || want_path > 7) {
+    if (want_path < 0 || want_path > 8) {
         free_ctx(c);
-        return create_fail(PT_EINVAL, "kernel_path must be 0..7");
+        return create_fail(PT_EINVAL, "kernel_path must be 0..8");
     }
     if ((want_path == kPathPacked || want_path == kPathPackedInline || want_path == kPathBits ||
-         want_path == kPathSplit || want_path == kPathSplitInline || want_path == kPathPackedChains) && !packed_ok) {
+         want_path == kPathSplit || want_path == kPathSplitInline || want_path == kPathPackedChains ||
+         want_path == kPathPeer) && !packed_ok) {
         free_ctx(c);
         return create_fail(PT_EINVAL, "the packed kernel needs P %% 8 == 0 and degree <= 7");
     }
@@ -577,6 +578,25 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         }
         return resident >= R;
     };
+    // path 8 when the produced-words layout fits and all R two-CTA clusters can be resident
+    auto peer_fits = [&](int th) {
+        if (!fits(kPathPacked) || th < 64) return false;
+        DevProblem q = p;
+        if (sweep_smem_bytes(q, kPathPeer, packed_dc) > (size_t)max_smem) q.tables_in_smem = 0;
+        if (sweep_smem_bytes(q, kPathPeer, packed_dc) > (size_t)max_smem) q.acc_in_smem = 0;
+        LaunchPlan probe;
+        probe.path = kPathPeer;
+        probe.dclass = packed_dc;
+        probe.threads = th;
+        probe.n_consumer = th;
+        probe.smem_bytes = sweep_smem_bytes(q, kPathPeer, packed_dc);
+        long long resident = 0;
+        if (prepare_sweep_kernel(probe) != cudaSuccess || sweep_resident_chains(q, probe, &resident) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        return resident >= R;
+    };
     if (path == 0) {
         path = kPathGeneric;
         if (packed_ok) {
@@ -602,13 +622,14 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                            c->plan.smem_bytes, max_smem);
     }
     if (opt && opt->threads_per_block > 0) {
-        const int tmax = (path == kPathGeneric || path == kPathSplit || path == kPathSplitInline) ? 512 : 1024;
+        const int tmax =
+            (path == kPathGeneric || path == kPathSplit || path == kPathSplitInline || path == kPathPeer) ? 512 : 1024;
         if (opt->threads_per_block % 32 || opt->threads_per_block > tmax) {
             free_ctx(c);
             return create_fail(PT_EINVAL, "threads_per_block must be a multiple of 32 <= %d for this kernel", tmax);
         }
         c->plan.threads = opt->threads_per_block;
-    } else if (path == kPathPacked || path == kPathSplit || path == kPathSplitInline) {
+    } else if (path == kPathPacked || path == kPathSplit || path == kPathSplitInline || path == kPathPeer) {
         c->plan.threads = 512;
     } else {
         // enough threads for the average level (units = items * padded groups per parity)
@@ -761,7 +782,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         return create_fail(PT_EINVAL, "swap_mode 1 needs all %d chains resident at once (%lld fit on %d SMs)", R,
                            resident, n_sm);
     }
-    if ((path == kPathSplit || path == kPathSplitInline) && resident < R) {
+    if ((path == kPathSplit || path == kPathSplitInline || path == kPathPeer) && resident < R) {
         // the two CTAs of a chain always run together, but the swap passes need every chain
         free_ctx(c);
         return create_fail(PT_EINVAL, "the split kernel needs all %d chains resident at once (%lld fit)", R,
@@ -831,6 +852,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                     if (th >= P / 16 + 1) cands.push_back({kPathSplitInline, th, 0});
             if (fits(kPathPackedInline))
                 for (int th : {256, 384, 512}) cands.push_back({kPathPackedInline, th, 0});
+            for (int th : {384, 512})
+                if (peer_fits(th)) cands.push_back({kPathPeer, th, 0});
             // every chain resident on one cluster (small problems: swaps never leave the
             // cluster), at the narrowest chain groups that fit and two wider ones
             for (int K : {1, 2, 4, 8})

@@ -73,7 +73,8 @@ enum {
     kPathBits = 4,
     kPathSplit = 5,
     kPathSplitInline = 6,
-    kPathPackedChains = 7
+    kPathPackedChains = 7,
+    kPathPeer = 8  // path 3's sweep on every thread of rank 0 of a two-CTA cluster; rank 1 makes its random words
 };
 
 struct LaunchPlan {

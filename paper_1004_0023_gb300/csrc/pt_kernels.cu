@@ -87,6 +87,7 @@ size_t split_smem_bytes(const DevProblem& p, int dclass, bool pre);
 
 size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass) {
     if (path == kPathGeneric) return GenericLayout(p).total;
+    if (path == kPathPeer) return FastLayout(p, dclass, true, false).total;
     if (path == kPathSplit || path == kPathSplitInline) return split_smem_bytes(p, dclass, path == kPathSplit);
     return FastLayout(p, dclass, path == kPathPacked, path == kPathBits).total;
 }
@@ -412,7 +413,10 @@ __device__ __forceinline__ void produce_words(uint4* buf, uint32_t t, const uint
 // random words of sweep s+1 into one shared buffer while the consumer warps run the levels
 // of sweep s out of the other; consumers synchronise levels on named barrier 1 and both
 // groups meet once per sweep.
-template <int DC, bool PRE, bool BITS = false, bool SPEC = true>
+// PEER (path 8): the CTA is rank 0 of a cluster of two, and rank 1 (peer_producer below)
+// writes the random words into this CTA's buffers through distributed shared memory; every
+// thread here sweeps, and the two CTAs meet at a cluster barrier once per sweep.
+template <int DC, bool PRE, bool BITS = false, bool SPEC = true, bool PEER = false>
 __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot, long long t0, long long q0,
                                                   int n_sweeps, int sweeps_per_swap, long long timeout_ns,
                                                   int n_consumer, unsigned char* smem) {
@@ -490,9 +494,12 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
         s_sum[0] = s_sum[1] = s_sum[2] = 0;  // the sweep's dE, dM and flips
     }
     __syncthreads();
-    if (PRE && !consumer)
+    if (PRE && !PEER && !consumer)
         produce_words(rbuf, (uint32_t)t0, s_items, n_items, G, lg, gmask, tid - NC, nt - NC, (uint32_t)slot, key);
-    if (PRE) __syncthreads();
+    if (PEER)
+        cluster_barrier();  // the peer CTA has written the first sweep's words
+    else if (PRE)
+        __syncthreads();
 
     // Level 0 of the next sweep can be evaluated while the swap decision is still pending:
     // its inputs are the spins after this sweep and the next sweep's random words; only its
@@ -580,7 +587,13 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
         }
         // the next sweep's random words are complete and every consumer has finished sweep s;
         // a wait that gave up in the previous sweep ends the launch here, for every thread
-        __syncthreads();
+        if constexpr (PEER) {
+            // the peer CTA learns at the same barrier that this CTA leaves, and leaves too
+            if (tid == 0) cg::this_cluster().map_shared_rank(s_ctl, 1)[6] = s_ctl[5];
+            cluster_barrier();
+        } else {
+            __syncthreads();
+        }
         if (s_ctl[5]) return;  // status holds PT_ETIMEDOUT
         if (!consumer) continue;
 
@@ -659,6 +672,59 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
         p.rung_of_slot[slot] = rung;
         p.slot_of_rung[rung] = slot;
     }
+}
+
+// Path 8, rank 1 of each cluster: the random words of every sweep of chain `slot`, written
+// one sweep ahead into rank 0's double buffer through distributed shared memory (the words
+// are a function of the chain, the sweep and the update, never of the rung, so they need no
+// swap decision). It passes the same cluster barriers as rank 0 (one before the first sweep,
+// one per sweep) and leaves after the one at which rank 0 reports that it leaves.
+template <int DC>
+__device__ void peer_producer(const DevProblem& p, int slot, long long t0, int n_sweeps, unsigned char* smem) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const FastLayout L(p, DC, true, false);
+    uint32_t* s_items = reinterpret_cast<uint32_t*>(smem + L.items);
+    int* s_ctl = reinterpret_cast<int*>(smem + L.ctl);
+    uint4* peer_rbuf = cluster.map_shared_rank(reinterpret_cast<uint4*>(smem + L.rbuf), 0);
+    const int n_items = 2 * p.N, G = p.P >> 3;
+    int lg = 0;
+    while ((1 << lg) < G) ++lg;
+    const int gmask = (1 << lg) - 1;
+    for (int x = tid; x < n_items; x += nt) s_items[x] = p.items[x];
+    if (tid == 0) s_ctl[6] = 0;
+    const PhiloxKey key = philox_schedule(p.key0, p.key1);
+    __syncthreads();
+    produce_words(peer_rbuf, (uint32_t)t0, s_items, n_items, G, lg, gmask, tid, nt, (uint32_t)slot, key);
+    cluster_barrier();
+    for (int s = 0; s < n_sweeps; ++s) {
+        if (s + 1 < n_sweeps)
+            produce_words(peer_rbuf + (size_t)((s + 1) & 1) * n_items * G, (uint32_t)(t0 + s + 1), s_items, n_items, G,
+                          lg, gmask, tid, nt, (uint32_t)slot, key);
+        cluster_barrier();
+        if (s_ctl[6]) return;  // rank 0's swap wait gave up; it leaves after this barrier too
+    }
+}
+
+// Path 8: R clusters of two CTAs; rank 0 sweeps chain (cluster index) with every thread,
+// rank 1 produces its random words. The cluster shape is compiled in, and checked on entry
+// (both CTAs return before any barrier or remote access if it is not 2).
+template <int DC>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(512, 1)
+    sweep_peer_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
+                      long long timeout_ns, int n_consumer) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    if (cluster.num_blocks() != 2) {
+        if (threadIdx.x == 0) atomicCAS(p.status, 0, PT_ECUDA);
+        return;
+    }
+    const int slot = (int)(blockIdx.x >> 1);
+    if (cluster.block_rank() == 0)
+        sweep_packed_body<DC, true, false, true, true>(p, slot, t0, q0, n_sweeps, sweeps_per_swap, timeout_ns,
+                                                       blockDim.x, smem);
+    else
+        peer_producer<DC>(p, slot, t0, n_sweeps, smem);
 }
 
 template <int DC, bool PRE, int MAXT, bool BITS = false>
@@ -1155,6 +1221,8 @@ static const void* sweep_fn(const LaunchPlan& plan) {
             default: return (const void*)sweep_kernel<32>;
         }
     }
+    if (plan.path == kPathPeer)
+        return plan.dclass == 4 ? (const void*)sweep_peer_kernel<4> : (const void*)sweep_peer_kernel<8>;
     if (plan.path == kPathSplit)
         return plan.dclass == 4 ? (const void*)sweep_split_kernel<4, true> : (const void*)sweep_split_kernel<8, true>;
     if (plan.path == kPathSplitInline)
@@ -1215,7 +1283,7 @@ static cudaLaunchConfig_t split_config(const DevProblem& p, const LaunchPlan& pl
 
 cudaError_t sweep_resident_chains(const DevProblem& p, const LaunchPlan& plan, long long* chains) {
     *chains = 0;
-    if (plan.path == kPathSplit || plan.path == kPathSplitInline) {
+    if (plan.path == kPathSplit || plan.path == kPathSplitInline || plan.path == kPathPeer) {
         cudaLaunchAttribute attr[2];
         cudaLaunchConfig_t cfg = split_config(p, plan, false, 0, attr);
         int clusters = 0;
@@ -1238,7 +1306,7 @@ cudaError_t launch_sweeps(const DevProblem& p, const LaunchPlan& plan, long long
     int n_consumer = plan.n_consumer;
     void* args[] = {&pp, &t0, &q0, &n_sweeps, &sweeps_per_swap, &timeout_ns, &n_consumer};
     const void* fn = sweep_fn(plan);
-    if (plan.path == kPathSplit || plan.path == kPathSplitInline) {
+    if (plan.path == kPathSplit || plan.path == kPathSplitInline || plan.path == kPathPeer) {
         cudaLaunchAttribute attr[2];
         cudaLaunchConfig_t cfg = split_config(p, plan, cooperative, s, attr);
         const cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);

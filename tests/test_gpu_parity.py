@@ -101,6 +101,21 @@ def test_medium_workload_full_length():
         assert_same(g, o, "sweep %d" % (100 * (chunk + 1)))
 
 
+def test_medium_workload_on_path_8():
+    """N=256, P=64, R=64 with each chain's random words made by a second CTA of its cluster
+    (path 8), 384 and 512 threads, checked every 200 sweeps."""
+    prob = instances.workload("regular3_n256_p64_r64", 1)
+    for th in (384, 512):
+        g, o = both(prob, kernel_path=8, threads_per_block=th)
+        assert g.info.kernel_path == 8
+        for chunk in range(3):
+            g.run(200, 1)
+            o.run(200, 1)
+            assert_same(g, o, "threads %d sweep %d" % (th, 200 * (chunk + 1)))
+        g.close()
+        o.close()
+
+
 @pytest.mark.parametrize("seed_index", [2, 3])
 def test_medium_workload_other_seeds(seed_index):
     prob = instances.workload("regular3_n256_p64_r64", seed_index)
@@ -120,7 +135,8 @@ def test_layouts_and_swap_modes_give_identical_bits():
                dict(kernel_path=3, threads_per_block=256, producer_threads=160), dict(kernel_path=3, swap_mode=2),
                dict(kernel_path=4), dict(kernel_path=4, threads_per_block=32), dict(kernel_path=4, swap_mode=2),
                dict(kernel_path=3, threads_per_block=64, producer_threads=32),
-               dict(test_exact_swaps=1), dict(test_exact_swaps=1, swap_mode=2)):
+               dict(test_exact_swaps=1), dict(test_exact_swaps=1, swap_mode=2),
+               dict(kernel_path=8), dict(kernel_path=8, threads_per_block=384), dict(kernel_path=8, swap_mode=2)):
         g = pt.PT.from_problem(prob, **kw)
         g.run(300, 1)
         g.run(77, 5)
@@ -133,7 +149,7 @@ def test_layouts_and_swap_modes_give_identical_bits():
                 assert np.array_equal(np.asarray(cur[1][k]), np.asarray(ref[1][k])), (kw, k)
 
 
-@pytest.mark.parametrize("path", [1, 2, 3, 4])
+@pytest.mark.parametrize("path", [1, 2, 3, 4, 8])
 def test_medium_workload_each_kernel_path(path):
     prob = instances.workload("regular3_n256_p64_r64", 4)
     g, o = both(prob, kernel_path=path)
@@ -143,7 +159,7 @@ def test_medium_workload_each_kernel_path(path):
     assert_same(g, o, "path %d" % path)
 
 
-@pytest.mark.parametrize("path", [1, 2, 3, 4])
+@pytest.mark.parametrize("path", [1, 2, 3, 4, 8])
 @pytest.mark.parametrize("name", ["prism_p8_r3", "complete8_p16_r4"])
 def test_tiny_packed_problems_each_path(name, path):
     prob = TINY[name]
@@ -173,7 +189,7 @@ def test_lattice_workload_bit_packed():
     assert_same(g, o, "sweep %d" % prob.n_sweeps)
 
 
-@pytest.mark.parametrize("path", [2, 3, 4])
+@pytest.mark.parametrize("path", [2, 3, 4, 8])
 @pytest.mark.parametrize("P", [8, 24, 136])
 def test_packed_row_lengths(P, path):
     """Rows of 8, 24 and 136 copies (1, 3 and 17 bytes bit-packed): the periodic Trotter
@@ -331,12 +347,13 @@ def test_invalid_arguments_are_rejected():
     g.run(10, 1)  # still usable after argument errors
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("path", [0, 1, 2, 3, 4, 8])
 def test_partner_that_never_publishes_times_out_without_fault(path):
     """The chain on rung 3 withholds its mailbox: its partner's bounded wait runs out, the
     call reports PT_ETIMEDOUT, and the device stays usable for a new context. On every
     one-CTA kernel, with sweeps left after the one whose wait gave up: the CTA that gave up
-    leaves at the next barrier without touching its random-word buffers."""
+    leaves at the next barrier without touching its random-word buffers; on path 8 its
+    random-word CTA learns at that same cluster barrier and leaves with it."""
     prob = instances.workload("regular3_n16_p32_r16", 5)
     g = pt.PT.from_problem(prob, wait_timeout_ms=200, test_withhold_rung=3, swap_mode=1, kernel_path=path)
     g.run(4, 1)
