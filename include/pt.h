@@ -90,7 +90,11 @@ typedef struct {
                                    group_threads threads, swap passes decided in shared memory
                                    (needs what paths 2-6 need; for problems too small to fill
                                    the GPU, whose sweeps would otherwise wait on the swap
-                                   mailboxes between SMs) */
+                                   mailboxes between SMs), 8 = path 3 with every thread
+                                   sweeping and the random words made by a second CTA of a
+                                   two-CTA cluster per chain, written into the first one's
+                                   shared memory one sweep ahead (needs all R clusters
+                                   resident at once; for ladders that leave SMs idle) */
     int32_t producer_threads;   /* paths 3 and 5: threads producing random words (0 = auto) */
     int32_t test_exact_swaps;   /* test hook: 1 = skip the FP32 pre-decision of swaps and always
                                    evaluate the FP64 rule (results are identical either way) */
@@ -101,7 +105,7 @@ typedef struct {
                                    for the process; results never depend on it) */
     int32_t no_autotune;        /* 0: when kernel_path and threads_per_block are automatic and
                                    the chains are int8 in shared memory, pt_create times a
-                                   short run of each candidate plan (paths 2, 3, 5, 6 and 7,
+                                   short run of each candidate plan (paths 2, 3, 5, 6, 7 and 8,
                                    block sizes 256-512, clusters of 1-8 CTAs), keeps the fastest
                                    and resets the context to its initial state; the choice is
                                    remembered per shape for the process. Results never depend
