@@ -68,7 +68,8 @@ KERNEL_NAMES = {1: "sweep_kernel (byte-wise)", 2: "sweep_packed_kernel (int8, in
                 3: "sweep_packed_kernel (int8, producer warps)", 4: "sweep_packed_kernel (bit-packed)",
                 5: "sweep_split_kernel (int8, producer warps, each chain on a 2-CTA cluster)",
                 6: "sweep_split_kernel (int8, inline Philox, each chain on a 2-CTA cluster)",
-                7: "batch_kernel (all chains of the problem packed on one cluster, swaps in shared memory)"}
+                7: "batch_kernel (all chains of the problem packed on one cluster, swaps in shared memory)",
+                8: "sweep_peer_kernel (int8, random words from a second CTA of each chain's cluster)"}
 
 
 # The sources each kernel is compiled from (its own file and the headers it includes).
@@ -123,6 +124,8 @@ def parse_args(argv=None):
     ap.add_argument("--kernel-path", type=int, default=0,
                     help="single-problem workload: force the kernel path (profiling runs; 0 = autotuned)")
     ap.add_argument("--threads-per-block", type=int, default=0, help="force its block size (with --kernel-path)")
+    ap.add_argument("--cluster-size", type=int, default=0, help="with --kernel-path 7: CTAs of the one cluster")
+    ap.add_argument("--group-threads", type=int, default=0, help="with --kernel-path 7: threads per chain group")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain-compare", action="store_true", help="skip the one-pt_run-per-request comparison")
@@ -435,7 +438,8 @@ def plain_headline(args, pt, instances, torch, n_sm, rank, world, local_rank, de
         prob.n_sweeps = args.sweeps
     rec = plain_record(args.workload, args, pt, instances, torch, n_sm, None, rank, world, device, prob=prob,
                        steps=args.steps, warmup=args.warmup, kernel_path=args.kernel_path,
-                       threads_per_block=args.threads_per_block, clocks=True)
+                       threads_per_block=args.threads_per_block, clocks=True, cluster_size=args.cluster_size,
+                       group_threads=args.group_threads)
     out = {"metric": METRIC, "value": rec["value"], "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "int8/int32 (integer-exact)", "data": "synthetic",
@@ -447,14 +451,15 @@ def plain_headline(args, pt, instances, torch, n_sm, rank, world, local_rank, de
 
 
 def plain_record(name, args, pt, instances, torch, n_sm, sm_mhz, rank, world, device, prob=None, steps=None,
-                 warmup=2, kernel_path=0, threads_per_block=0, clocks=False):
+                 warmup=2, kernel_path=0, threads_per_block=0, clocks=False, cluster_size=0, group_threads=0):
     """A single-problem workload on the device: the autotuned plan, L2 flushed between
     timed steps, value, roofline and a CPU-oracle baseline."""
     prob = prob or instances.workload(name, 1 + rank)
     steps = steps or args.plain_steps
     stream = torch.cuda.Stream()
     ctx = pt.PT.from_problem(prob, stream=stream.cuda_stream, kernel_path=kernel_path,
-                             threads_per_block=threads_per_block)
+                             threads_per_block=threads_per_block, cluster_size=cluster_size,
+                             group_threads=group_threads)
     info = ctx.info
     for _ in range(warmup):
         ctx.run(prob.n_sweeps, prob.sweeps_per_swap)
