@@ -496,10 +496,14 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     __syncthreads();
     if (PRE && !PEER && !consumer)
         produce_words(rbuf, (uint32_t)t0, s_items, n_items, G, lg, gmask, tid - NC, nt - NC, (uint32_t)slot, key);
-    if (PEER)
-        cluster_barrier();  // the peer CTA has written the first sweep's words
-    else if (PRE)
+    if (PEER) {
+        // the peer CTA has written the first sweep's words (its arrival releases them); this
+        // CTA's arrival orders nothing of its own, so it is relaxed
+        cluster_arrive_relaxed();
+        cluster_wait_acquire();
+    } else if (PRE) {
         __syncthreads();
+    }
 
     // Level 0 of the next sweep can be evaluated while the swap decision is still pending:
     // its inputs are the spins after this sweep and the next sweep's random words; only its
@@ -588,9 +592,17 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
         // the next sweep's random words are complete and every consumer has finished sweep s;
         // a wait that gave up in the previous sweep ends the launch here, for every thread
         if constexpr (PEER) {
-            // the peer CTA learns at the same barrier that this CTA leaves, and leaves too
-            if (tid == 0) cg::this_cluster().map_shared_rank(s_ctl, 1)[6] = s_ctl[5];
-            cluster_barrier();
+            // the peer CTA learns at the same barrier that this CTA leaves, and leaves too.
+            // Otherwise the arrival is relaxed: a release would first wait for this sweep's
+            // mailbox store to reach L2, on the way to the swap decision. The words this CTA
+            // read are in registers by now, so the peer may overwrite their buffer.
+            if (s_ctl[5]) {
+                if (tid == 0) cg::this_cluster().map_shared_rank(s_ctl, 1)[6] = 1;
+                cluster_arrive_release();
+            } else {
+                cluster_arrive_relaxed();
+            }
+            cluster_wait_acquire();
         } else {
             __syncthreads();
         }
@@ -696,7 +708,7 @@ __device__ void peer_producer(const DevProblem& p, int slot, long long t0, int n
     const PhiloxKey key = philox_schedule(p.key0, p.key1);
     __syncthreads();
     produce_words(peer_rbuf, (uint32_t)t0, s_items, n_items, G, lg, gmask, tid, nt, (uint32_t)slot, key);
-    cluster_barrier();
+    cluster_barrier();  // release: the words are visible to rank 0 after its wait
     for (int s = 0; s < n_sweeps; ++s) {
         if (s + 1 < n_sweeps)
             produce_words(peer_rbuf + (size_t)((s + 1) & 1) * n_items * G, (uint32_t)(t0 + s + 1), s_items, n_items, G,
