@@ -38,7 +38,7 @@ def test_autotuned_context_starts_from_the_initial_state_and_matches_the_oracle(
     prob = _problem(98, 64, 22, 4242)
     g = pt.PT.from_problem(prob)
     assert g.info.tuned_plans >= 2
-    assert g.info.kernel_path in (2, 3, 5, 6)
+    assert g.info.kernel_path in (2, 3, 5, 6, 7, 8)
     o = Oracle.from_problem(prob, threads=THREADS)
     _same(g, o)  # the timed sweeps were undone
     g.run(150, 1)
