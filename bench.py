@@ -92,13 +92,14 @@ def kernel_source_hash(which: str) -> str:
 # kernel, from one ncu capture: (kernel, workload key) -> (source set, kernel_source_hash()
 # of the build captured, bytes). A figure whose hash no longer matches is reported as null.
 MEASURED_TRAFFIC: dict = {
-    # one 1000-sweep launch of the N=256, P=64, R=64 plan (path 2, 384 threads): 1.60 MB read, 0 written
-    ("sweep_packed_kernel (int8, inline Philox)", "regular3_n256_p64_r64_2000"): ("sweep", "97048c22377e0ae3", 1595904),
+    # one 1000-sweep launch of the N=256, P=64, R=64 plan (path 8, 384 threads): 1.79 MB read, 0 written
+    ("sweep_peer_kernel (int8, random words from a second CTA of each chain's cluster)", "regular3_n256_p64_r64_2000"):
+        ("sweep", "eee35048a51f7642", 1788928),
     # one 500-sweep launch of the K4,4 lattice, bit-packed (path 4, 512 threads)
-    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("sweep", "97048c22377e0ae3", 26657024 + 5120),
+    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("sweep", "eee35048a51f7642", 26765824 + 4352),
     # one graph-replayed launch of the 512-request mix, 1000 sweeps each (clusters of 2, one
-    # warp per chain): 1.288 TB read + 1.343 TB written, 1.85 B per attempt
-    ("batch_kernel", "batched_512x1000"): ("batch", "ebc14daccf9f3072", 1287723221504 + 1343270942720),
+    # warp per chain): 1.287 TB read + 1.343 TB written, 1.85 B per attempt
+    ("batch_kernel", "batched_512x1000"): ("batch", "846e749a1a388b79", 1286753979392 + 1343174020352),
 }
 
 
