@@ -94,8 +94,15 @@ typedef struct {
                                    sweeping and the random words made by a second CTA of a
                                    two-CTA cluster per chain, written into the first one's
                                    shared memory one sweep ahead (needs all R clusters
-                                   resident at once; for ladders that leave SMs idle) */
-    int32_t producer_threads;   /* paths 3 and 5: threads producing random words (0 = auto) */
+                                   resident at once; for ladders that leave SMs idle),
+                                   9 = path 2 (or path 3 with producer_threads > 0) with the
+                                   CTAs of all R chains in one thread-block cluster and the
+                                   swap mailboxes in every CTA's shared memory, so that a
+                                   chain waits for its partner on its own SM (needs what
+                                   paths 2-6 need, R <= 16 and threads_per_block <= 384) */
+    int32_t producer_threads;   /* paths 3 and 5: threads producing random words (0 = auto);
+                                   path 9: 0 = random words inline, else this many producer
+                                   threads (a multiple of 32 below threads_per_block) */
     int32_t test_exact_swaps;   /* test hook: 1 = skip the FP32 pre-decision of swaps and always
                                    evaluate the FP64 rule (results are identical either way) */
     int32_t cluster_size;       /* batched launches: CTAs per thread-block cluster (1..16), or
@@ -105,8 +112,8 @@ typedef struct {
                                    for the process; results never depend on it) */
     int32_t no_autotune;        /* 0: when kernel_path and threads_per_block are automatic and
                                    the chains are int8 in shared memory, pt_create times a
-                                   short run of each candidate plan (paths 2, 3, 5, 6, 7 and 8,
-                                   block sizes 256-512, clusters of 1-8 CTAs), keeps the fastest
+                                   short run of each candidate plan (paths 2, 3, 5, 6, 7, 8 and
+                                   9, block sizes 128-512, clusters of 1-16 CTAs), keeps the fastest
                                    and resets the context to its initial state; the choice is
                                    remembered per shape for the process. Results never depend
                                    on it. 1: off. */

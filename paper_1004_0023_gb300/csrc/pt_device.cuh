@@ -74,35 +74,39 @@ __device__ __forceinline__ double det_exp(double x) {
     return __dmul_rn(poly, scale);
 }
 
-// Swap decision for X on rung rl and Y on rung rl + 1 at pass q.
+// The uniform word of swap pass q for the pair (rl, rl + 1).
 template <typename Key = PhiloxKey>
-__device__ __forceinline__ bool swap_accept(long long EX, long long EY, long long MX, long long MY,
-                                            double a, double c, uint32_t q, uint32_t rl,
-                                            const Key& key) {
+__device__ __forceinline__ uint32_t swap_word(uint32_t q, uint32_t rl, const Key& key) {
+    return philox(make_uint4(q, rl, 0u, kTagSwap << 28), key).x;
+}
+
+// Swap decision for X on rung rl and Y on rung rl + 1, with the pass's uniform word from
+// word() (called only when Delta falls in the band where it matters).
+template <typename WordFn>
+__device__ __forceinline__ bool swap_accept_by(long long EX, long long EY, long long MX, long long MY, double a,
+                                               double c, WordFn word) {
     const double dE = __ll2double_rn(EX - EY);
     const double dM = __ll2double_rn(MX - MY);
     const double delta = __dadd_rn(__dmul_rn(a, dE), __dmul_rn(c, dM));
     if (delta >= 0.0) return true;
     if (!(delta > -23.0)) return false;
-    const uint4 u = philox(make_uint4(q, rl, 0u, kTagSwap << 28), key);
     const double v = floor(__dmul_rn(det_exp(delta), 4294967296.0));
     const uint32_t ts = (v >= 4294967295.0) ? 0xFFFFFFFFu : (uint32_t)v;
-    return u.x < ts;
+    return word() < ts;
 }
 
 // The same decision without FP64 in the common case. GB300's FP64 pipe makes the ~40
-// dependent FP64 operations of swap_accept cost over a microsecond, so Delta and exp(Delta)
+// dependent FP64 operations of swap_accept_by cost over a microsecond, so Delta and exp(Delta)
 // are first estimated in FP32 with an error bound:
 //   |D - Delta| <= err = 5*2^-24 * (|a dE| + |c dM|)   (conversions of a, c, dE, dM, two
 //   products, one sum, and the FP64 roundings of Delta itself, with room to spare), and
 //   2^32 exp(D) within a relative 1e-5 + 1.01 err of 2^32 exp(Delta) (expf is within 2 ulp).
 // The estimate decides only when u is farther than that margin (plus float rounding of u)
-// from the threshold, or Delta's sign and the -23 cut are certain; otherwise swap_accept
-// decides. Either way the result equals swap_accept's.
-template <typename Key = PhiloxKey>
-__device__ __forceinline__ bool swap_accept_fast(long long EX, long long EY, long long MX, long long MY,
-                                                 double a, double c, uint32_t q, uint32_t rl,
-                                                 const Key& key, bool exact_only) {
+// from the threshold, or Delta's sign and the -23 cut are certain; otherwise swap_accept_by
+// decides. Either way the result equals swap_accept_by's.
+template <typename WordFn>
+__device__ __forceinline__ bool swap_accept_fast_by(long long EX, long long EY, long long MX, long long MY,
+                                                    double a, double c, WordFn word, bool exact_only) {
     if (!exact_only) {
         const float pa = (float)a * (float)(EX - EY);
         const float pc = (float)c * (float)(MX - MY);
@@ -112,16 +116,29 @@ __device__ __forceinline__ bool swap_accept_fast(long long EX, long long EY, lon
         if (err < 0.25f) {
             if (D < -23.5f) return false;                         // Delta <= -23
             if (D + 2.0f * err < 0.0f && D > -22.5f) {
-                const uint4 r4 = philox(make_uint4(q, rl, 0u, kTagSwap << 28), key);
                 const float v = 4294967296.0f * expf(D);
                 const float margin = v * (1.0e-5f + 1.01f * err) + 512.0f;
-                const float uf = (float)r4.x;
+                const float uf = (float)word();
                 if (uf + margin < v) return true;
                 if (uf - margin > v) return false;
             }
         }
     }
-    return swap_accept<Key>(EX, EY, MX, MY, a, c, q, rl, key);
+    return swap_accept_by(EX, EY, MX, MY, a, c, word);
+}
+
+// The two rules with the word drawn from (q, rl) under `key` when needed.
+template <typename Key = PhiloxKey>
+__device__ __forceinline__ bool swap_accept(long long EX, long long EY, long long MX, long long MY,
+                                            double a, double c, uint32_t q, uint32_t rl,
+                                            const Key& key) {
+    return swap_accept_by(EX, EY, MX, MY, a, c, [&] { return swap_word(q, rl, key); });
+}
+template <typename Key = PhiloxKey>
+__device__ __forceinline__ bool swap_accept_fast(long long EX, long long EY, long long MX, long long MY,
+                                                 double a, double c, uint32_t q, uint32_t rl,
+                                                 const Key& key, bool exact_only) {
+    return swap_accept_fast_by(EX, EY, MX, MY, a, c, [&] { return swap_word(q, rl, key); }, exact_only);
 }
 
 // ------------------------------------------------------------------------- PTX helpers
@@ -172,6 +189,24 @@ __device__ __forceinline__ void cluster_barrier() {
 __device__ __forceinline__ void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory"); }
 __device__ __forceinline__ void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait_acquire() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
+
+// A 64-bit word into CTA `rank`'s copy of a shared-memory location (distributed shared
+// memory), relaxed at cluster scope: the readers poll the word itself, so no other ordering
+// is needed.
+__device__ __forceinline__ void st_cluster_u64(const void* local, unsigned rank, unsigned long long v) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("st.relaxed.cluster.shared::cluster.u64 [%0], %1;" ::"r"(ra), "l"(v) : "memory");
+}
+
+// This CTA's shared-memory word, as the other CTAs of the cluster last wrote it.
+__device__ __forceinline__ unsigned long long ld_cluster_local_u64(const void* local) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned long long v;
+    asm volatile("ld.relaxed.cluster.shared::cta.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
 
 __device__ __forceinline__ void named_barrier(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");

@@ -511,13 +511,13 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     const int packed_dc = (dmax + 1 <= 4) ? 4 : ((dmax + 1 <= 8) ? 8 : 0);
     const bool packed_ok = (P % 8 == 0) && packed_dc > 0;
     const int want_path = opt ? opt->kernel_path : 0;
-    if (want_path < 0 || want_path > 8) {
+    if (want_path < 0 || want_path > 9) {
         free_ctx(c);
-        return create_fail(PT_EINVAL, "kernel_path must be 0..8");
+        return create_fail(PT_EINVAL, "kernel_path must be 0..9");
     }
     if ((want_path == kPathPacked || want_path == kPathPackedInline || want_path == kPathBits ||
          want_path == kPathSplit || want_path == kPathSplitInline || want_path == kPathPackedChains ||
-         want_path == kPathPeer) && !packed_ok) {
+         want_path == kPathPeer || want_path == kPathCluster) && !packed_ok) {
         free_ctx(c);
         return create_fail(PT_EINVAL, "the packed kernel needs P %% 8 == 0 and degree <= 7");
     }
@@ -540,6 +540,15 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         return create_fail(PT_EINVAL,
                            "kernel_path 7 takes cluster_size (0..16) and group_threads (0 or 32..512, a power of "
                            "two), no threads_per_block and no test hooks");
+    }
+    if (want_path == kPathCluster &&
+        (R > 16 || (opt->threads_per_block != 0 && (opt->threads_per_block < 64 || opt->threads_per_block > 384)) ||
+         opt->producer_threads < 0 || opt->producer_threads % 32 ||
+         opt->producer_threads >= (opt->threads_per_block ? opt->threads_per_block : 128))) {
+        free_ctx(c);
+        return create_fail(PT_EINVAL,
+                           "kernel_path 9 needs R <= 16, threads_per_block 0 or 64..384 and producer_threads a "
+                           "multiple of 32 below it (0 = random words inline)");
     }
     int path = want_chains ? kPathPackedInline : want_path;
     const int want_threads = opt ? opt->threads_per_block : 0;
@@ -613,9 +622,11 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     }
     c->plan.path = path;
     c->plan.dclass = (path == kPathGeneric) ? dclass : packed_dc;
-    if (p.tables_in_smem && sweep_smem_bytes(p, path, c->plan.dclass) > (size_t)max_smem) p.tables_in_smem = 0;
-    if (p.acc_in_smem && sweep_smem_bytes(p, path, c->plan.dclass) > (size_t)max_smem) p.acc_in_smem = 0;
-    c->plan.smem_bytes = sweep_smem_bytes(p, path, c->plan.dclass);
+    const bool cl_pre = path == kPathCluster && opt->producer_threads > 0;
+    if (p.tables_in_smem && sweep_smem_bytes(p, path, c->plan.dclass, cl_pre) > (size_t)max_smem)
+        p.tables_in_smem = 0;
+    if (p.acc_in_smem && sweep_smem_bytes(p, path, c->plan.dclass, cl_pre) > (size_t)max_smem) p.acc_in_smem = 0;
+    c->plan.smem_bytes = sweep_smem_bytes(p, path, c->plan.dclass, cl_pre);
     if ((long long)c->plan.smem_bytes > (long long)max_smem) {
         free_ctx(c);
         return create_fail(PT_EINVAL, "one chain needs %zu bytes of shared memory; the device allows %d",
@@ -631,6 +642,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         c->plan.threads = opt->threads_per_block;
     } else if (path == kPathPacked || path == kPathSplit || path == kPathSplitInline || path == kPathPeer) {
         c->plan.threads = 512;
+    } else if (path == kPathCluster) {
+        c->plan.threads = 128;
     } else {
         // enough threads for the average level (units = items * padded groups per parity)
         int G = ((P / 2) + 3) / 4, Gp = 1;
@@ -641,6 +654,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         c->plan.threads = (int)std::min<long long>(512, std::max<long long>(128, avg));
     }
     c->plan.n_consumer = c->plan.threads;
+    if (path == kPathCluster) c->plan.n_consumer = c->plan.threads - opt->producer_threads;
     if (path == kPathPacked || path == kPathSplit) {
         int prod = (opt && opt->producer_threads > 0) ? opt->producer_threads
                                                       : std::max(32, (c->plan.threads / 4) / 32 * 32);
@@ -782,7 +796,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         return create_fail(PT_EINVAL, "swap_mode 1 needs all %d chains resident at once (%lld fit on %d SMs)", R,
                            resident, n_sm);
     }
-    if ((path == kPathSplit || path == kPathSplitInline || path == kPathPeer) && resident < R) {
+    if ((path == kPathSplit || path == kPathSplitInline || path == kPathPeer || path == kPathCluster) &&
+        resident < R) {
         // the two CTAs of a chain always run together, but the swap passes need every chain
         free_ctx(c);
         return create_fail(PT_EINVAL, "the split kernel needs all %d chains resident at once (%lld fit)", R,
@@ -854,6 +869,13 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                 for (int th : {256, 384, 512}) cands.push_back({kPathPackedInline, th, 0});
             for (int th : {384, 512})
                 if (peer_fits(th)) cands.push_back({kPathPeer, th, 0});
+            // every chain's CTA in one cluster, swap mailboxes in shared memory (R <= 16), with
+            // the random words inline or from producer warps
+            if (R <= 16)
+                for (int th : {128, 256}) {
+                    cands.push_back({kPathCluster, th, 0});
+                    cands.push_back({kPathCluster, th, th / 4});
+                }
             // every chain resident on one cluster (small problems: swaps never leave the
             // cluster), at the narrowest chain groups that fit and two wider ones
             for (int K : {1, 2, 4, 8})
@@ -879,13 +901,15 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             }
             pc.acc_in_smem = (size_t)R * kAccCount * 8 <= 16384 ? 1 : 0;
             pc.tables_in_smem = (size_t)R * p.nL3 * 4 <= 49152 ? 1 : 0;
-            if (pc.tables_in_smem && sweep_smem_bytes(pc, cd.path, packed_dc) > (size_t)max_smem) pc.tables_in_smem = 0;
-            if (pc.acc_in_smem && sweep_smem_bytes(pc, cd.path, packed_dc) > (size_t)max_smem) pc.acc_in_smem = 0;
+            const bool cpre = cd.path == kPathCluster && cd.producers > 0;
+            if (pc.tables_in_smem && sweep_smem_bytes(pc, cd.path, packed_dc, cpre) > (size_t)max_smem)
+                pc.tables_in_smem = 0;
+            if (pc.acc_in_smem && sweep_smem_bytes(pc, cd.path, packed_dc, cpre) > (size_t)max_smem) pc.acc_in_smem = 0;
             pl.path = cd.path;
             pl.dclass = packed_dc;
             pl.threads = cd.threads;
             pl.n_consumer = cd.threads - cd.producers;
-            pl.smem_bytes = sweep_smem_bytes(pc, cd.path, packed_dc);
+            pl.smem_bytes = sweep_smem_bytes(pc, cd.path, packed_dc, cpre);
             int cols = 1;
             if (cd.path == kPathSplit || cd.path == kPathSplitInline) {
                 cols = P / 16 + 1;
@@ -1025,6 +1049,21 @@ static int guard(pt_ctx* c) {
 }
 
 static int enqueue_sweeps(pt_ctx* c, long long n, int sps) {
+    if (c->plan.path == kPathCluster) {
+        // mailboxes in shared memory, cleared by every launch: only the sweep counter bounds one
+        long long done = 0;
+        while (done < n) {
+            long long chunk = n - done;
+            chunk = std::min<long long>(chunk, sps > 0 ? ((1ll << 30) / sps) * sps : (1ll << 30));
+            CUDA_OR_FAIL(c, launch_sweeps(c->dp, c->plan, c->t, c->q, (int)chunk, sps, c->timeout_ns, sps > 0,
+                                          c->stream));
+            c->launches += 1;
+            c->t += chunk;
+            if (sps > 0) c->q += chunk / sps;
+            done += chunk;
+        }
+        return PT_OK;
+    }
     if (c->plan.path == kPathPackedChains) {
         // swaps in shared memory: no mailboxes, so only the sweep counter bounds a launch
         long long done = 0;

@@ -27,6 +27,7 @@ struct alignas(16) Mailbox {
     unsigned long long b;
 };
 constexpr long long kTagPeriod = 16777215ll;
+constexpr int kClusterMailPasses = 4;  // path 9: swap passes whose mailboxes each CTA holds at once
 
 // Per-rung statistics, in this order, as unsigned 64-bit two's-complement sums.
 enum { kAccN = 0, kAccE, kAccE2, kAccM, kAccM2, kAccFlip, kAccCount };
@@ -74,7 +75,8 @@ enum {
     kPathSplit = 5,
     kPathSplitInline = 6,
     kPathPackedChains = 7,
-    kPathPeer = 8  // path 3's sweep on every thread of rank 0 of a two-CTA cluster; rank 1 makes its random words
+    kPathPeer = 8,  // path 3's sweep on every thread of rank 0 of a two-CTA cluster; rank 1 makes its random words
+    kPathCluster = 9  // paths 2 / 3 with every chain's CTA in one cluster; swap mailboxes in shared memory
 };
 
 struct LaunchPlan {
@@ -89,7 +91,8 @@ struct LaunchPlan {
 };
 
 // Sizes of the dynamic shared-memory carve-up of the sweep kernel for a path.
-size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass);
+// cluster_pre: path 9 with producer warps (its plan's n_consumer < threads)
+size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass, bool cluster_pre = false);
 
 // One request of a batched launch (device view). Every chain of the request is swept by
 // one CTA of the thread-block cluster that takes the request; the cluster's CTAs split the

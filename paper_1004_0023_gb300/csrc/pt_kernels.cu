@@ -61,9 +61,11 @@ struct GenericLayout {
 // the random words are produced ahead, two buffers of one sweep's words each.
 // With bits, the chain is P/8 bytes per site, the constant row holds +1 copies as zero bits,
 // and two 256-entry tables spread parity bits into +1/-1 bytes.
+// With cswap (path 9), each CTA also holds the swap mailboxes of the cluster's chains: four
+// passes of R (E, M) words each (see eos_decide_cluster).
 struct FastLayout {
-    size_t spins, ones, lut, desc, items, loff, thr, acc, red, ctl, rbuf, total;
-    __host__ __device__ FastLayout(const DevProblem& p, int dc, bool pre, bool bits = false) {
+    size_t spins, ones, lut, desc, items, loff, thr, acc, red, ctl, cmb, rbuf, total;
+    __host__ __device__ FastLayout(const DevProblem& p, int dc, bool pre, bool bits = false, bool cswap = false) {
         const int N = p.N, P = p.P;
         const size_t row = bits ? (size_t)P / 8 : (size_t)P;
         size_t o = 0;
@@ -77,6 +79,7 @@ struct FastLayout {
         acc = o;   o += acc_bytes(p);
         red = o;   o += 32 * 3 * 8;
         ctl = o;   o += 32;
+        cmb = o;   o += cswap ? (size_t)kClusterMailPasses * p.R * 16 : 0;
         rbuf = o;
         if (pre) o += (size_t)2 * (2 * N) * (P / 8) * 16;
         total = o;
@@ -85,8 +88,9 @@ struct FastLayout {
 
 size_t split_smem_bytes(const DevProblem& p, int dclass, bool pre);
 
-size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass) {
+size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass, bool cluster_pre) {
     if (path == kPathGeneric) return GenericLayout(p).total;
+    if (path == kPathCluster) return FastLayout(p, dclass, cluster_pre, false, true).total;
     if (path == kPathPeer) return FastLayout(p, dclass, true, false).total;
     if (path == kPathSplit || path == kPathSplitInline) return split_smem_bytes(p, dclass, path == kPathSplit);
     return FastLayout(p, dclass, path == kPathPacked, path == kPathBits).total;
@@ -141,18 +145,27 @@ __device__ SwapSide eos_publish(const DevProblem& p, int rung, long long& E, lon
     return w;
 }
 
+static_assert(kAccN == 0 && kAccE == 1 && kAccE2 == 2 && kAccM == 3 && kAccM2 == 4 && kAccFlip == 5 && kAccCount == 6,
+              "eos_stats pairs the counters in this order");
+
 // Thread 0: the statistics of the rung the chain sat on during the sweep (to `acc`, shared or
 // global), from the updated E and M.
 __device__ __forceinline__ void eos_stats(const DevProblem& p, unsigned long long* acc, int rung, long long E,
                                           long long M, long long nflip) {
     unsigned long long* a = acc + (size_t)rung * kAccCount;
     if (p.acc_in_smem) {
-        a[kAccN] += 1ull;
-        a[kAccE] += (unsigned long long)E;
-        a[kAccE2] += (unsigned long long)(E * E);
-        a[kAccM] += (unsigned long long)M;
-        a[kAccM2] += (unsigned long long)(M * M);
-        a[kAccFlip] += (unsigned long long)nflip;
+        // the rung's six counters (48 bytes, 16-byte aligned) in three paired loads and stores
+        ulonglong2* a2 = reinterpret_cast<ulonglong2*>(a);
+        ulonglong2 v0 = a2[0], v1 = a2[1], v2 = a2[2];
+        v0.x += 1ull;                                // kAccN
+        v0.y += (unsigned long long)E;               // kAccE
+        v1.x += (unsigned long long)(E * E);         // kAccE2
+        v1.y += (unsigned long long)M;               // kAccM
+        v2.x += (unsigned long long)(M * M);         // kAccM2
+        v2.y += (unsigned long long)nflip;           // kAccFlip
+        a2[0] = v0;
+        a2[1] = v1;
+        a2[2] = v2;
     } else {
         atomicAdd(a + kAccN, 1ull);
         atomicAdd(a + kAccE, (unsigned long long)E);
@@ -203,6 +216,51 @@ __device__ int eos_decide(const DevProblem& p, const SwapSide& w, int rung, long
                                            p.coef[rl], p.coef[(R - 1) + rl], (uint32_t)w.q, (uint32_t)rl, key,
                                            p.exact_swaps != 0);
     if (lower && count) {
+        atomicAdd(p.swap_stats + 2 * rl, 1ull);
+        if (acc_swap) atomicAdd(p.swap_stats + 2 * rl + 1, 1ull);
+    }
+    return acc_swap ? w.partner : rung;
+}
+
+// Path 9 (one cluster holds every chain): the same decision with the partner's (E, M) read
+// from this CTA's own copy of the cluster mailboxes. Every chain that publishes for a pass
+// writes its two tagged words into every CTA of the cluster, at [pass mod 4][rung], so the
+// wait polls local shared memory. Four slots suffice: the chain that would overwrite the
+// slot a waiting chain reads (the holder of that rung three passes later) must first finish
+// the pass two later, in which it waits for the reader's own publication again.
+__device__ int eos_decide_cluster(const DevProblem& p, const unsigned long long* s_cmb, const SwapSide& w, int rung,
+                                  long long E, long long M, long long timeout_ns, const PhiloxKey& key, int* abort) {
+    *abort = 0;
+    if (!w.active) return rung;
+    const int R = p.R;
+    const unsigned long long* mb = s_cmb + ((size_t)(w.pass & (kClusterMailPasses - 1)) * R + w.partner) * 2;
+    long long pE, pM;
+    const unsigned long long start = globaltimer_ns();
+    unsigned int nap = 0;
+    for (int polls = 0;; ++polls) {
+        const unsigned long long wa = ld_cluster_local_u64(mb);
+        const unsigned long long wb = ld_cluster_local_u64(mb + 1);
+        if ((wa & 0xFFFFFFull) == w.tag && (wb & 0xFFFFFFull) == w.tag) {
+            pE = (long long)wa >> 24;
+            pM = (long long)(int32_t)(uint32_t)(wb >> 32);
+            break;
+        }
+        if ((long long)(globaltimer_ns() - start) > timeout_ns) {
+            atomicCAS(p.status, 0, PT_ETIMEDOUT);
+            *abort = 1;
+            return rung;
+        }
+        if (polls >= 32) {
+            nap = nap ? min(2u * nap, 256u) : 16u;
+            __nanosleep(nap);
+        }
+    }
+    const int rl = w.rl;
+    const bool lower = (rung == rl);
+    const bool acc_swap = swap_accept_fast(lower ? E : pE, lower ? pE : E, lower ? M : pM, lower ? pM : M,
+                                           p.coef[rl], p.coef[(R - 1) + rl], (uint32_t)w.q, (uint32_t)rl, key,
+                                           p.exact_swaps != 0);
+    if (lower) {
         atomicAdd(p.swap_stats + 2 * rl, 1ull);
         if (acc_swap) atomicAdd(p.swap_stats + 2 * rl + 1, 1ull);
     }
@@ -416,13 +474,16 @@ __device__ __forceinline__ void produce_words(uint4* buf, uint32_t t, const uint
 // PEER (path 8): the CTA is rank 0 of a cluster of two, and rank 1 (peer_producer below)
 // writes the random words into this CTA's buffers through distributed shared memory; every
 // thread here sweeps, and the two CTAs meet at a cluster barrier once per sweep.
-template <int DC, bool PRE, bool BITS = false, bool SPEC = true, bool PEER = false>
+// CSWAP (path 9): the CTAs of all R chains form one cluster (slot = rank) and the swap
+// mailboxes live in every CTA's shared memory (eos_decide_cluster); the CTAs meet at a
+// cluster barrier only after the mailboxes are cleared and before they leave.
+template <int DC, bool PRE, bool BITS = false, bool SPEC = true, bool PEER = false, bool CSWAP = false>
 __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot, long long t0, long long q0,
                                                   int n_sweeps, int sweeps_per_swap, long long timeout_ns,
                                                   int n_consumer, unsigned char* smem) {
     const int N = p.N, P = p.P;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const FastLayout L(p, DC, PRE, BITS);
+    const FastLayout L(p, DC, PRE, BITS, CSWAP);
     int8_t* sp = reinterpret_cast<int8_t*>(smem + L.spins);
     uint8_t* bp = reinterpret_cast<uint8_t*>(smem + L.spins);
     uint32_t* s_lut = reinterpret_cast<uint32_t*>(smem + L.lut);
@@ -434,6 +495,7 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
     int* s_ctl = reinterpret_cast<int*>(smem + L.ctl);
     uint4* rbuf = reinterpret_cast<uint4*>(smem + L.rbuf);
     unsigned long long* s_acc = reinterpret_cast<unsigned long long*>(smem + L.acc);
+    unsigned long long* s_cmb = reinterpret_cast<unsigned long long*>(smem + L.cmb);
     const int NC = PRE ? n_consumer : nt;
     const bool consumer = tid < NC;
     const int DW = SiteDesc<DC>::DW;
@@ -493,7 +555,10 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
         int* s_sum = reinterpret_cast<int*>(s_red);
         s_sum[0] = s_sum[1] = s_sum[2] = 0;  // the sweep's dE, dM and flips
     }
+    if (CSWAP)
+        for (int x = tid; x < kClusterMailPasses * p.R * 2; x += nt) s_cmb[x] = 0ull;
     __syncthreads();
+    if (CSWAP) cluster_barrier();  // every CTA's mailboxes are clear before anyone publishes
     if (PRE && !PEER && !consumer)
         produce_words(rbuf, (uint32_t)t0, s_items, n_items, G, lg, gmask, tid - NC, nt - NC, (uint32_t)slot, key);
     if (PEER) {
@@ -581,8 +646,20 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
                     since_pass = 0;
                     pass = next_pass++;
                 }
-                side = eos_publish(p, rung, E, M, sE, sM, pass, q0, qmod0);
+                side = eos_publish(p, rung, E, M, sE, sM, pass, q0, qmod0, !CSWAP);
                 s_ctl[4] = side.active ? side.partner : -1;
+                if (CSWAP && side.active && rung != p.withhold_rung) {
+                    // the publication, into every CTA of the cluster (thread 0 alone: having
+                    // warp 0's lanes share the stores would make them wait for this thread,
+                    // which measured slower)
+                    const int idx = ((side.pass & (kClusterMailPasses - 1)) * p.R + rung) * 2;
+                    const unsigned long long wa = ((unsigned long long)E << 24) | side.tag;
+                    const unsigned long long wb = ((unsigned long long)(uint32_t)(int32_t)M << 32) | side.tag;
+                    for (int r = 0; r < p.R; ++r) {
+                        st_cluster_u64(s_cmb + idx, (unsigned)r, wa);
+                        st_cluster_u64(s_cmb + idx + 1, (unsigned)r, wb);
+                    }
+                }
             }
         } else if (PRE && !consumer && s + 1 < n_sweeps) {
             // producer warps only: a consumer whose swap wait gave up skips to the barrier below
@@ -606,7 +683,10 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
         } else {
             __syncthreads();
         }
-        if (s_ctl[5]) return;  // status holds PT_ETIMEDOUT
+        if (s_ctl[5]) {  // status holds PT_ETIMEDOUT
+            if (CSWAP) break;  // to the cluster barrier that every CTA passes before leaving
+            return;
+        }
         if (!consumer) continue;
 
         // level 0 of sweep s + 1 under both candidate rungs
@@ -637,7 +717,8 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
             // the partner's mailbox may still be on its way
             eos_stats(p, p.acc_in_smem ? s_acc : p.acc, rung, E, M, sweep_flips);
             int abort_flag = 0;
-            s_ctl[2 * (s & 1)] = eos_decide(p, side, rung, E, M, timeout_ns, key, &abort_flag);
+            s_ctl[2 * (s & 1)] = CSWAP ? eos_decide_cluster(p, s_cmb, side, rung, E, M, timeout_ns, key, &abort_flag)
+                                       : eos_decide(p, side, rung, E, M, timeout_ns, key, &abort_flag);
             if (abort_flag) s_ctl[5] = 1;  // a partner never arrived
         }
         if (PRE) named_barrier(1, NC); else __syncthreads();
@@ -660,6 +741,9 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
         if (PRE) named_barrier(1, NC); else __syncthreads();
     }
     __syncthreads();
+    // no CTA of a path-9 cluster leaves while another may still write its mailboxes (every
+    // wait is bounded, so every CTA gets here)
+    if (CSWAP) cluster_barrier();
     if (s_ctl[5]) return;  // the last sweep's wait gave up
     flush_acc(p, s_acc, tid, nt);
 
@@ -747,6 +831,24 @@ sweep_packed_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int 
     // the held level-0 units do not fit the 64 registers of a 1024-thread block
     sweep_packed_body<DC, PRE, BITS, (MAXT <= 512)>(p, blockIdx.x, t0, q0, n_sweeps, sweeps_per_swap, timeout_ns,
                                                     n_consumer, smem);
+}
+
+// Path 9: one cluster of R CTAs, CTA r sweeping chain r as paths 2 (PRE = false) and 3 do,
+// with the swap mailboxes in shared memory. The cluster shape is set at launch and checked
+// on entry: if the cluster is not the whole grid, every CTA returns before any cluster
+// barrier or remote access.
+template <int DC, bool PRE>
+__global__ void __launch_bounds__(384, 1)
+    sweep_cluster_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
+                         long long timeout_ns, int n_consumer) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    if (cluster.num_blocks() != (unsigned)p.R || gridDim.x != (unsigned)p.R) {
+        if (threadIdx.x == 0) atomicCAS(p.status, 0, PT_ECUDA);
+        return;
+    }
+    sweep_packed_body<DC, PRE, false, true, false, true>(p, (int)cluster.block_rank(), t0, q0, n_sweeps,
+                                                         sweeps_per_swap, timeout_ns, n_consumer, smem);
 }
 
 // Several problems in one cooperative launch (all chains resident at once): block b sweeps
@@ -1235,6 +1337,12 @@ static const void* sweep_fn(const LaunchPlan& plan) {
     }
     if (plan.path == kPathPeer)
         return plan.dclass == 4 ? (const void*)sweep_peer_kernel<4> : (const void*)sweep_peer_kernel<8>;
+    if (plan.path == kPathCluster) {
+        const bool pre = plan.n_consumer < plan.threads;
+        if (plan.dclass == 4)
+            return pre ? (const void*)sweep_cluster_kernel<4, true> : (const void*)sweep_cluster_kernel<4, false>;
+        return pre ? (const void*)sweep_cluster_kernel<8, true> : (const void*)sweep_cluster_kernel<8, false>;
+    }
     if (plan.path == kPathSplit)
         return plan.dclass == 4 ? (const void*)sweep_split_kernel<4, true> : (const void*)sweep_split_kernel<8, true>;
     if (plan.path == kPathSplitInline)
@@ -1268,6 +1376,11 @@ cudaError_t prepare_sweep_kernel(const LaunchPlan& plan) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
+    if (plan.path == kPathCluster) {
+        // clusters of up to 16 CTAs (above 8 is a non-portable size)
+        e = cudaFuncSetAttribute(sweep_fn(plan), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(sweep_fn(plan), cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
 }
 
@@ -1293,8 +1406,34 @@ static cudaLaunchConfig_t split_config(const DevProblem& p, const LaunchPlan& pl
     return cfg;
 }
 
+// Path 9's launch: one cluster of all R CTAs.
+static cudaLaunchConfig_t cluster_config(const DevProblem& p, const LaunchPlan& plan, cudaStream_t s,
+                                         cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p.R);
+    cfg.blockDim = dim3(plan.threads);
+    cfg.dynamicSmemBytes = plan.smem_bytes;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)p.R;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
 cudaError_t sweep_resident_chains(const DevProblem& p, const LaunchPlan& plan, long long* chains) {
     *chains = 0;
+    if (plan.path == kPathCluster) {
+        if (p.R > 16) return cudaSuccess;
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = cluster_config(p, plan, 0, attr);
+        int clusters = 0;
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, sweep_fn(plan), &cfg);
+        if (e == cudaSuccess) *chains = (long long)clusters * p.R;
+        return e;
+    }
     if (plan.path == kPathSplit || plan.path == kPathSplitInline || plan.path == kPathPeer) {
         cudaLaunchAttribute attr[2];
         cudaLaunchConfig_t cfg = split_config(p, plan, false, 0, attr);
@@ -1318,6 +1457,14 @@ cudaError_t launch_sweeps(const DevProblem& p, const LaunchPlan& plan, long long
     int n_consumer = plan.n_consumer;
     void* args[] = {&pp, &t0, &q0, &n_sweeps, &sweeps_per_swap, &timeout_ns, &n_consumer};
     const void* fn = sweep_fn(plan);
+    if (plan.path == kPathCluster) {
+        // one cluster holds every chain, so the swap passes never need a cooperative launch
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = cluster_config(p, plan, s, attr);
+        const cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
+        if (e != cudaSuccess) (void)cudaGetLastError();
+        return e;
+    }
     if (plan.path == kPathSplit || plan.path == kPathSplitInline || plan.path == kPathPeer) {
         cudaLaunchAttribute attr[2];
         cudaLaunchConfig_t cfg = split_config(p, plan, cooperative, s, attr);

@@ -38,7 +38,7 @@ def test_autotuned_context_starts_from_the_initial_state_and_matches_the_oracle(
     prob = _problem(98, 64, 22, 4242)
     g = pt.PT.from_problem(prob)
     assert g.info.tuned_plans >= 2
-    assert g.info.kernel_path in (2, 3, 5, 6, 7, 8)
+    assert g.info.kernel_path in (2, 3, 5, 6, 7, 8, 9)
     o = Oracle.from_problem(prob, threads=THREADS)
     _same(g, o)  # the timed sweeps were undone
     g.run(150, 1)
@@ -55,3 +55,16 @@ def test_autotuned_context_starts_from_the_initial_state_and_matches_the_oracle(
     assert f.info.tuned_plans == 0 and f.info.kernel_path == 3
     f.run(150, 1)
     assert np.array_equal(f.read_state(), g.read_state())
+
+
+def test_autotuned_short_ladder_may_take_the_one_cluster_plan():
+    # R = 12 <= 16: path 9 (every chain's CTA in one cluster) is among the candidates
+    prob = _problem(40, 32, 12, 4343)
+    g = pt.PT.from_problem(prob)
+    assert g.info.tuned_plans >= 2
+    assert g.info.kernel_path in (2, 3, 7, 8, 9)
+    o = Oracle.from_problem(prob, threads=THREADS)
+    _same(g, o)
+    g.run(200, 1)
+    o.run(200, 1)
+    _same(g, o)

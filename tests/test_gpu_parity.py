@@ -101,6 +101,33 @@ def test_medium_workload_full_length():
         assert_same(g, o, "sweep %d" % (100 * (chunk + 1)))
 
 
+@pytest.mark.parametrize("producers", [0, 32])
+def test_small_workload_on_path_9(producers):
+    """N=16, P=32, R=16 with all 16 chains' CTAs in one cluster and the swap mailboxes in
+    shared memory (random words inline, or from a producer warp): full length, checked every
+    1000 sweeps."""
+    prob = instances.workload("regular3_n16_p32_r16", 1)
+    g, o = both(prob, kernel_path=9, producer_threads=producers)
+    assert g.info.kernel_path == 9
+    for chunk in range(prob.n_sweeps // 1000):
+        g.run(1000, 1)
+        o.run(1000, 1)
+        assert_same(g, o, "sweep %d" % (1000 * (chunk + 1)))
+
+
+def test_path_9_needs_the_ladder_in_one_cluster():
+    prob = instances.workload("regular3_n256_p64_r64", 1)  # R = 64 > 16
+    with pytest.raises(pt.PTError) as e:
+        pt.PT.from_problem(prob, kernel_path=9)
+    assert e.value.code == pt.PT_EINVAL
+    small = instances.workload("regular3_n16_p32_r16", 1)
+    for kw in (dict(threads_per_block=32), dict(threads_per_block=512), dict(producer_threads=16),
+               dict(producer_threads=128)):
+        with pytest.raises(pt.PTError) as e:
+            pt.PT.from_problem(small, kernel_path=9, **kw)
+        assert e.value.code == pt.PT_EINVAL, kw
+
+
 def test_medium_workload_on_path_8():
     """N=256, P=64, R=64 with each chain's random words made by a second CTA of its cluster
     (path 8), 384 and 512 threads, checked every 200 sweeps."""
@@ -136,7 +163,10 @@ def test_layouts_and_swap_modes_give_identical_bits():
                dict(kernel_path=4), dict(kernel_path=4, threads_per_block=32), dict(kernel_path=4, swap_mode=2),
                dict(kernel_path=3, threads_per_block=64, producer_threads=32),
                dict(test_exact_swaps=1), dict(test_exact_swaps=1, swap_mode=2),
-               dict(kernel_path=8), dict(kernel_path=8, threads_per_block=384), dict(kernel_path=8, swap_mode=2)):
+               dict(kernel_path=8), dict(kernel_path=8, threads_per_block=384), dict(kernel_path=8, swap_mode=2),
+               dict(kernel_path=9), dict(kernel_path=9, threads_per_block=64),
+               dict(kernel_path=9, threads_per_block=256, producer_threads=64),
+               dict(kernel_path=9, producer_threads=32), dict(kernel_path=9, swap_mode=2)):
         g = pt.PT.from_problem(prob, **kw)
         g.run(300, 1)
         g.run(77, 5)
@@ -159,7 +189,7 @@ def test_medium_workload_each_kernel_path(path):
     assert_same(g, o, "path %d" % path)
 
 
-@pytest.mark.parametrize("path", [1, 2, 3, 4, 8])
+@pytest.mark.parametrize("path", [1, 2, 3, 4, 8, 9])
 @pytest.mark.parametrize("name", ["prism_p8_r3", "complete8_p16_r4"])
 def test_tiny_packed_problems_each_path(name, path):
     prob = TINY[name]
@@ -189,7 +219,7 @@ def test_lattice_workload_bit_packed():
     assert_same(g, o, "sweep %d" % prob.n_sweeps)
 
 
-@pytest.mark.parametrize("path", [2, 3, 4, 8])
+@pytest.mark.parametrize("path", [2, 3, 4, 8, 9])
 @pytest.mark.parametrize("P", [8, 24, 136])
 def test_packed_row_lengths(P, path):
     """Rows of 8, 24 and 136 copies (1, 3 and 17 bytes bit-packed): the periodic Trotter
@@ -347,13 +377,14 @@ def test_invalid_arguments_are_rejected():
     g.run(10, 1)  # still usable after argument errors
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 3, 4, 8])
+@pytest.mark.parametrize("path", [0, 1, 2, 3, 4, 8, 9])
 def test_partner_that_never_publishes_times_out_without_fault(path):
     """The chain on rung 3 withholds its mailbox: its partner's bounded wait runs out, the
     call reports PT_ETIMEDOUT, and the device stays usable for a new context. On every
     one-CTA kernel, with sweeps left after the one whose wait gave up: the CTA that gave up
     leaves at the next barrier without touching its random-word buffers; on path 8 its
-    random-word CTA learns at that same cluster barrier and leaves with it."""
+    random-word CTA learns at that same cluster barrier and leaves with it; on path 9 every
+    CTA of the cluster reaches the closing cluster barrier (each wait is bounded)."""
     prob = instances.workload("regular3_n16_p32_r16", 5)
     g = pt.PT.from_problem(prob, wait_timeout_ms=200, test_withhold_rung=3, swap_mode=1, kernel_path=path)
     g.run(4, 1)
