@@ -93,14 +93,14 @@ def kernel_source_hash(which: str) -> str:
 # kernel, from one ncu capture: (kernel, workload key) -> (source set, kernel_source_hash()
 # of the build captured, bytes). A figure whose hash no longer matches is reported as null.
 MEASURED_TRAFFIC: dict = {
-    # one 1000-sweep launch of the N=256, P=64, R=64 plan (path 8, 384 threads): 1.79 MB read, 0 written
+    # one 1000-sweep launch of the N=256, P=64, R=64 plan (path 8, 384 threads): 1.66 MB read, 0 written
     ("sweep_peer_kernel (int8, random words from a second CTA of each chain's cluster)", "regular3_n256_p64_r64_2000"):
-        ("sweep", "eee35048a51f7642", 1788928),
+        ("sweep", "e641c89e5fc05d66", 1658112),
     # one 500-sweep launch of the K4,4 lattice, bit-packed (path 4, 512 threads)
-    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("sweep", "eee35048a51f7642", 26765824 + 4352),
+    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("sweep", "e641c89e5fc05d66", 26862592 + 4096),
     # one graph-replayed launch of the 512-request mix, 1000 sweeps each (clusters of 2, one
-    # warp per chain): 1.287 TB read + 1.343 TB written, 1.85 B per attempt
-    ("batch_kernel", "batched_512x1000"): ("batch", "846e749a1a388b79", 1286753979392 + 1343174020352),
+    # warp per chain): 1.288 TB read + 1.343 TB written, 1.85 B per attempt
+    ("batch_kernel", "batched_512x1000"): ("batch", "43a0a750b3cb936d", 1287553507328 + 1343299756800),
 }
 
 
@@ -128,6 +128,8 @@ def parse_args(argv=None):
     ap.add_argument("--threads-per-block", type=int, default=0, help="force its block size (with --kernel-path)")
     ap.add_argument("--cluster-size", type=int, default=0, help="with --kernel-path 7: CTAs of the one cluster")
     ap.add_argument("--group-threads", type=int, default=0, help="with --kernel-path 7: threads per chain group")
+    ap.add_argument("--producer-threads", type=int, default=0,
+                    help="with --kernel-path 3, 5 or 9: random-word producer threads per CTA")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain-compare", action="store_true", help="skip the one-pt_run-per-request comparison")
@@ -441,7 +443,7 @@ def plain_headline(args, pt, instances, torch, n_sm, rank, world, local_rank, de
     rec = plain_record(args.workload, args, pt, instances, torch, n_sm, None, rank, world, device, prob=prob,
                        steps=args.steps, warmup=args.warmup, kernel_path=args.kernel_path,
                        threads_per_block=args.threads_per_block, clocks=True, cluster_size=args.cluster_size,
-                       group_threads=args.group_threads)
+                       group_threads=args.group_threads, producer_threads=args.producer_threads)
     out = {"metric": METRIC, "value": rec["value"], "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "int8/int32 (integer-exact)", "data": "synthetic",
@@ -453,7 +455,8 @@ def plain_headline(args, pt, instances, torch, n_sm, rank, world, local_rank, de
 
 
 def plain_record(name, args, pt, instances, torch, n_sm, sm_mhz, rank, world, device, prob=None, steps=None,
-                 warmup=2, kernel_path=0, threads_per_block=0, clocks=False, cluster_size=0, group_threads=0):
+                 warmup=2, kernel_path=0, threads_per_block=0, clocks=False, cluster_size=0, group_threads=0,
+                 producer_threads=0):
     """A single-problem workload on the device: the autotuned plan, L2 flushed between
     timed steps, value, roofline and a CPU-oracle baseline."""
     prob = prob or instances.workload(name, 1 + rank)
@@ -461,7 +464,7 @@ def plain_record(name, args, pt, instances, torch, n_sm, sm_mhz, rank, world, de
     stream = torch.cuda.Stream()
     ctx = pt.PT.from_problem(prob, stream=stream.cuda_stream, kernel_path=kernel_path,
                              threads_per_block=threads_per_block, cluster_size=cluster_size,
-                             group_threads=group_threads)
+                             group_threads=group_threads, producer_threads=producer_threads)
     info = ctx.info
     for _ in range(warmup):
         ctx.run(prob.n_sweeps, prob.sweeps_per_swap)
