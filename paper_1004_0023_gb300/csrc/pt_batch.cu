@@ -23,6 +23,8 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "pt.h"
@@ -465,6 +467,8 @@ struct pt_batch {
     int tuned;               // layouts timed by the autotuner (0 = layout given)
     cudaGraphExec_t exec;    // the captured run (memset of the work counter + persistent launch)
     int graph_failed;        // capture was not possible; runs launch directly
+    unsigned char* h_obs;    // pinned staging for pt_batch_read_observables: the device record,
+    size_t h_obs_bytes;      // then one request's (E, M, permutation, statistics) block
     int err;
     char msg[256];
 };
@@ -507,6 +511,7 @@ static int bfail(pt_batch* b, int code, const char* fmt, ...) {
 
 static void free_batch(pt_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->h_obs) cudaFreeHost(b->h_obs);
     for (void* p : b->allocs) cudaFree(p);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -828,13 +833,35 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) return bfail(nullptr, PT_ENODEV, "no CUDA device");
     std::vector<Prepared> pr(count);
     char why[200];
-    for (int k = 0; k < count; ++k) {
-        // levels balanced for one-warp chain groups (the default and the usual autotuned
-        // width): 32 threads over the power-of-two word columns of an item
-        int cols = 1;
-        while (cols < reqs[k].P / 8) cols <<= 1;
-        const int rc = prepare_request(reqs[k], pr[k], why, sizeof(why), reqs[k].P >= 8 ? std::max(1, 32 / cols) : 0);
-        if (rc) return bfail(nullptr, rc, "request %d: %s", k, why);
+    {
+        // Requests are prepared independently (checks, tables, level schedule, descriptors),
+        // on up to 16 host threads; the first failing request in index order is reported.
+        // Levels are balanced for one-warp chain groups (the default and the usual autotuned
+        // width): 32 threads over the power-of-two word columns of an item.
+        std::vector<int> rcs(count, PT_OK);
+        std::vector<std::string> whys(count);
+        auto work = [&](int first, int step) {
+            char w[200];
+            for (int k = first; k < count; k += step) {
+                int cols = 1;
+                while (cols < reqs[k].P / 8) cols <<= 1;
+                rcs[k] = prepare_request(reqs[k], pr[k], w, sizeof(w), reqs[k].P >= 8 ? std::max(1, 32 / cols) : 0);
+                if (rcs[k]) whys[k] = w;
+            }
+        };
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int n_threads = (int)std::min<unsigned>(std::min(hw, 16u), (unsigned)((count + 7) / 8));
+        if (n_threads <= 1) {
+            work(0, 1);
+        } else {
+            std::vector<std::thread> pool;
+            pool.reserve(n_threads - 1);
+            for (int t = 1; t < n_threads; ++t) pool.emplace_back(work, t, n_threads);
+            work(0, n_threads);
+            for (std::thread& th : pool) th.join();
+        }
+        for (int k = 0; k < count; ++k)
+            if (rcs[k]) return bfail(nullptr, rcs[k], "request %d: %s", k, whys[k].c_str());
     }
     if (opt && (opt->cluster_size < 0 || opt->cluster_size > 16))
         return bfail(nullptr, PT_EINVAL, "cluster_size must be 0 (autotune) or 1..16");
@@ -847,6 +874,8 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
     b->d_map = nullptr;
     b->exec = nullptr;
     b->graph_failed = 0;
+    b->h_obs = nullptr;
+    b->h_obs_bytes = 0;
     b->tuned = 0;
     b->widen = 0;
     b->err = 0;
@@ -933,6 +962,16 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
                      cudaGetErrorString(e));
     }
     b->arena = arena;
+    {
+        size_t most = 0;
+        for (int k = 0; k < count; ++k) most = std::max(most, pr[k].off_sw + (size_t)pr[k].R * 16 - pr[k].off_E);
+        b->h_obs_bytes = sizeof(BatchInstance) + most;
+        if ((e = cudaMallocHost(&b->h_obs, b->h_obs_bytes)) != cudaSuccess) {
+            b->h_obs = nullptr;
+            free_batch(b);
+            return bfail(nullptr, PT_ENOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
+        }
+    }
     std::vector<unsigned char> host_const(const_bytes, 0);
     std::vector<int2> map;
     for (int k = 0; k < count; ++k) {
@@ -1103,22 +1142,29 @@ extern "C" int pt_batch_read_observables(pt_batch* b, int32_t index, pt_observab
     if (index < 0 || index >= b->count || !o) return bfail(b, PT_EINVAL, "bad index or null observables");
     const BatchInstance& I = b->h_inst[index];
     const int R = I.R;
-    std::vector<long long> E(R), M(R);
-    std::vector<int32_t> slot_of(R);
-    std::vector<unsigned long long> acc((size_t)R * kAccCount), sw(2 * (size_t)R);
-    BatchInstance dev_rec;  // the device record: its counters also count replays of a caller's graph
+    // the device record (its counters also count replays of a caller's graph), then the
+    // request's state block from E to the swap counts (contiguous in the arena), in two copies
+    // into pinned staging
+    const unsigned char* blk = reinterpret_cast<const unsigned char*>(I.E);
+    const size_t blk_bytes =
+        (size_t)(reinterpret_cast<const unsigned char*>(I.swap_stats) - blk) + (size_t)R * 16;
+    unsigned char* h_blk = b->h_obs + sizeof(BatchInstance);
     cudaStream_t s = b->stream;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(&dev_rec, b->d_inst + index, sizeof(BatchInstance), cudaMemcpyDeviceToHost, s)) !=
+    if ((e = cudaMemcpyAsync(b->h_obs, b->d_inst + index, sizeof(BatchInstance), cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess ||
-        (e = cudaMemcpyAsync(E.data(), I.E, R * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(M.data(), I.M, R * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(slot_of.data(), I.slot_of_rung, R * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(acc.data(), I.acc, acc.size() * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(sw.data(), I.swap_stats, sw.size() * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        (e = cudaMemcpyAsync(h_blk, blk, blk_bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return bfail(b, PT_ECUDA, "%s", cudaGetErrorString(e));
     int rc = bcheck(b);
     if (rc) return rc;
+    BatchInstance dev_rec;
+    memcpy(&dev_rec, b->h_obs, sizeof(BatchInstance));
+    auto at = [&](const void* dev) { return h_blk + (reinterpret_cast<const unsigned char*>(dev) - blk); };
+    const long long* E = reinterpret_cast<const long long*>(at(I.E));
+    const long long* M = reinterpret_cast<const long long*>(at(I.M));
+    const int32_t* slot_of = reinterpret_cast<const int32_t*>(at(I.slot_of_rung));
+    const unsigned long long* acc = reinterpret_cast<const unsigned long long*>(at(I.acc));
+    const unsigned long long* sw = reinterpret_cast<const unsigned long long*>(at(I.swap_stats));
     o->t = dev_rec.t0;
     o->q = dev_rec.q0;
     for (int r = 0; r < R; ++r) {
