@@ -142,6 +142,19 @@ def test_batch_rejects_unsupported_requests():
     assert e.value.code == pt.PT_EINVAL
 
 
+def test_batch_reports_the_first_unsupported_request_in_order():
+    """Requests are prepared on several host threads; the error still names the first bad
+    request by index, whichever thread met it."""
+    rng = np.random.default_rng(2)
+    probs = instances.batch_problems(count=96, index=3, n_sweeps=2)
+    for k in (41, 77):
+        probs[k] = instances.make_problem("regular", rng, n=8, degree=3, P=6, R=2, n_sweeps=2)
+    with pytest.raises(pt.PTError) as e:
+        pt.Batch(probs)
+    assert e.value.code == pt.PT_EINVAL
+    assert "request 41:" in str(e.value)
+
+
 def _energy_and_trotter(prob, state):
     """E (summed over copies) and M of every rung of a rung-ordered state, recomputed."""
     s = state.astype(np.int64)  # [R, N, P]
