@@ -135,6 +135,8 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
     const PhiloxKeyShared skey{s_keys};  // update units and swap decisions: round keys in shared memory
     const int G = P >> 3;
     const uint32_t ginv = chunk_ginv(G);
+    const bool p16 = (P & 15) == 0;  // streamed chains move 16 copies per load and store
+    const uint32_t hinv = chunk_ginv(P >> 4);
     int lg = 0;
     while ((1 << lg) < G) ++lg;
     const int gmask = (1 << lg) - 1;
@@ -150,7 +152,12 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
         for (int lc = grp < ngroups ? grp : c_count; lc < c_count; lc += ngroups) {  // threads past the last group idle
             const int rho = c_begin + lc;
             int8_t* buf = reinterpret_cast<int8_t*>(s_chains + (size_t)(I.resident ? lc : grp) * L.chain_stride);
-            if (!I.resident) load_split(buf, I.spins + (size_t)rho * I.slot_stride, N, P, G, ginv, gtid, gsize);
+            if (!I.resident) {
+                if (p16)
+                    load_split16(buf, I.spins + (size_t)rho * I.slot_stride, N, P, P >> 4, hinv, gtid, gsize);
+                else
+                    load_split(buf, I.spins + (size_t)rho * I.slot_stride, N, P, G, ginv, gtid, gsize);
+            }
             const int rung = s_rung[rho];
             const uint32_t* thr_c;
             if (I.thr_resident) {
@@ -192,7 +199,12 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
                 red_g[gwarp * 3 + 1] = dM;
                 red_g[gwarp * 3 + 2] = nf;
             }
-            if (!I.resident) store_split(I.spins + (size_t)rho * I.slot_stride, buf, N, P, G, ginv, gtid, gsize);
+            if (!I.resident) {
+                if (p16)
+                    store_split16(I.spins + (size_t)rho * I.slot_stride, buf, N, P, P >> 4, hinv, gtid, gsize);
+                else
+                    store_split(I.spins + (size_t)rho * I.slot_stride, buf, N, P, G, ginv, gtid, gsize);
+            }
             group_sync(bar, gsize);
             if (gtid == 0) {
                 long long sE = 0, sM = 0, sF = 0;

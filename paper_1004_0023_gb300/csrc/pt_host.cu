@@ -836,8 +836,9 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
 
     // Plan autotuning. When the path and the block size are automatic and the chains are
     // int8 in shared memory, each candidate plan (producer-warp kernel, inline-word kernel
-    // with 256, 384 or 512 threads, split kernel) sweeps a short stretch of one continuous
-    // run, and the fastest is kept. Results do not depend on the plan; the context is then
+    // with 256, 384 or 512 threads, split kernels, peer-produced words, chains packed on one
+    // cluster, one cluster of one-chain CTAs) sweeps a short stretch of one continuous run,
+    // twice, and the fastest is kept. Results do not depend on the plan; the context is then
     // reset to its initial state. The choice is cached per problem shape for the process.
     // (also when the fixed plan cannot hold every chain at once: a candidate that can runs the
     // swap passes inside its launch; every candidate timed is one whose chains are all resident)
@@ -930,10 +931,15 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             cudaEventCreate(&ev[0]);
             cudaEventCreate(&ev[1]);
             cudaEventCreate(&ev[2]);
-            float best_ms = 1e30f;
             long long t = 0, q = 0;
             const int warm = 4, shortn = 4, longn = std::min(36, c->max_passes);
-            for (size_t k = 0; k < cands.size(); ++k) {
+            // two passes, the second in reverse order, keeping each candidate's faster time:
+            // a clock still rising at the start of the timing then favours no candidate
+            std::vector<float> cand_ms(cands.size(), 1e30f);
+            bool stop = false;
+            for (int pass = 0; pass < 2 && !stop; ++pass)
+            for (size_t i = 0; i < cands.size() && !stop; ++i) {
+                const size_t k = pass == 0 ? i : cands.size() - 1 - i;
                 LaunchPlan pl;
                 DevProblem pc;
                 std::vector<uint32_t> it_c;
@@ -976,19 +982,23 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                         free_ctx(c);
                         return create_fail(PT_ECUDA, "plan autotuning: %s", cudaGetErrorString(cudaGetLastError()));
                     }
-                    ++timed_plans;
+                    if (pass == 0) ++timed_plans;
+                    stop = true;
                     break;
                 }
                 float ms_short = 0.f, ms_long = 0.f;
                 cudaEventElapsedTime(&ms_short, ev[0], ev[1]);
                 cudaEventElapsedTime(&ms_long, ev[1], ev[2]);
                 const float ms = (ms_long - ms_short) / (float)(longn - shortn);
-                ++timed_plans;
-                if (ms < best_ms) {
-                    best_ms = ms;
+                if (pass == 0) ++timed_plans;
+                cand_ms[k] = std::min(cand_ms[k], ms);
+            }
+            float best_ms = 1e30f;
+            for (size_t k = 0; k < cands.size(); ++k)
+                if (cand_ms[k] < best_ms) {
+                    best_ms = cand_ms[k];
                     best = (int)k;
                 }
-            }
             for (cudaEvent_t x : ev) cudaEventDestroy(x);
         }
         if (best >= 0) {
