@@ -75,7 +75,7 @@ __device__ __forceinline__ void group_sync(int bar, int gsize) {
 }
 
 template <int DC>
-__device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* s_keys, cg::cluster_group& cluster,
+__device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint4* s_keys, cg::cluster_group& cluster,
                             int rank, int K) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const BatchLayout L(I, K, nt);
@@ -100,7 +100,8 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
     // ---- the problem's schedule, descriptors, round keys and rung permutation; this CTA's chains
     {
         if (tid < 10)
-            s_keys[tid] = make_uint2(I.key0 + (uint32_t)tid * 0x9E3779B9u, I.key1 + (uint32_t)tid * 0xBB67AE85u);
+            reinterpret_cast<uint2*>(s_keys)[tid] =
+                make_uint2(I.key0 + (uint32_t)tid * 0x9E3779B9u, I.key1 + (uint32_t)tid * 0xBB67AE85u);
         const int4* src = reinterpret_cast<const int4*>(I.sdesc);
         int4* dst = reinterpret_cast<int4*>(s_sdesc);
         for (int x = tid; x < N * L.DW / 4; x += nt) dst[x] = src[x];
@@ -279,7 +280,7 @@ __device__ void run_problem(const BatchInstance& I, unsigned char* smem, uint2* 
 __global__ void __launch_bounds__(512, 1) batch_kernel(BatchParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_job;
-    __shared__ uint2 s_keys[10];
+    __shared__ uint4 s_keys[5];  // round keys, two rounds per word
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int K = (int)cluster.num_blocks();

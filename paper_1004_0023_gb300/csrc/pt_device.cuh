@@ -21,12 +21,11 @@ struct PhiloxKey {
     __device__ __forceinline__ uint32_t b(int r) const { return k1[r]; }
 };
 
-// The same round keys read from shared memory ((k0, k1) of round r at k[r]), for kernels
-// that cannot spare 20 registers per thread for them.
+// The same round keys read from shared memory, for kernels that cannot spare 20 registers
+// per thread for them: rounds 2j and 2j+1 in one 16-byte word k[j] = (k0, k1, k0', k1'), so a
+// pair of rounds costs one shared load.
 struct PhiloxKeyShared {
-    const uint2* k;
-    __device__ __forceinline__ uint32_t a(int r) const { return k[r].x; }
-    __device__ __forceinline__ uint32_t b(int r) const { return k[r].y; }
+    const uint4* k;
 };
 
 __device__ __forceinline__ PhiloxKey philox_schedule(uint32_t key0, uint32_t key1) {
@@ -39,14 +38,24 @@ __device__ __forceinline__ PhiloxKey philox_schedule(uint32_t key0, uint32_t key
     return k;
 }
 
-template <typename Key>
-__device__ __forceinline__ uint4 philox(uint4 c, const Key& k) {
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t ka, uint32_t kb) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    return make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ ka, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ kb, (uint32_t)p0);
+}
+
+__device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKey& k) {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
-        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.a(r), (uint32_t)p1,
-                       (uint32_t)(p0 >> 32) ^ c.w ^ k.b(r), (uint32_t)p0);
+    for (int r = 0; r < 10; ++r) c = philox_round(c, k.a(r), k.b(r));
+    return c;
+}
+
+__device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKeyShared& k) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const uint4 kk = k.k[j];
+        c = philox_round(c, kk.x, kk.y);
+        c = philox_round(c, kk.z, kk.w);
     }
     return c;
 }
