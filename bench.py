@@ -93,14 +93,14 @@ def kernel_source_hash(which: str) -> str:
 # kernel, from one ncu capture: (kernel, workload key) -> (source set, kernel_source_hash()
 # of the build captured, bytes). A figure whose hash no longer matches is reported as null.
 MEASURED_TRAFFIC: dict = {
-    # one 1000-sweep launch of the N=256, P=64, R=64 plan (path 8, 384 threads): 1.66 MB read, 0 written
+    # one 1000-sweep launch of the N=256, P=64, R=64 plan (path 8, 384 threads): 1.67 MB read, 0 written
     ("sweep_peer_kernel (int8, random words from a second CTA of each chain's cluster)", "regular3_n256_p64_r64_2000"):
-        ("sweep", "e641c89e5fc05d66", 1658112),
+        ("sweep", "7c72ef1e9c313d0a", 1673216),
     # one 500-sweep launch of the K4,4 lattice, bit-packed (path 4, 512 threads)
-    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("sweep", "e641c89e5fc05d66", 26862592 + 4096),
+    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("sweep", "7c72ef1e9c313d0a", 26619904 + 3840),
     # one graph-replayed launch of the 512-request mix, 1000 sweeps each (clusters of 2, one
-    # warp per chain): 1.288 TB read + 1.343 TB written, 1.85 B per attempt
-    ("batch_kernel", "batched_512x1000"): ("batch", "43a0a750b3cb936d", 1287553507328 + 1343299756800),
+    # warp per chain): 1.286 TB read + 1.342 TB written, 1.85 B per attempt
+    ("batch_kernel", "batched_512x1000"): ("batch", "8b468e631fd4413b", 1285585459456 + 1342376079872),
 }
 
 
