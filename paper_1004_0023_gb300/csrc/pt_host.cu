@@ -232,6 +232,21 @@ void ptq::level_schedule(int N, const std::vector<std::vector<int>>& adj, std::v
     }
 }
 
+// A classical chain (P = 1) has no odd-parity copy: its updates (i, 1) change nothing, so
+// they are dropped with the levels they leave empty. Each remaining level is a subset of a
+// valid one, in the same order, so the result is the same; the sweep has fewer levels.
+static void drop_odd_updates(std::vector<uint32_t>& items, std::vector<int32_t>& level_off) {
+    std::vector<uint32_t> it;
+    std::vector<int32_t> off(1, 0);
+    for (size_t l = 0; l + 1 < level_off.size(); ++l) {
+        for (int x = level_off[l]; x < level_off[l + 1]; ++x)
+            if (!(items[x] & 1u)) it.push_back(items[x]);
+        if ((int32_t)it.size() > off.back()) off.push_back((int32_t)it.size());
+    }
+    items.swap(it);
+    level_off.swap(off);
+}
+
 // ---------------------------------------------------------------------------------
 // Packed-path site descriptors (see SiteDesc in pt_kernels.cu).
 // P = bytes per chain row: the copy count for int8 chains, copies / 8 for bit-packed ones.
@@ -488,6 +503,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     std::vector<uint32_t> items;
     std::vector<int32_t> level_off;
     level_schedule(N, adj, items, level_off);
+    if (P == 1) drop_odd_updates(items, level_off);
 
     DevProblem& p = c->dp;
     memset(&p, 0, sizeof(p));
@@ -648,7 +664,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         // enough threads for the average level (units = items * padded groups per parity)
         int G = ((P / 2) + 3) / 4, Gp = 1;
         while (Gp < G) Gp <<= 1;
-        const long long units = 2ll * N * Gp;
+        const long long units = (long long)items.size() * Gp;
         long long avg = (units + p.n_levels - 1) / p.n_levels;
         avg = ((avg + 31) / 32) * 32;
         c->plan.threads = (int)std::min<long long>(512, std::max<long long>(128, avg));
@@ -687,6 +703,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             while (cols < G) cols <<= 1;
         }
         level_schedule(N, adj, items, level_off, std::max(1, c->plan.n_consumer / cols));
+        if (P == 1) drop_odd_updates(items, level_off);
+        p.n_levels = (int)level_off.size() - 1;
     }
 
     // packed-path site descriptors: row offset i*P, i, packed J bytes (two words), then the
@@ -724,7 +742,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     DevCarve carve;
     carve.add(&d_nbr, nbr.size());
     carve.add(&d_h, (size_t)N);
-    carve.add(&d_items, items.size());
+    carve.add(&d_items, 2 * (size_t)N);  // room for both parities' updates (P = 1 uses half)
     carve.add(&d_loff, level_off.size());
     carve.add(&d_thr, c->thr.size());
     carve.add(&d_desc, desc.size());
