@@ -481,7 +481,8 @@ struct pt_batch {
     cudaGraphExec_t exec;    // the captured run (memset of the work counter + persistent launch)
     int graph_failed;        // capture was not possible; runs launch directly
     unsigned char* h_obs;    // pinned staging for pt_batch_read_observables: the device record,
-    size_t h_obs_bytes;      // then one request's (E, M, permutation, statistics) block
+    size_t h_obs_bytes;      // then one request's (E, M, permutation, statistics) block; the
+                             // status word follows at h_obs + h_obs_bytes
     int err;
     char msg[256];
 };
@@ -978,8 +979,8 @@ extern "C" int pt_batch_create(const pt_request* reqs, int32_t count, const pt_o
     {
         size_t most = 0;
         for (int k = 0; k < count; ++k) most = std::max(most, pr[k].off_sw + (size_t)pr[k].R * 16 - pr[k].off_E);
-        b->h_obs_bytes = sizeof(BatchInstance) + most;
-        if ((e = cudaMallocHost(&b->h_obs, b->h_obs_bytes)) != cudaSuccess) {
+        b->h_obs_bytes = (sizeof(BatchInstance) + most + 15) & ~(size_t)15;
+        if ((e = cudaMallocHost(&b->h_obs, b->h_obs_bytes + 16)) != cudaSuccess) {  // + the status word
             b->h_obs = nullptr;
             free_batch(b);
             return bfail(nullptr, PT_ENOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
@@ -1064,11 +1065,15 @@ static int bguard(pt_batch* b) {
 }
 
 static int bcheck(pt_batch* b) {
-    int st = 0;
-    cudaError_t e = cudaMemcpyAsync(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    // the status word through the pinned staging once it exists (a copy into pageable memory
+    // is staged by the driver and costs more than the synchronisation itself)
+    int local = 0;
+    int* st = b->h_obs ? reinterpret_cast<int*>(b->h_obs + b->h_obs_bytes) : &local;
+    *st = 0;
+    cudaError_t e = cudaMemcpyAsync(st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, PT_ECUDA, "CUDA error: %s", cudaGetErrorString(e));
-    if (st) return bfail(b, PT_ECUDA, "device status %d", st);
+    if (*st) return bfail(b, PT_ECUDA, "device status %d", *st);
     return PT_OK;
 }
 
