@@ -70,7 +70,8 @@ KERNEL_NAMES = {1: "sweep_kernel (byte-wise)", 2: "sweep_packed_kernel (int8, in
                 6: "sweep_split_kernel (int8, inline Philox, each chain on a 2-CTA cluster)",
                 7: "batch_kernel (all chains of the problem packed on one cluster, swaps in shared memory)",
                 8: "sweep_peer_kernel (int8, random words from a second CTA of each chain's cluster)",
-                9: "sweep_cluster_kernel (int8, every chain's CTA in one cluster, swap mailboxes in shared memory)"}
+                9: "sweep_cluster_kernel (int8, every chain's CTA in one cluster, swap mailboxes in shared memory)",
+                10: "sweep_classical_kernel (P = 1, chains packed several to a CTA on one cluster)"}
 
 
 # The sources each kernel is compiled from (its own file and the headers it includes).

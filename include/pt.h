@@ -99,13 +99,18 @@ typedef struct {
                                    CTAs of all R chains in one thread-block cluster and the
                                    swap mailboxes in every CTA's shared memory, so that a
                                    chain waits for its partner on its own SM (needs what
-                                   paths 2-6 need, R <= 16 and threads_per_block <= 384) */
+                                   paths 2-6 need, R <= 16 and threads_per_block <= 384),
+                                   10 = classical chains (P = 1) packed several to a CTA,
+                                   chain fastest in shared memory, on one thread-block cluster
+                                   of about cluster_size CTAs (0 = 16 chains a CTA; at most 16
+                                   CTAs) with the swap mailboxes in every CTA's shared memory */
     int32_t producer_threads;   /* paths 3 and 5: threads producing random words (0 = auto);
                                    path 9: 0 = random words inline, else this many producer
                                    threads (a multiple of 32 below threads_per_block) */
     int32_t test_exact_swaps;   /* test hook: 1 = skip the FP32 pre-decision of swaps and always
                                    evaluate the FP64 rule (results are identical either way) */
-    int32_t cluster_size;       /* batched launches: CTAs per thread-block cluster (1..16), or
+    int32_t cluster_size;       /* path 10: CTAs of its cluster (see kernel_path);
+                                   batched launches: CTAs per thread-block cluster (1..16), or
                                    0 = autotune (pt_batch_create times a short run of each
                                    layout and keeps the fastest, remembered per batch shape --
                                    every request's N, P, R, degree class, levels and sweeps --
@@ -113,7 +118,8 @@ typedef struct {
     int32_t no_autotune;        /* 0: when kernel_path and threads_per_block are automatic and
                                    the chains are int8 in shared memory, pt_create times a
                                    short run of each candidate plan (paths 2, 3, 5, 6, 7, 8 and
-                                   9, block sizes 128-512, clusters of 1-16 CTAs), keeps the fastest
+                                   9, block sizes 128-512, clusters of 1-16 CTAs; for P = 1,
+                                   paths 1 and 10), keeps the fastest
                                    and resets the context to its initial state; the choice is
                                    remembered per shape for the process. Results never depend
                                    on it. 1: off. */

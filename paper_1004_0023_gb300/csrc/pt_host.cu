@@ -527,9 +527,18 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     const int packed_dc = (dmax + 1 <= 4) ? 4 : ((dmax + 1 <= 8) ? 8 : 0);
     const bool packed_ok = (P % 8 == 0) && packed_dc > 0;
     const int want_path = opt ? opt->kernel_path : 0;
-    if (want_path < 0 || want_path > 9) {
+    if (want_path < 0 || want_path > 10) {
         free_ctx(c);
-        return create_fail(PT_EINVAL, "kernel_path must be 0..9");
+        return create_fail(PT_EINVAL, "kernel_path must be 0..10");
+    }
+    if (want_path == kPathClassical &&
+        (P != 1 || opt->cluster_size < 0 || opt->cluster_size > 16 ||
+         (opt->threads_per_block != 0 &&
+          (opt->threads_per_block < 32 || opt->threads_per_block > 512 || opt->threads_per_block % 32)))) {
+        free_ctx(c);
+        return create_fail(PT_EINVAL,
+                           "kernel_path 10 needs P = 1, cluster_size 0..16 and threads_per_block 0 or a multiple "
+                           "of 32 up to 512");
     }
     if ((want_path == kPathPacked || want_path == kPathPackedInline || want_path == kPathBits ||
          want_path == kPathSplit || want_path == kPathSplitInline || want_path == kPathPackedChains ||
@@ -568,6 +577,21 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     }
     int path = want_chains ? kPathPackedInline : want_path;
     const int want_threads = opt ? opt->threads_per_block : 0;
+    // path 10's shape for a cluster of about K CTAs: C = the power of two at or above R / K
+    // chains per CTA, ceil(R / C) CTAs; and its block: a multiple of 32 and of C holding one
+    // update of every chain of the CTA for the average level, at most 512 threads
+    auto classical_chains = [&](int K) {
+        int C = 1;
+        while ((long long)C * K < R) C <<= 1;
+        return C;
+    };
+    auto classical_threads = [&](int C) {
+        const int unit = std::max(32, C);
+        const long long per_level = ((long long)items.size() + p.n_levels - 1) / p.n_levels;
+        long long t = (per_level * C + unit - 1) / unit * unit;
+        t = std::max<long long>(t, std::max(64, unit));
+        return (int)std::min<long long>(t, 512 / unit * unit);
+    };
     // a layout fits if it does with the threshold rows and / or the statistics moved out
     auto fits = [&](int pth) {
         DevProblem q = p;
@@ -637,12 +661,26 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         }
     }
     c->plan.path = path;
-    c->plan.dclass = (path == kPathGeneric) ? dclass : packed_dc;
+    c->plan.dclass = (path == kPathGeneric || path == kPathClassical) ? dclass : packed_dc;
+    if (path == kPathClassical) {
+        // every rung's row and this launch's statistics live in each CTA's shared memory
+        const int C = classical_chains(opt->cluster_size > 0 ? opt->cluster_size : std::max(1, (R + 15) / 16));
+        c->plan.chains_per_cta = C;
+        c->plan.cluster = (R + C - 1) / C;
+        p.acc_in_smem = 1;
+        p.tables_in_smem = 1;
+        if (C > 512 || c->plan.cluster > 16 || (want_threads > 0 && want_threads % C)) {
+            free_ctx(c);
+            return create_fail(PT_EINVAL, "kernel_path 10: %d chains per CTA on %d CTAs does not fit (threads %d)", C,
+                               c->plan.cluster, want_threads);
+        }
+    }
     const bool cl_pre = path == kPathCluster && opt->producer_threads > 0;
     if (p.tables_in_smem && sweep_smem_bytes(p, path, c->plan.dclass, cl_pre) > (size_t)max_smem)
         p.tables_in_smem = 0;
     if (p.acc_in_smem && sweep_smem_bytes(p, path, c->plan.dclass, cl_pre) > (size_t)max_smem) p.acc_in_smem = 0;
-    c->plan.smem_bytes = sweep_smem_bytes(p, path, c->plan.dclass, cl_pre);
+    c->plan.smem_bytes = path == kPathClassical ? classical_smem_bytes(p, c->plan.chains_per_cta)
+                                                : sweep_smem_bytes(p, path, c->plan.dclass, cl_pre);
     if ((long long)c->plan.smem_bytes > (long long)max_smem) {
         free_ctx(c);
         return create_fail(PT_EINVAL, "one chain needs %zu bytes of shared memory; the device allows %d",
@@ -660,6 +698,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         c->plan.threads = 512;
     } else if (path == kPathCluster) {
         c->plan.threads = 128;
+    } else if (path == kPathClassical) {
+        c->plan.threads = classical_threads(c->plan.chains_per_cta);
     } else {
         // enough threads for the average level (units = items * padded groups per parity)
         int G = ((P / 2) + 3) / 4, Gp = 1;
@@ -702,9 +742,19 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             const int G = (path == kPathGeneric) ? ((P / 2) + 3) / 4 : P / 8;
             while (cols < G) cols <<= 1;
         }
-        level_schedule(N, adj, items, level_off, std::max(1, c->plan.n_consumer / cols));
+        const int per_round = path == kPathClassical ? c->plan.threads / c->plan.chains_per_cta
+                                                     : c->plan.n_consumer / cols;
+        level_schedule(N, adj, items, level_off, std::max(1, per_round));
         if (P == 1) drop_odd_updates(items, level_off);
         p.n_levels = (int)level_off.size() - 1;
+        // the level offsets live in shared memory: size it for this schedule's level count
+        c->plan.smem_bytes = path == kPathClassical ? classical_smem_bytes(p, c->plan.chains_per_cta)
+                                                    : sweep_smem_bytes(p, path, c->plan.dclass, cl_pre);
+        if ((long long)c->plan.smem_bytes > (long long)max_smem) {
+            free_ctx(c);
+            return create_fail(PT_EINVAL, "one chain needs %zu bytes of shared memory; the device allows %d",
+                               c->plan.smem_bytes, max_smem);
+        }
     }
 
     // packed-path site descriptors: row offset i*P, i, packed J bytes (two words), then the
@@ -814,7 +864,8 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         return create_fail(PT_EINVAL, "swap_mode 1 needs all %d chains resident at once (%lld fit on %d SMs)", R,
                            resident, n_sm);
     }
-    if ((path == kPathSplit || path == kPathSplitInline || path == kPathPeer || path == kPathCluster) &&
+    if ((path == kPathSplit || path == kPathSplitInline || path == kPathPeer || path == kPathCluster ||
+         path == kPathClassical) &&
         resident < R) {
         // the two CTAs of a chain always run together, but the swap passes need every chain
         free_ctx(c);
@@ -862,11 +913,12 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     // swap passes inside its launch; every candidate timed is one whose chains are all resident)
     const bool tune = want_path == 0 && want_threads == 0 && !(opt && opt->no_autotune) && coop_ok && mode != 2 &&
                       R > 1 && p.withhold_rung < 0 && !p.exact_swaps &&
-                      (path == kPathPacked || path == kPathPackedInline || path == kPathSplit);
+                      (path == kPathPacked || path == kPathPackedInline || path == kPathSplit ||
+                       (path == kPathGeneric && P == 1));
     if (tune) {
         struct Cand {
             int path, threads, producers;
-            int cluster = 1, group_threads = 0;  // path 7
+            int cluster = 1, group_threads = 0;  // path 7; path 10: CTAs and chains per CTA
         };
         const PlanKey key{N, P, R, packed_dc, p.n_levels, nE};
         std::vector<Cand> cands;
@@ -878,7 +930,18 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                                  it->second.group_threads});
         }
         const bool cached = !cands.empty();
-        if (!cached) {
+        if (!cached && P == 1) {
+            // classical chains: one chain a CTA (byte-wise kernel), or several chains a CTA on
+            // one cluster (path 10) for clusters of about 1 to 16 CTAs
+            cands.push_back({kPathGeneric, 128, 0});
+            cands.push_back({kPathGeneric, 64, 0});
+            for (int K : {1, 2, 4, 8, 16}) {
+                const int C = classical_chains(K), ctas = (R + C - 1) / C;
+                bool dup = C > 512 || ctas > 16;
+                for (const Cand& cd : cands) dup = dup || (cd.path == kPathClassical && cd.group_threads == C);
+                if (!dup) cands.push_back({kPathClassical, classical_threads(C), 0, ctas, C});
+            }
+        } else if (!cached) {
             if (fits(kPathPacked)) cands.push_back({kPathPacked, 512, 128});
             if (split_fits()) cands.push_back({kPathSplit, 512, 128});
             if (split_fits(kPathSplitInline))
@@ -911,11 +974,27 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         auto make = [&](const Cand& cd, LaunchPlan& pl, DevProblem& pc, std::vector<uint32_t>& it_c,
                         std::vector<int32_t>& off_c) {
             pc = p;
+            if (cd.path == kPathClassical) {
+                pc.acc_in_smem = 1;
+                pc.tables_in_smem = 1;
+                pl.path = kPathClassical;
+                pl.dclass = dclass;
+                pl.threads = cd.threads;
+                pl.n_consumer = cd.threads;
+                pl.chains_per_cta = cd.group_threads;
+                pl.cluster = cd.cluster;
+                level_schedule(N, adj, it_c, off_c, std::max(1, cd.threads / cd.group_threads));
+                drop_odd_updates(it_c, off_c);
+                pc.n_levels = (int)off_c.size() - 1;
+                pl.smem_bytes = classical_smem_bytes(pc, cd.group_threads);  // sized for this schedule
+                return pl.smem_bytes <= (size_t)max_smem;
+            }
             if (cd.path == kPathPackedChains) {
                 if (!chains_plan(pc, packed_dc, cd.cluster, kGroupWidenDefault, pl, cd.group_threads)) return false;
                 int cols = 1;
                 while (cols < P / 8) cols <<= 1;
                 level_schedule(N, adj, it_c, off_c, std::max(1, pl.group_threads / cols));
+                pc.n_levels = (int)off_c.size() - 1;
                 return true;
             }
             pc.acc_in_smem = (size_t)R * kAccCount * 8 <= 16384 ? 1 : 0;
@@ -925,7 +1004,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                 pc.tables_in_smem = 0;
             if (pc.acc_in_smem && sweep_smem_bytes(pc, cd.path, packed_dc, cpre) > (size_t)max_smem) pc.acc_in_smem = 0;
             pl.path = cd.path;
-            pl.dclass = packed_dc;
+            pl.dclass = cd.path == kPathGeneric ? dclass : packed_dc;
             pl.threads = cd.threads;
             pl.n_consumer = cd.threads - cd.producers;
             pl.smem_bytes = sweep_smem_bytes(pc, cd.path, packed_dc, cpre);
@@ -936,6 +1015,9 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                 while (cols < P / 8) cols <<= 1;
             }
             level_schedule(N, adj, it_c, off_c, std::max(1, pl.n_consumer / cols));
+            if (P == 1) drop_odd_updates(it_c, off_c);
+            pc.n_levels = (int)off_c.size() - 1;
+            pl.smem_bytes = sweep_smem_bytes(pc, cd.path, pl.dclass, cpre);  // sized for this schedule
             return pl.smem_bytes <= (size_t)max_smem;
         };
         cudaStream_t s = c->stream;
@@ -1022,11 +1104,17 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         if (best >= 0) {
             LaunchPlan pl;
             DevProblem pc;
-            if (make(cands[best], pl, pc, items, level_off)) {
+            std::vector<uint32_t> it_b;
+            std::vector<int32_t> off_b;
+            if (make(cands[best], pl, pc, it_b, off_b)) {
                 long long res = 0;
                 if (pl.path == kPathPackedChains ||
                     (prepare_sweep_kernel(pl) == cudaSuccess && sweep_resident_chains(pc, pl, &res) == cudaSuccess &&
                      res >= R)) {
+                    // the plan with the schedule its shared memory was sized for
+                    items.swap(it_b);
+                    level_off.swap(off_b);
+                    p.n_levels = pc.n_levels;
                     c->plan = pl;
                     c->cooperative = true;  // resident (checked above), cooperative launch available
                     p.acc_in_smem = pc.acc_in_smem;

@@ -76,7 +76,8 @@ enum {
     kPathSplitInline = 6,
     kPathPackedChains = 7,
     kPathPeer = 8,  // path 3's sweep on every thread of rank 0 of a two-CTA cluster; rank 1 makes its random words
-    kPathCluster = 9  // paths 2 / 3 with every chain's CTA in one cluster; swap mailboxes in shared memory
+    kPathCluster = 9,   // paths 2 / 3 with every chain's CTA in one cluster; swap mailboxes in shared memory
+    kPathClassical = 10  // P = 1: chains packed several to a CTA, one cluster, swap mailboxes in shared memory
 };
 
 struct LaunchPlan {
@@ -88,11 +89,14 @@ struct LaunchPlan {
     int cluster = 1;     // path 7: CTAs in the one cluster
     int group_threads = 0;  // path 7: threads sweeping one chain
     int thr_resident = 0;   // path 7: every rung's threshold row in shared memory
+    int chains_per_cta = 1; // path 10: chains packed on one CTA (cluster = ceil(R / chains_per_cta))
 };
 
 // Sizes of the dynamic shared-memory carve-up of the sweep kernel for a path.
 // cluster_pre: path 9 with producer warps (its plan's n_consumer < threads)
 size_t sweep_smem_bytes(const DevProblem& p, int path, int dclass, bool cluster_pre = false);
+// path 10: the shared memory of a CTA holding `chains` classical chains
+size_t classical_smem_bytes(const DevProblem& p, int chains);
 
 // One request of a batched launch (device view). Every chain of the request is swept by
 // one CTA of the thread-block cluster that takes the request; the cluster's CTAs split the

@@ -445,6 +445,203 @@ sweep_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_
     }
 }
 
+// ------------------------------------------------------------------------- classical sweep
+// Path 10 (P = 1, classical tempering): the R chains packed C to a CTA (C a power of two),
+// chain fastest in shared memory (site i of chain c at byte i C + c), on one cluster of
+// K = ceil(R / C) CTAs. A level's updates are (site, chain) pairs, chain fastest, and every
+// thread keeps one chain (blockDim is a multiple of C), so a warp reads one site's neighbour
+// list for up to 32 chains and their bytes side by side, and the thread's threshold row is
+// its chain's. After a sweep thread c of the CTA ends chain c's sweep: statistics, then the
+// swap publication into every CTA of the cluster and the partner's wait in its own shared
+// memory, as path 9 does (eos_decide_cluster). The update, its counter and its table entry
+// are the byte-wise kernel's for P = 1.
+struct ClassicalLayout {
+    size_t spins, nbr, h, items, loff, thr, acc, cmb, E, M, rung, sums, ctl, total;
+    __host__ __device__ ClassicalLayout(const DevProblem& p, int C) {
+        size_t o = 0;
+        spins = o; o += up16((size_t)p.N * C);
+        nbr = o;   o += up16((size_t)p.N * p.dmax * 4);
+        h = o;     o += up16((size_t)p.N);
+        items = o; o += up16((size_t)2 * p.N * 4);
+        loff = o;  o += up16((size_t)(p.n_levels + 1) * 4);
+        thr = o;   o += up16((size_t)p.R * p.nL3 * 4);  // every rung's row
+        acc = o;   o += (size_t)p.R * kAccCount * 8;      // this launch's statistics, by rung
+        cmb = o;   o += (size_t)kClusterMailPasses * p.R * 16;
+        E = o;     o += up16((size_t)C * 8);
+        M = o;     o += up16((size_t)C * 8);
+        rung = o;  o += up16((size_t)C * 4);
+        sums = o;  o += up16((size_t)C * 8);               // per chain: dE and flips of the sweep
+        ctl = o;   o += 16;
+        total = o;
+    }
+};
+
+size_t classical_smem_bytes(const DevProblem& p, int chains) { return ClassicalLayout(p, chains).total; }
+
+template <int DCLASS>
+__global__ void __launch_bounds__(512, 1)
+    sweep_classical_kernel(DevProblem p, long long t0, long long q0, int n_sweeps, int sweeps_per_swap,
+                           long long timeout_ns, int C) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int K = (p.R + C - 1) / C;
+    if (cluster.num_blocks() != (unsigned)K || gridDim.x != (unsigned)K || p.P != 1 || C < 1 || (C & (C - 1)) ||
+        (blockDim.x % (unsigned)C) || (blockDim.x & 31u)) {
+        if (threadIdx.x == 0) atomicCAS(p.status, 0, PT_ECUDA);
+        return;  // every CTA returns here, before any cluster barrier
+    }
+    const int N = p.N, R = p.R;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const int rank = (int)cluster.block_rank();
+    const int c0 = rank * C, nc = min(C, R - c0);  // this CTA's chains: slots c0 .. c0 + nc - 1
+    const ClassicalLayout L(p, C);
+    int8_t* sp = reinterpret_cast<int8_t*>(smem + L.spins);
+    uint32_t* s_nbr = reinterpret_cast<uint32_t*>(smem + L.nbr);
+    int8_t* s_h = reinterpret_cast<int8_t*>(smem + L.h);
+    uint32_t* s_items = reinterpret_cast<uint32_t*>(smem + L.items);
+    int32_t* s_loff = reinterpret_cast<int32_t*>(smem + L.loff);
+    uint32_t* s_thr = reinterpret_cast<uint32_t*>(smem + L.thr);
+    unsigned long long* s_acc = reinterpret_cast<unsigned long long*>(smem + L.acc);
+    unsigned long long* s_cmb = reinterpret_cast<unsigned long long*>(smem + L.cmb);
+    long long* s_E = reinterpret_cast<long long*>(smem + L.E);
+    long long* s_M = reinterpret_cast<long long*>(smem + L.M);
+    int* s_rung = reinterpret_cast<int*>(smem + L.rung);
+    int* s_sums = reinterpret_cast<int*>(smem + L.sums);  // [c][0] = dE, [c][1] = flips
+    int* s_ctl = reinterpret_cast<int*>(smem + L.ctl);
+
+    for (int x = tid; x < N * C; x += nt) {
+        const int i = x / C, c = x - i * C;
+        sp[x] = c < nc ? p.spins[(size_t)(c0 + c) * p.slot_stride + i] : (int8_t)1;
+    }
+    for (int x = tid; x < N * DCLASS; x += nt) s_nbr[x] = p.nbr[x];
+    for (int x = tid; x < N; x += nt) s_h[x] = p.h[x];
+    for (int x = tid; x < 2 * N; x += nt) s_items[x] = p.items[x];
+    for (int x = tid; x <= p.n_levels; x += nt) s_loff[x] = p.level_off[x];
+    for (int x = tid; x < R * p.nL3; x += nt) s_thr[x] = p.thr[x];
+    for (int x = tid; x < R * kAccCount; x += nt) s_acc[x] = 0ull;
+    for (int x = tid; x < kClusterMailPasses * R * 2; x += nt) s_cmb[x] = 0ull;
+    for (int c = tid; c < C; c += nt) {
+        s_E[c] = c < nc ? p.E[c0 + c] : 0;
+        s_M[c] = c < nc ? p.M[c0 + c] : 0;
+        s_rung[c] = c < nc ? p.rung_of_slot[c0 + c] : 0;
+        s_sums[2 * c] = s_sums[2 * c + 1] = 0;
+    }
+    if (tid == 0) s_ctl[0] = 0;
+    __syncthreads();
+    cluster_barrier();  // every CTA's mailboxes are clear before anyone publishes
+
+    const PhiloxKey key = philox_schedule(p.key0, p.key1);
+    const int Lmax = p.Lmax;
+    const int my_c = tid & (C - 1);  // this thread's chain, the same in every level
+    int lgC = 0;
+    while ((1 << lgC) < C) ++lgC;
+    const bool live = my_c < nc;
+    const uint32_t my_slot = (uint32_t)(c0 + my_c);
+    const uint32_t* thr = s_thr + (size_t)s_rung[my_c] * p.nL3 + 1;  // m = 0 column
+    const uint32_t qmod0 = (uint32_t)(q0 % kTagPeriod);
+    int since_pass = 0, next_pass = 0;  // thread c < nc: chain c's swap schedule
+
+    for (int s = 0; s < n_sweeps; ++s) {
+        const uint32_t t = (uint32_t)(t0 + s);
+        int dE = 0, nf = 0;
+        for (int lev = 0; lev < p.n_levels; ++lev) {
+            const int base = s_loff[lev];
+            const int units = (s_loff[lev + 1] - base) << lgC;
+            if (live)
+                for (int u = tid; u < units; u += nt) {
+                    const int i = (int)(s_items[base + (u >> lgC)] >> 1);
+                    const uint32_t r = philox(make_uint4(t, (uint32_t)i, my_slot, 0u), key).x;
+                    int f = s_h[i];
+#pragma unroll
+                    for (int d = 0; d < DCLASS; ++d) {
+                        const uint32_t nb = s_nbr[i * DCLASS + d];
+                        f += (int)(int8_t)(nb & 0xFFu) * (int)sp[(size_t)(nb >> 8) * C + my_c];
+                    }
+                    int8_t* own = sp + (size_t)i * C + my_c;
+                    const int sk = *own;
+                    const int Lf = sk * f;
+                    const uint32_t th = thr[(Lf + Lmax) * 3];
+                    if (th == 0xFFFFFFFFu || r < th) {
+                        *own = (int8_t)(-sk);
+                        dE -= 2 * Lf;
+                        nf += 1;
+                    }
+                }
+            __syncthreads();
+        }
+        // the sweep's changes of each chain: lanes of a warp that share a chain are C apart
+        for (int o = 16; o >= C; o >>= 1) {
+            dE += __shfl_xor_sync(0xFFFFFFFFu, dE, o);
+            nf += __shfl_xor_sync(0xFFFFFFFFu, nf, o);
+        }
+        if (live && lane < C && (dE | nf)) {
+            atomicAdd(s_sums + 2 * my_c, dE);
+            atomicAdd(s_sums + 2 * my_c + 1, nf);
+        }
+        __syncthreads();
+        // chain tid's end of sweep, in two phases: every chain of the CTA publishes before
+        // any of them waits, so partners on one CTA never wait on a thread that has not
+        // published yet (spreading the copies over the CTA's threads, behind one more
+        // barrier, measured slower)
+        SwapSide side;
+        long long E = 0, M = 0;
+        int rung = 0;
+        if (tid < nc) {
+            const int c = tid;
+            E = s_E[c];
+            M = s_M[c];
+            rung = s_rung[c];
+            const int sE = s_sums[2 * c], sF = s_sums[2 * c + 1];
+            s_sums[2 * c] = s_sums[2 * c + 1] = 0;
+            int pass = -1;
+            if (sweeps_per_swap > 0 && ++since_pass == sweeps_per_swap) {
+                since_pass = 0;
+                pass = next_pass++;
+            }
+            side = eos_publish(p, rung, E, M, sE, 0, pass, q0, qmod0, false);
+            eos_stats(p, s_acc, rung, E, M, sF);
+            if (side.active && rung != p.withhold_rung) {
+                const int idx = ((side.pass & (kClusterMailPasses - 1)) * R + rung) * 2;
+                const unsigned long long wa = ((unsigned long long)E << 24) | side.tag;
+                const unsigned long long wb = ((unsigned long long)(uint32_t)(int32_t)M << 32) | side.tag;
+                for (int r = 0; r < K; ++r) {
+                    st_cluster_u64(s_cmb + idx, (unsigned)r, wa);
+                    st_cluster_u64(s_cmb + idx + 1, (unsigned)r, wb);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < nc) {
+            const int c = tid;
+            int abort_flag = 0;
+            s_rung[c] = eos_decide_cluster(p, s_cmb, side, rung, E, M, timeout_ns, key, &abort_flag);
+            s_E[c] = E;
+            s_M[c] = M;
+            if (abort_flag) s_ctl[0] = 1;  // a partner never arrived
+        }
+        __syncthreads();
+        if (s_ctl[0]) break;  // to the cluster barrier that every CTA passes before leaving
+        thr = s_thr + (size_t)s_rung[my_c] * p.nL3 + 1;
+    }
+    __syncthreads();
+    // no CTA leaves while another may still write its mailboxes (every wait is bounded)
+    cluster_barrier();
+    if (s_ctl[0]) return;  // status holds PT_ETIMEDOUT
+    for (int x = tid; x < R * kAccCount; x += nt)
+        if (s_acc[x]) atomicAdd(p.acc + x, s_acc[x]);
+    for (int x = tid; x < N * nc; x += nt) {
+        const int c = x / N, i = x - c * N;
+        p.spins[(size_t)(c0 + c) * p.slot_stride + i] = sp[(size_t)i * C + c];
+    }
+    for (int c = tid; c < nc; c += nt) {
+        const int rung = s_rung[c];
+        p.E[c0 + c] = s_E[c];
+        p.M[c0 + c] = s_M[c];
+        p.rung_of_slot[c0 + c] = rung;
+        p.slot_of_rung[rung] = c0 + c;
+    }
+}
+
 // ------------------------------------------------------------------------- packed sweep
 // Random words of one sweep for the producer warps: word w of philox((t, i, slot,
 // p<<24 | g)) goes with copy 8g + p + 2w of site i (the same counter the update would use).
@@ -1337,6 +1534,13 @@ __global__ void scatter_kernel(DevProblem p, const int8_t* in) {
 
 // ------------------------------------------------------------------------- launchers
 static const void* sweep_fn(const LaunchPlan& plan) {
+    if (plan.path == kPathClassical) {
+        switch (plan.dclass) {
+            case 4: return (const void*)sweep_classical_kernel<4>;
+            case 8: return (const void*)sweep_classical_kernel<8>;
+            default: return (const void*)sweep_classical_kernel<32>;
+        }
+    }
     if (plan.path == kPathGeneric) {
         switch (plan.dclass) {
             case 4: return (const void*)sweep_kernel<4>;
@@ -1385,7 +1589,7 @@ cudaError_t prepare_sweep_kernel(const LaunchPlan& plan) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    if (plan.path == kPathCluster) {
+    if (plan.path == kPathCluster || plan.path == kPathClassical) {
         // clusters of up to 16 CTAs (above 8 is a non-portable size)
         e = cudaFuncSetAttribute(sweep_fn(plan), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
@@ -1415,16 +1619,17 @@ static cudaLaunchConfig_t split_config(const DevProblem& p, const LaunchPlan& pl
     return cfg;
 }
 
-// Path 9's launch: one cluster of all R CTAs.
+// Path 9's launch: one cluster of all R CTAs; path 10's: one cluster of ceil(R / C) CTAs.
 static cudaLaunchConfig_t cluster_config(const DevProblem& p, const LaunchPlan& plan, cudaStream_t s,
                                          cudaLaunchAttribute* attr) {
+    const int ctas = plan.path == kPathClassical ? (p.R + plan.chains_per_cta - 1) / plan.chains_per_cta : p.R;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(p.R);
+    cfg.gridDim = dim3(ctas);
     cfg.blockDim = dim3(plan.threads);
     cfg.dynamicSmemBytes = plan.smem_bytes;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)p.R;
+    attr[0].val.clusterDim.x = (unsigned)ctas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -1434,8 +1639,9 @@ static cudaLaunchConfig_t cluster_config(const DevProblem& p, const LaunchPlan& 
 
 cudaError_t sweep_resident_chains(const DevProblem& p, const LaunchPlan& plan, long long* chains) {
     *chains = 0;
-    if (plan.path == kPathCluster) {
-        if (p.R > 16) return cudaSuccess;
+    if (plan.path == kPathCluster || plan.path == kPathClassical) {
+        const int ctas = plan.path == kPathClassical ? (p.R + plan.chains_per_cta - 1) / plan.chains_per_cta : p.R;
+        if (ctas > 16) return cudaSuccess;
         cudaLaunchAttribute attr[1];
         cudaLaunchConfig_t cfg = cluster_config(p, plan, 0, attr);
         int clusters = 0;
@@ -1463,10 +1669,11 @@ cudaError_t launch_sweeps(const DevProblem& p, const LaunchPlan& plan, long long
                           int n_sweeps, int sweeps_per_swap, long long timeout_ns, bool cooperative,
                           cudaStream_t s) {
     DevProblem pp = p;
-    int n_consumer = plan.n_consumer;
+    // the last argument: consumer threads, or (path 10) chains per CTA
+    int n_consumer = plan.path == kPathClassical ? plan.chains_per_cta : plan.n_consumer;
     void* args[] = {&pp, &t0, &q0, &n_sweeps, &sweeps_per_swap, &timeout_ns, &n_consumer};
     const void* fn = sweep_fn(plan);
-    if (plan.path == kPathCluster) {
+    if (plan.path == kPathCluster || plan.path == kPathClassical) {
         // one cluster holds every chain, so the swap passes never need a cooperative launch
         cudaLaunchAttribute attr[1];
         cudaLaunchConfig_t cfg = cluster_config(p, plan, s, attr);

@@ -115,6 +115,37 @@ def test_small_workload_on_path_9(producers):
         assert_same(g, o, "sweep %d" % (1000 * (chunk + 1)))
 
 
+def test_classical_partner_that_never_publishes_times_out_on_path_10():
+    """Path 10: the chain on rung 3 withholds its publication; its partner's bounded wait in
+    shared memory runs out, every CTA of the cluster reaches the closing cluster barrier, and
+    the call reports PT_ETIMEDOUT; the device stays usable."""
+    prob = instances.workload("classical_regular3_n256_r64", 2)
+    g = pt.PT.from_problem(prob, wait_timeout_ms=200, test_withhold_rung=3, kernel_path=10)
+    g.run(4, 1)
+    with pytest.raises(pt.PTError) as e:
+        g.sync()
+    assert e.value.code == pt.PT_ETIMEDOUT
+    g.close()
+    h, o = both(prob, kernel_path=10)
+    h.run(50, 1)
+    o.run(50, 1)
+    assert_same(h, o, "after timeout")
+
+
+def test_path_10_needs_classical_chains():
+    prob = instances.workload("regular3_n16_p32_r16", 1)  # P = 32
+    with pytest.raises(pt.PTError) as e:
+        pt.PT.from_problem(prob, kernel_path=10)
+    assert e.value.code == pt.PT_EINVAL
+    classical = instances.workload("classical_regular3_n256_r64", 1)  # R = 64
+    # (cluster_size 1 puts all 64 chains on one CTA, which needs a multiple of 64 threads)
+    for kw in (dict(cluster_size=17), dict(threads_per_block=48), dict(threads_per_block=1024),
+               dict(cluster_size=1, threads_per_block=32)):
+        with pytest.raises(pt.PTError) as e:
+            pt.PT.from_problem(classical, kernel_path=10, **kw)
+        assert e.value.code == pt.PT_EINVAL, kw
+
+
 def test_path_9_needs_the_ladder_in_one_cluster():
     prob = instances.workload("regular3_n256_p64_r64", 1)  # R = 64 > 16
     with pytest.raises(pt.PTError) as e:
@@ -239,14 +270,20 @@ def test_packed_row_lengths(P, path):
         assert_same(g, o, "%s P=%d after 200 more" % (graph, P))
 
 
-def test_classical_tiny_problem_every_sweep():
+@pytest.mark.parametrize("kw", [dict(kernel_path=1), dict(kernel_path=10, cluster_size=1),
+                                dict(kernel_path=10, cluster_size=2), dict(kernel_path=10, cluster_size=3),
+                                dict(kernel_path=10, cluster_size=1, threads_per_block=32), dict()])
+def test_classical_tiny_problem_every_sweep(kw):
     """Classical parallel tempering (P = 1, Gamma = 0, temperature ladder) on the byte-wise
-    kernel: bits after every sweep, then after 500 more with a swap every third sweep."""
+    kernel and on path 10 (three chains on one CTA with a fourth, idle slot; on two CTAs of two
+    and one; on three CTAs): bits after every sweep, then after 500 more with a swap every
+    third sweep."""
     edges = [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 0), (0, 3), (1, 4)]
     prob = instances.tiny_problem(6, edges, [1, -2, 1, -1, 2, -1, 1, -2], [1, 0, -1, 0, 1, 0], 1,
                                   [0.7, 1.4, 3.0], [0.0, 0.0, 0.0], seed=31)
-    g, o = both(prob)
-    assert g.info.kernel_path == 1
+    g, o = both(prob, **kw)
+    assert g.info.kernel_path == kw.get("kernel_path", g.info.kernel_path)
+    assert g.info.kernel_path in (1, 10)
     for s in range(30):
         g.run(1, 1)
         o.run(1, 1)
@@ -256,11 +293,14 @@ def test_classical_tiny_problem_every_sweep():
     assert_same(g, o, "after 500 more")
 
 
-def test_classical_workload_full_length():
+@pytest.mark.parametrize("kw", [dict(), dict(kernel_path=1), dict(kernel_path=10),
+                                dict(kernel_path=10, cluster_size=16)])
+def test_classical_workload_full_length(kw):
     """Random 3-regular N=256, P=1, R=64 temperatures geometric 0.1..3.0, 2000 sweeps with a
-    swap pass after every sweep; checked every 200 sweeps."""
+    swap pass after every sweep; checked every 200 sweeps: the autotuned plan, the byte-wise
+    kernel, and path 10 with 16 chains on each of 4 CTAs and 4 chains on each of 16."""
     prob = instances.workload("classical_regular3_n256_r64", 1)
-    g, o = both(prob)
+    g, o = both(prob, **kw)
     for chunk in range(prob.n_sweeps // 200):
         g.run(200, 1)
         o.run(200, 1)
