@@ -115,6 +115,26 @@ def test_small_workload_on_path_9(producers):
         assert_same(g, o, "sweep %d" % (1000 * (chunk + 1)))
 
 
+@pytest.mark.parametrize("R,cluster", [(1, 0), (5, 2), (17, 0), (20, 8)])
+def test_classical_ladders_of_any_length_on_path_10(R, cluster):
+    """Path 10 with one chain, with a last CTA holding fewer chains than the others (5 = 4 + 1,
+    17 = 16 + 1, 20 = 3 x 8 - 4 idle slots), and the default cluster."""
+    ladder_T = np.geomspace(0.4, 3.0, R)
+    edges = [(i, (i + 1) % 24) for i in range(24)] + [(i, (i + 12) % 24) for i in range(12)]
+    J = [((3 * i + 1) % 5) - 2 or 1 for i in range(len(edges))]
+    h = [((5 * i) % 3) - 1 for i in range(24)]
+    prob = instances.tiny_problem(24, edges, J, h, 1, ladder_T, np.zeros(R), seed=600 + R)
+    g, o = both(prob, kernel_path=10, cluster_size=cluster)
+    assert g.info.kernel_path == 10
+    for s in range(12):
+        g.run(1, 1)
+        o.run(1, 1)
+        assert_same(g, o, "sweep %d" % (s + 1))
+    g.run(300, 2)
+    o.run(300, 2)
+    assert_same(g, o, "after 300 more")
+
+
 def test_classical_partner_that_never_publishes_times_out_on_path_10():
     """Path 10: the chain on rung 3 withholds its publication; its partner's bounded wait in
     shared memory runs out, every CTA of the cluster reaches the closing cluster barrier, and
