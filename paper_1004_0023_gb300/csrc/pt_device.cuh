@@ -199,14 +199,16 @@ __device__ __forceinline__ void cluster_arrive_relaxed() { asm volatile("barrier
 __device__ __forceinline__ void cluster_arrive_release() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait_acquire() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 
-// A 64-bit word into CTA `rank`'s copy of a shared-memory location (distributed shared
-// memory), relaxed at cluster scope: the readers poll the word itself, so no other ordering
-// is needed.
-__device__ __forceinline__ void st_cluster_u64(const void* local, unsigned rank, unsigned long long v) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+// Two adjacent 64-bit words (16-byte aligned) into CTA `rank`'s copy of a shared-memory
+// location (distributed shared memory), in one store, relaxed at cluster scope: each word
+// carries its own tag and the readers poll the words themselves, so no other ordering is
+// needed.
+__device__ __forceinline__ void st_cluster_u64x2(const void* local, unsigned rank, unsigned long long a,
+                                                 unsigned long long b) {
+    const unsigned l = (unsigned)__cvta_generic_to_shared(local);
     unsigned ra;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
-    asm volatile("st.relaxed.cluster.shared::cluster.u64 [%0], %1;" ::"r"(ra), "l"(v) : "memory");
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(l), "r"(rank));
+    asm volatile("st.relaxed.cluster.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(ra), "l"(a), "l"(b) : "memory");
 }
 
 // This CTA's shared-memory word, as the other CTAs of the cluster last wrote it.

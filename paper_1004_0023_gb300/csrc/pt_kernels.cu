@@ -604,10 +604,7 @@ __global__ void __launch_bounds__(512, 1)
                 const int idx = ((side.pass & (kClusterMailPasses - 1)) * R + rung) * 2;
                 const unsigned long long wa = ((unsigned long long)E << 24) | side.tag;
                 const unsigned long long wb = ((unsigned long long)(uint32_t)(int32_t)M << 32) | side.tag;
-                for (int r = 0; r < K; ++r) {
-                    st_cluster_u64(s_cmb + idx, (unsigned)r, wa);
-                    st_cluster_u64(s_cmb + idx + 1, (unsigned)r, wb);
-                }
+                for (int r = 0; r < K; ++r) st_cluster_u64x2(s_cmb + idx, (unsigned)r, wa, wb);
             }
         }
         __syncthreads();
@@ -852,10 +849,7 @@ __device__ __forceinline__ void sweep_packed_body(const DevProblem& p, int slot,
                     const int idx = ((side.pass & (kClusterMailPasses - 1)) * p.R + rung) * 2;
                     const unsigned long long wa = ((unsigned long long)E << 24) | side.tag;
                     const unsigned long long wb = ((unsigned long long)(uint32_t)(int32_t)M << 32) | side.tag;
-                    for (int r = 0; r < p.R; ++r) {
-                        st_cluster_u64(s_cmb + idx, (unsigned)r, wa);
-                        st_cluster_u64(s_cmb + idx + 1, (unsigned)r, wb);
-                    }
+                    for (int r = 0; r < p.R; ++r) st_cluster_u64x2(s_cmb + idx, (unsigned)r, wa, wb);
                 }
             }
         } else if (PRE && !consumer && s + 1 < n_sweeps) {
