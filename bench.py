@@ -96,12 +96,12 @@ def kernel_source_hash(which: str) -> str:
 MEASURED_TRAFFIC: dict = {
     # one 1000-sweep launch of the N=256, P=64, R=64 plan (path 8, 384 threads): 1.67 MB read, 0 written
     ("sweep_peer_kernel (int8, random words from a second CTA of each chain's cluster)", "regular3_n256_p64_r64_2000"):
-        ("sweep", "35a9079bc5007d10", 1660160),
+        ("sweep", "eeb5a47f876062d7", 1631488),
     # one 500-sweep launch of the K4,4 lattice, bit-packed (path 4, 512 threads)
-    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("sweep", "35a9079bc5007d10", 26760192 + 3584),
+    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("sweep", "eeb5a47f876062d7", 26654208 + 4352),
     # one graph-replayed launch of the 512-request mix, 1000 sweeps each (clusters of 2, one
     # warp per chain): 1.286 TB read + 1.342 TB written, 1.85 B per attempt
-    ("batch_kernel", "batched_512x1000"): ("batch", "3fc68c595ae6a118", 1285691055104 + 1342281900032),
+    ("batch_kernel", "batched_512x1000"): ("batch", "03c48b7897e5aea9", 1285412840192 + 1342290039808),
 }
 
 
