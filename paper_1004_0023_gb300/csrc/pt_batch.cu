@@ -623,7 +623,7 @@ int ptq::prepare_request(const pt_request& r, Prepared& pr, char* why, size_t wh
     pr.slot_stride = (int)(((size_t)N * P + 15) & ~(size_t)15);
     build_tables(R, P, Lmax, r.ladder, pr.thr, pr.coef);
     if (pr.coef.size() < 2) pr.coef.assign(2, 0.0);
-    level_schedule(N, adj, pr.items, pr.level_off, per_round);
+    level_schedule(N, adj, pr.items, pr.level_off, per_round, P / 4);  // rows of P bytes (int8 packed)
     pr.n_levels = (int)pr.level_off.size() - 1;
     build_site_desc(N, P, pr.dc, adj, adjJ, inst->h, pr.sdesc);
     return PT_OK;

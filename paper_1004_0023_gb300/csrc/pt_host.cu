@@ -127,7 +127,7 @@ void ptq::build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vecto
 // they are (i,0) and (i,1), or (i,p) and (j,p) with i, j adjacent; the level of an update
 // is one more than the largest level of the earlier updates it conflicts with.
 void ptq::level_schedule(int N, const std::vector<std::vector<int>>& adj, std::vector<uint32_t>& items,
-                           std::vector<int32_t>& level_off, int per_round) {
+                           std::vector<int32_t>& level_off, int per_round, int row_words) {
     // as early as possible: l0 / l1 = the longest chain of predecessors of (i, 0) / (i, 1)
     std::vector<int> l0(N), l1(N);
     int nlev = 0;
@@ -229,6 +229,35 @@ void ptq::level_schedule(int N, const std::vector<std::vector<int>>& adj, std::v
     for (int i = 0; i < N; ++i) {
         items[fill[l0[i]]++] = ((uint32_t)i << 1) | 0u;
         items[fill[l1[i]]++] = ((uint32_t)i << 1) | 1u;
+    }
+    if (row_words > 0) {
+        // Within a level the order is free. The packed kernels give consecutive items of a
+        // level to neighbouring lanes of a warp, each lane a 4-byte word at column g of the
+        // item's row half, so an item's words start at shared-memory bank
+        // (i * row_words + parity * row_words / 2) mod 32. Dealing the level's items round
+        // robin over those start banks puts items with different starts side by side, so a
+        // warp's loads of its items' own words (and, for rows of 32 words, of every
+        // neighbour word) fall in different banks.
+        std::vector<uint32_t> lev_items;
+        std::vector<std::vector<uint32_t>> by_bank(32);
+        for (int l = 0; l < nlev; ++l) {
+            for (auto& b : by_bank) b.clear();
+            for (int x = level_off[l]; x < level_off[l + 1]; ++x) {
+                const uint32_t it = items[x], i = it >> 1, par = it & 1u;
+                by_bank[(i * (uint32_t)row_words + par * (uint32_t)(row_words / 2)) & 31u].push_back(it);
+            }
+            lev_items.clear();
+            for (size_t k = 0;; ++k) {
+                bool any = false;
+                for (auto& b : by_bank)
+                    if (k < b.size()) {
+                        lev_items.push_back(b[k]);
+                        any = true;
+                    }
+                if (!any) break;
+            }
+            std::copy(lev_items.begin(), lev_items.end(), items.begin() + level_off[l]);
+        }
     }
 }
 
@@ -580,6 +609,14 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
     // path 10's shape for a cluster of about K CTAs: C = the power of two at or above R / K
     // chains per CTA, ceil(R / C) CTAs; and its block: a multiple of 32 and of C holding one
     // update of every chain of the CTA for the average level, at most 512 threads
+    // the int8 packed kernels' rows are P bytes, P/4 words: their levels are ordered for the
+    // shared-memory banks (see level_schedule); the other layouts keep site order
+    auto row_words_for = [&](int pth) {
+        return (pth == kPathPacked || pth == kPathPackedInline || pth == kPathPeer || pth == kPathCluster ||
+                pth == kPathPackedChains)
+                   ? P / 4
+                   : 0;
+    };
     auto classical_chains = [&](int K) {
         int C = 1;
         while ((long long)C * K < R) C <<= 1;
@@ -744,7 +781,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         }
         const int per_round = path == kPathClassical ? c->plan.threads / c->plan.chains_per_cta
                                                      : c->plan.n_consumer / cols;
-        level_schedule(N, adj, items, level_off, std::max(1, per_round));
+        level_schedule(N, adj, items, level_off, std::max(1, per_round), row_words_for(path));
         if (P == 1) drop_odd_updates(items, level_off);
         p.n_levels = (int)level_off.size() - 1;
         // the level offsets live in shared memory: size it for this schedule's level count
@@ -888,7 +925,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
         }
         int cols = 1;
         while (cols < P / 8) cols <<= 1;
-        level_schedule(N, adj, items, level_off, std::max(1, pl.group_threads / cols));
+        level_schedule(N, adj, items, level_off, std::max(1, pl.group_threads / cols), P / 4);
         cudaStream_t s = c->stream;
         if ((e = cudaMemcpyAsync(d_items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s)) !=
                 cudaSuccess ||
@@ -993,7 +1030,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
                 if (!chains_plan(pc, packed_dc, cd.cluster, kGroupWidenDefault, pl, cd.group_threads)) return false;
                 int cols = 1;
                 while (cols < P / 8) cols <<= 1;
-                level_schedule(N, adj, it_c, off_c, std::max(1, pl.group_threads / cols));
+                level_schedule(N, adj, it_c, off_c, std::max(1, pl.group_threads / cols), P / 4);
                 pc.n_levels = (int)off_c.size() - 1;
                 return true;
             }
@@ -1014,7 +1051,7 @@ extern "C" int pt_create(const pt_instance* inst, int32_t P, const pt_rung* ladd
             } else {
                 while (cols < P / 8) cols <<= 1;
             }
-            level_schedule(N, adj, it_c, off_c, std::max(1, pl.n_consumer / cols));
+            level_schedule(N, adj, it_c, off_c, std::max(1, pl.n_consumer / cols), row_words_for(cd.path));
             if (P == 1) drop_odd_updates(it_c, off_c);
             pc.n_levels = (int)off_c.size() - 1;
             pl.smem_bytes = sweep_smem_bytes(pc, cd.path, pl.dclass, cpre);  // sized for this schedule

@@ -167,8 +167,10 @@ void build_tables(int R, int P, int Lmax, const pt_rung* ladder, std::vector<uin
                   std::vector<double>& coef);
 // per_round > 0: levels balanced for a kernel that takes per_round items of a level at a
 // time (same level count, same dependencies); 0: every update as early as possible.
+// row_words > 0: each level's items ordered for a packed kernel whose rows are row_words
+// 4-byte words (see level_schedule); 0: in site order.
 void level_schedule(int N, const std::vector<std::vector<int>>& adj, std::vector<uint32_t>& items,
-                    std::vector<int32_t>& level_off, int per_round = 0);
+                    std::vector<int32_t>& level_off, int per_round = 0, int row_words = 0);
 void build_site_desc(int N, int row_bytes, int dclass, const std::vector<std::vector<int>>& adj,
                      const std::vector<std::vector<int>>& adjJ, const int32_t* h, std::vector<uint32_t>& desc);
 
