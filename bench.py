@@ -96,12 +96,12 @@ def kernel_source_hash(which: str) -> str:
 MEASURED_TRAFFIC: dict = {
     # one 1000-sweep launch of the N=256, P=64, R=64 plan (path 8, 384 threads): 1.67 MB read, 0 written
     ("sweep_peer_kernel (int8, random words from a second CTA of each chain's cluster)", "regular3_n256_p64_r64_2000"):
-        ("sweep", "eeb5a47f876062d7", 1631488),
+        ("sweep", "f982c437e1429c9c", 1646848),
     # one 500-sweep launch of the K4,4 lattice, bit-packed (path 4, 512 threads)
-    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("sweep", "eeb5a47f876062d7", 26654208 + 4352),
+    ("sweep_packed_kernel (bit-packed)", "chimera16_n2048_p128_r96_500"): ("sweep", "f982c437e1429c9c", 26689280 + 4096),
     # one graph-replayed launch of the 512-request mix, 1000 sweeps each (clusters of 2, one
     # warp per chain): 1.286 TB read + 1.342 TB written, 1.85 B per attempt
-    ("batch_kernel", "batched_512x1000"): ("batch", "03c48b7897e5aea9", 1285412840192 + 1342290039808),
+    ("batch_kernel", "batched_512x1000"): ("batch", "5d28179cf3346bf2", 1285770739456 + 1342508638720),
 }
 
 
@@ -587,7 +587,8 @@ def run_serving(args, torch, capacity, gpu_index=0):
     offered = sum(p.attempts_per_sweep * p.n_sweeps for _, p in trace) / max(args.overload_seconds, 1e-9)
     sampler = ClockSampler(gpu_index)
     sampler.start()
-    res = serve.replay_batched(trace, stream=stream.cuda_stream, deadline=args.overload_seconds + 30.0)
+    # about 3x capacity: the queue drains for about twice the arrival window after it closes
+    res = serve.replay_batched(trace, stream=stream.cuda_stream, deadline=args.overload_seconds + 50.0)
     res["clocks"] = sampler.stop()
     res.update(rate_per_s=args.serving_rate, arrival_seconds=args.overload_seconds, offered_attempts_per_s=offered,
                arrived=len(trace))
